@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark of the sketching hot path on the tall regression workload.
+
+Workload (seeded, synthetic): A is 1,048,576 x 256 FP32 with N(0,1) entries times a per-row lognormal(0,1)
+factor, b = A x* + N(0, 1e-3) noise.  One step = one sketch-and-solve (rmc_lsr_sketch: [A, b] sketched in
+one pass, then the FP64 solve) for each sketch kind (count sketch, SRHT, Gaussian) and each sketch size
+s in {1024, 4096}: six calls.  The metric is sketch throughput in GB/s: the algorithmic bytes of the six
+calls (read A and b, write the s x 257 sketch) divided by the step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one process per GPU): every rank runs its own replica of the workload (the path has no
+data exchange); value = bytes of all ranks / max over ranks of the timed region ("scaling": "weak").
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, N_COLS = 1 << 20, 256
+STEP = [("countsketch", 1024), ("countsketch", 4096), ("srht", 1024), ("srht", 4096),
+        ("gaussian", 1024), ("gaussian", 4096)]
+SEED = 20150527
+ORACLE_SAMPLE_ROWS = 4096          # rows of A the CPU oracle sketches per call
+GAUSS_PREC = os.environ.get("RMC_BENCH_GAUSS_PREC", "fp32")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"], "sm_max_mhz": p.get("sm_max_mhz", 2070.0),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def call_bytes(m, n, s):
+    """Algorithmic bytes of one sketch of [A, b]: read A and b once, write the s x (n+1) sketch."""
+    return 4 * (m * n + m + s * (n + 1))
+
+
+# ------------------------------------------------------------------------------------------ rank helpers
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def combine_over_ranks(seconds, nbytes, world):
+    """(max time over ranks, total bytes over ranks); identity at world size 1."""
+    if world == 1:
+        return seconds, nbytes
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    b = torch.tensor([float(nbytes)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(b.item())
+
+
+# ------------------------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is None:
+            return False
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+        return False
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------------------------------- CPU arm
+
+def oracle_sample(seconds_budget=None):
+    """The FP64 oracle as it stands, on the first ORACLE_SAMPLE_ROWS rows of the workload recipe (drawn on the
+    CPU), for every call of the step.  Returns (GB/s, seconds, bytes, description)."""
+    import numpy as np
+    import workloads
+    from oracle import lsr
+    A, b, _ = workloads.tall_lsr_numpy(ORACLE_SAMPLE_ROWS, N_COLS, seed=SEED)
+    nbytes = 0
+    t0 = time.perf_counter()
+    for kind, s in STEP:
+        s_eff = min(s, ORACLE_SAMPLE_ROWS)
+        lsr.lsr_sketch(A, b, s_eff, kind, SEED)
+        nbytes += call_bytes(ORACLE_SAMPLE_ROWS, N_COLS, s_eff)
+    dt = time.perf_counter() - t0
+    desc = ("oracle lsr_sketch (FP64 NumPy) for the 6 calls of one step on a %d x %d sample of the workload "
+            "(s capped at the sample's rows); GB/s = algorithmic bytes of the sample / wall time" %
+            (ORACLE_SAMPLE_ROWS, N_COLS))
+    return nbytes / dt / 1e9, dt, nbytes, desc
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        oracle_sample()
+    total_b, total_t = 0, 0.0
+    for _ in range(args.steps):
+        _, dt, nb, desc = oracle_sample()
+        total_b += nb
+        total_t += dt
+    value = total_b / total_t / 1e9
+    line = {
+        "impl": "reference", "metric": "sketch HBM GB/s", "value": value, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "tall-lsr sample %dx%d (6 sketch-and-solve calls per step)" % (ORACLE_SAMPLE_ROWS, N_COLS)},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------------------------- GPU arm
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_1505_07570_gb300 as rmc
+    import workloads
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    A, b, _ = workloads.tall_lsr_torch(M, N_COLS, seed=SEED + rank)
+    torch.cuda.synchronize()
+    step_bytes = sum(call_bytes(M, N_COLS, s) for _, s in STEP)
+
+    def step():
+        for kind, s in STEP:
+            rmc.rmc_lsr_sketch(A, b, s, kind, SEED, prec=GAUSS_PREC if kind == "gaussian" else "fp32")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    rmc.rmc_sync()
+    stream = torch.cuda.current_stream()
+    launches0 = rmc.rmc_launch_counter()
+    rmc.rmc_profile_begin()
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    rmc.rmc_sync()
+    seconds = ev0.elapsed_time(ev1) / 1e3
+    launches = rmc.rmc_launch_counter() - launches0
+    kernels = {}
+    for name, tag in [("countsketch_gather", rmc.K_COUNTSKETCH), ("srht_stage1", rmc.K_SRHT),
+                      ("srht_stage2", rmc.K_SRHT_REDUCE), ("gaussian_sketch", rmc.K_GAUSSIAN),
+                      ("gram_fp64", rmc.K_GRAM), ("small_fp64", rmc.K_SMALL)]:
+        cnt, ms = rmc.rmc_profile_read(tag)
+        if cnt:
+            kernels[name] = {"launches": cnt, "ms_total": ms}
+    rmc.rmc_profile_end()
+    tmax, total_bytes = combine_over_ranks(seconds, step_bytes * args.steps, world)
+
+    # e2e: inputs copied from pinned host memory every step, results read back
+    A_h = A.cpu().pin_memory()
+    b_h = b.cpu().pin_memory()
+    h2d = A_h.numel() * 4 + b_h.numel() * 4
+    xs = []
+    for _ in range(max(1, args.warmup)):
+        A.copy_(A_h, non_blocking=True)
+        b.copy_(b_h, non_blocking=True)
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    d2h = 0
+    for _ in range(args.steps):
+        A.copy_(A_h, non_blocking=True)
+        b.copy_(b_h, non_blocking=True)
+        outs = [rmc.rmc_lsr_sketch(A, b, s, kind, SEED, prec=GAUSS_PREC if kind == "gaussian" else "fp32")
+                for kind, s in STEP]
+        host = [x.to("cpu", non_blocking=False) for x in outs]
+        d2h = sum(x.numel() * 8 for x in host)
+        xs = host
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_seconds, _ = combine_over_ranks(e0.elapsed_time(e1) / 1e3, 0, world)
+    e2e_value = step_bytes * args.steps * world / e2e_seconds / 1e9
+    assert all(bool(torch.isfinite(x).all()) for x in xs)
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    pk = peaks()
+    value = total_bytes / tmax / 1e9
+    # roofline of the dominant kernel
+    dom = max(kernels.items(), key=lambda kv: kv[1]["ms_total"]) if kernels else None
+    roof = None
+    if dom:
+        name, rec = dom
+        avg_s = rec["ms_total"] / rec["launches"] / 1e3
+        if name == "gaussian_sketch":
+            # per launch: one (kind, s) call; flops of the product, averaged over the two sketch sizes
+            flops = sum(2.0 * M * s * (N_COLS + 1) for k, s in STEP if k == "gaussian") / 2
+            if GAUSS_PREC == "fp32":
+                peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+                roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
+            else:
+                ratio = 1.1 / 2.25 if GAUSS_PREC == "tf32" else 1.0
+                peak = pk["bf16_tflops"] * ratio
+                roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "peak_source": "%s bf16 x nominal %s/bf16 ratio" % (pk["source"], GAUSS_PREC)}
+        else:
+            per_launch = sum(call_bytes(M, N_COLS, s) for k, s in STEP if k == name.split("_")[0]) / 2
+            roof = {"bound": "hbm", "achieved": per_launch / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "peak_source": pk["source"]}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["kernel"] = name
+        roof["traffic"] = None
+    for name, rec in kernels.items():
+        avg_s = rec["ms_total"] / rec["launches"] / 1e3
+        rec["ms_avg"] = avg_s * 1e3
+        kind = name.split("_")[0]
+        if kind in ("countsketch", "srht") and name != "srht_stage2":
+            rec["hbm_frac_of_" + pk["source"]] = (sum(call_bytes(M, N_COLS, s) for k, s in STEP if k == kind) / 2
+                                                 / avg_s / 1e9 / pk["hbm_gbs"])
+
+    cpu = None
+    if world == 1:
+        v, dt, nb, desc = oracle_sample()
+        cpu = {"value": v, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+
+    line = {
+        "metric": "sketch HBM GB/s", "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "tall-lsr 1048576x256 FP32 + b; step = lsr_sketch x {countsketch, srht, gaussian}"
+                               " x s {1024, 4096}", "gaussian_prec": GAUSS_PREC, "l2": "inputs (1.07 GB) > L2",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernels,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * rmc.h -- randomized matrix computations on one NVIDIA GB300 (sm_103a): sketching, randomized SVD and
+ * sketch-and-solve least squares, after S. Wang, "A Practical Guide to Randomized Matrix Computations with
+ * MATLAB Implementations" (arXiv:1505.07570).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Matrices are FP32, row-major, with a leading dimension (elements between the starts of consecutive
+ *    rows) >= the number of columns.  A is m x n.
+ *  - Matrix and vector pointers are DEVICE pointers owned by the caller; the library never frees them and
+ *    never keeps them after the call returns.  Outputs must not alias inputs.
+ *  - Every call is asynchronous on the context's CUDA stream: it returns once the work is enqueued.
+ *    Outputs are valid after rmc_sync(ctx) (or after the stream completes).
+ *  - Argument errors are returned synchronously and nothing is enqueued.  Errors found on the device
+ *    (a non-positive pivot, an iteration cap, a bounded wait that expired) are written to the context's
+ *    device status word and returned by the next rmc_sync.  No kernel traps.
+ *  - Workspace is owned by the context (stream-ordered device allocations, capped by the HBM budget given
+ *    to rmc_create); a call whose workspace would exceed the budget returns RMC_ENOMEM.
+ *  - The sketch acts on the ROW dimension: C = S^T A is s x n, the orientation of the sketched least
+ *    squares problem of Sec. 4.2.  The column sketch C = A S of Ch. 3 is rmc_sketch applied to A^T.
+ *
+ * Randomness (one definition, shared with the oracle through this header and nothing else)
+ * ------------------------------------------------------------------------------------------
+ *  Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  key = (seed mod 2^32, seed div 2^32);
+ *  counter = (index mod 2^32, index div 2^32, stream, instance).  u(w) = ((w >> 9) + 1/2) * 2^-23.
+ *   stream 0  Gaussian entries.  Entry (i, j) of a rows x cols matrix uses block index
+ *             i * ceil(cols/4) + j/4; words (0,1) -> columns 4t, 4t+1 and words (2,3) -> 4t+2, 4t+3 by
+ *             Box-Muller: r = sqrt(-2 ln u(w_a)), (r cos 2 pi u(w_b), r sin 2 pi u(w_b)).
+ *   stream 1  SRHT row sign of row i: -1 if bit 31 of word 0 of block i is set, else +1.
+ *   stream 2  count-sketch row i: bucket h(i) = (word0 * s) >> 32, sign g(i) = -1 if bit 31 of word 1.
+ *   stream 3  SRHT sample key of index j: (word0 << 32) | word1 of block j; the sample is the s indices
+ *             with the smallest keys (ties to the smaller index), in ascending order.
+ *  Hashes, signs and sample indices are bit-identical to the oracle's; Gaussian entries agree to FP32
+ *  rounding of log/sqrt/sin/cos.
+ */
+#ifndef RMC_H
+#define RMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------------------------ status */
+#define RMC_OK        0
+#define RMC_EINVAL    1   /* bad argument: null pointer, ld < cols, s < 1, s > N (SRHT), k < 1, ...     */
+#define RMC_EALIGN    2   /* a pointer or leading dimension breaks the 16-byte rule of a TMA-fed path    */
+#define RMC_ENOMEM    3   /* workspace would exceed the context's HBM budget, or allocation failed       */
+#define RMC_ENUMERIC  4   /* non-positive Cholesky pivot, or Jacobi SVD hit its sweep cap                */
+#define RMC_ETIMEOUT  5   /* a bounded device-side wait expired                                          */
+#define RMC_ECUDA     6   /* a CUDA runtime call or kernel launch failed                                 */
+#define RMC_PENDING   7   /* request not finished yet                                                    */
+
+/* ----------------------------------------------------------------------------------- sketch kinds */
+#define RMC_GAUSSIAN     0   /* S = G / sqrt(s), G iid N(0,1)                                Sec. 3.2.1 */
+#define RMC_SRHT         1   /* S^T = (1/sqrt(s)) P^T H_N D, rows zero-padded to N = 2^ceil(log2 m)
+                                                                                             Sec. 3.2.2 */
+#define RMC_COUNTSKETCH  2   /* one +-1 per row of S, in a uniformly hashed column   Sec. 3.2.3, Alg. 3.1 */
+
+/* ------------------------------------------------------------- GEMM operand precision (accumulate FP32) */
+#define RMC_FP32  0   /* FP32 operands on the CUDA cores (the plain form)                                 */
+#define RMC_TF32  1   /* TF32 operands on the tensor cores (tcgen05.mma kind::tf32), FP32 accumulation    */
+#define RMC_BF16  2   /* BF16 operands on the tensor cores (tcgen05.mma kind::f16), FP32 accumulation     */
+
+typedef struct rmc_ctx rmc_ctx;
+
+/* ------------------------------------------------------------------------------------------ context */
+
+/* Create a context bound to the current CUDA device and to `cuda_stream` (a cudaStream_t; NULL = the legacy
+ * default stream).  hbm_budget_bytes caps the context's workspace (0 = 64 GiB).  On success *ctx owns the
+ * workspace and a device status word; release with rmc_destroy.  Errors: RMC_EINVAL (ctx NULL),
+ * RMC_ECUDA. */
+int rmc_create(rmc_ctx **ctx, void *cuda_stream, size_t hbm_budget_bytes);
+
+/* Wait for the context's stream, free its workspace and the context.  NULL is accepted. */
+int rmc_destroy(rmc_ctx *ctx);
+
+/* Rebind the context to another stream (later calls are enqueued there). */
+int rmc_set_stream(rmc_ctx *ctx, void *cuda_stream);
+
+/* Wait for the context's stream, then return and clear the device status word: RMC_OK, or the first
+ * device-detected error since the last rmc_sync (RMC_ENUMERIC, RMC_ETIMEOUT), or RMC_ECUDA. */
+int rmc_sync(rmc_ctx *ctx);
+
+/* A static description of a status code. */
+const char *rmc_status_string(int status);
+
+/* Bytes of device workspace the context currently holds. */
+int rmc_workspace_bytes(const rmc_ctx *ctx, size_t *bytes);
+
+/* ---------------------------------------------------------------------------------- the three calls */
+
+/* Sketch: C = S^T A, C is s x n with leading dimension ldc (Sec. 3.2; sketch C = A S, Ch. 3 opening, in the
+ * row orientation of Sec. 4.2).
+ *   kind  RMC_GAUSSIAN: S = G / sqrt(s), m x s (Sec. 3.2.1); any s >= 1.
+ *         RMC_SRHT: rows sign-flipped (D), zero-padded to N = next power of two >= m, transformed by the
+ *                   unnormalised Hadamard matrix H_N (Sylvester order), s sampled rows without replacement
+ *                   kept in ascending index order, scaled by 1/sqrt(s) (Sec. 3.2.2); 1 <= s <= N.
+ *         RMC_COUNTSKETCH: C[h(i), :] += g(i) A[i, :] for every row i (Algorithm 3.1); any s >= 1.
+ *   prec  GEMM operand precision of the Gaussian kind (RMC_FP32, RMC_TF32, RMC_BF16); ignored otherwise.
+ *   seed  64-bit Philox key; the same (seed, m, s, kind) always gives the same S.
+ * Errors: RMC_EINVAL, RMC_ENOMEM, RMC_ECUDA. */
+int rmc_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda,
+               int64_t s, int kind, uint64_t seed, int prec, float *C, int64_t ldc);
+
+/* Sketch-and-solve least squares (Sec. 4.2): sketch the augmented matrix [A, b] with ONE operator S (as the
+ * listing of Sec. 4.2 does), then x = argmin_x || (S^T A) x - S^T b ||_2 solved in FP64 by CholeskyQR2 of the
+ * augmented s x (n+1) sketch (x = R11^-1 r12 from its R factor).  b has m entries; x (device, FP64) n.
+ * Requires s >= n.  Errors: RMC_EINVAL, RMC_ENOMEM, RMC_ECUDA at the call; RMC_ENUMERIC at rmc_sync when the
+ * sketch is numerically rank deficient (non-positive pivot). */
+int rmc_lsr_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b,
+                   int64_t s, int kind, uint64_t seed, int prec, double *x);
+
+/* Randomized k-SVD with q power iterations (Algorithm 5.2 with the power step of the Sec. 5.1 listing),
+ * l = k + p:
+ *   Y = A Omega (Omega n x l iid N(0,1), stream 0), Q = orth(Y);
+ *   q times: Z = orth(A^T Q), Q = orth(A Z)              (orth = CholeskyQR2, FP64 Gram and Cholesky);
+ *   B = Q^T A (l x n); B = U_B diag(sigma) V_B^T (FP64 one-sided Jacobi on the R factor of B^T);
+ *   U = Q U_B[:, :k] (m x k, ldu), sigma[k] descending, V = V_B[:, :k] (n x k, ldv).
+ * Each column pair (u_i, v_i) is signed so the largest-magnitude entry of v_i is positive.
+ * prec selects the operand precision of the products with A.  Requires 1 <= k, l <= min(m, n), l <= 256,
+ * q >= 0.  Errors: RMC_EINVAL, RMC_ENOMEM, RMC_ECUDA; RMC_ENUMERIC at rmc_sync (breakdown of CholeskyQR2
+ * or no Jacobi convergence). */
+int rmc_rsvd(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, int k, int p, int q,
+             uint64_t seed, int prec, float *U, int64_t ldu, float *sigma, float *V, int64_t ldv);
+
+/* ------------------------------------------------- steps of the path, exposed for step-level checks */
+
+/* Philox4x32-10 words of one stream: out[4*t + w] = word w of block (first + t), t < count (device, u32). */
+int rmc_philox(rmc_ctx *ctx, uint64_t seed, uint32_t stream, uint32_t instance, uint64_t first,
+               int64_t count, uint32_t *out);
+
+/* The rows x cols standard-normal matrix of stream 0 (row-major, leading dimension ld), FP32. */
+int rmc_gaussian_matrix(rmc_ctx *ctx, uint64_t seed, uint32_t instance, int64_t rows, int64_t cols,
+                        float *out, int64_t ld);
+
+/* Count-sketch hash of rows 0..m-1: bucket[i] = h(i) in [0, s), sign[i] = g(i) (Algorithm 3.1). */
+int rmc_countsketch_hash(rmc_ctx *ctx, uint64_t seed, uint32_t instance, int64_t m, int64_t s,
+                         int32_t *bucket, float *sign);
+
+/* The SRHT sample (the randsample-then-sort step of the Sec. 3.2.2 listing): idx[0..s) = the s indices of
+ * [0, N) with the smallest stream-3 keys, ascending.  1 <= s <= N <= 2^31. */
+int rmc_srht_sample(rmc_ctx *ctx, uint64_t seed, uint32_t instance, int64_t N, int64_t s, int64_t *idx);
+
+/* CholeskyQR2 in place (the qr(., 0) of Algorithm 5.2 and of the Sec. 5.1 listing): Y (m x l, ldy, FP32) is
+ * overwritten by Q with orthonormal columns; R (l x l row-major FP64, upper triangular, optional: NULL) gets
+ * the factor with Y_in = Q R.  The Gram matrices are accumulated in FP64 and factored in FP64.
+ * Requires 1 <= l <= 256, m >= l.  RMC_ENUMERIC at rmc_sync on a non-positive pivot. */
+int rmc_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l, int64_t ldy, double *R);
+
+/* SVD of a short, wide matrix B (l x n, ldb, l <= n, l <= 256) -- the svd(Q^T A, 'econ') step of Algorithm
+ * 5.2: B = Ub diag(sigma) Vb^T with Ub l x l (row-major, FP32), sigma[l] descending (FP32) and Vb n x l
+ * (ldv, FP32).  Computed as CholeskyQR2 of B^T followed by FP64 one-sided Jacobi on the l x l factor. */
+int rmc_svd_wide(rmc_ctx *ctx, const float *B, int64_t l, int64_t n, int64_t ldb, float *Ub,
+                 float *sigma, float *Vb, int64_t ldv);
+
+/* The products with A of the range finder, power iterations and projection (Algorithm 5.2 steps 3 and 5,
+ * and the C = A' * C; C = A * C power step of the Sec. 5.1 listing):
+ *   rmc_matmul_an:  Y (m x l, ldy) = A (m x n) * X, with X n x l (ldx).
+ *   rmc_matmul_at:  W (l x n, ldw) = X^T * A,       with X m x l (ldx).
+ * prec: RMC_FP32 (CUDA cores) or RMC_TF32 (tensor cores); FP32 accumulation.  1 <= l <= 256. */
+int rmc_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X,
+                  int64_t l, int64_t ldx, int prec, float *Y, int64_t ldy);
+int rmc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X,
+                  int64_t l, int64_t ldx, int prec, float *W, int64_t ldw);
+
+/* ------------------------------------------------------------------------------- measurement hooks */
+
+/* Kernel tags for rmc_profile_read. */
+#define RMC_K_COUNTSKETCH  0   /* count-sketch gather-accumulate pass over A                         */
+#define RMC_K_SRHT         1   /* SRHT stage 1: sign flip + in-cluster FWHT of A's row blocks        */
+#define RMC_K_SRHT_REDUCE  2   /* SRHT stage 2: combination of the row blocks for the sampled rows   */
+#define RMC_K_GAUSSIAN     3   /* Gaussian sketch product with in-kernel Philox draws                */
+#define RMC_K_MATMUL_AN    4   /* Y = A X                                                            */
+#define RMC_K_MATMUL_AT    5   /* W = X^T A                                                          */
+#define RMC_K_GRAM         6   /* FP64 Gram matrix of CholeskyQR2 / the least-squares solve          */
+#define RMC_K_SMALL        7   /* Cholesky, triangular inverse, Jacobi SVD (single-block kernels)    */
+#define RMC_K_NTAGS        8
+
+/* While profiling is on, the kernels above are bracketed by CUDA events recorded on the context's stream.
+ * rmc_profile_begin clears the records; rmc_profile_read waits for the stream and returns, for one tag, the
+ * number of launches and their summed device time in milliseconds (profiling stays on). */
+int rmc_profile_begin(rmc_ctx *ctx);
+int rmc_profile_read(rmc_ctx *ctx, int tag, int64_t *launches, double *total_ms);
+int rmc_profile_end(rmc_ctx *ctx);
+
+/* Number of kernels this library has launched in the process so far (all contexts). */
+int rmc_launch_counter(uint64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RMC_H */

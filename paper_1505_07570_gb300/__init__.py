@@ -1,0 +1,283 @@
+"""Python binding of librmc (include/rmc.h): argument marshalling only.
+
+Every function takes and returns torch tensors on the current CUDA device and calls the C entry point of the
+same name; all arithmetic runs in the library's CUDA kernels.  There is no CPU path: importing this package
+fails if the compiled library is missing (build it with ``python -m paper_1505_07570_gb300.build`` or
+``__graft_entry__.build()``).
+
+Calls are asynchronous on the current torch stream; ``rmc_sync()`` waits and raises ``RmcError`` for a
+device-detected error (non-positive pivot, iteration cap).
+"""
+import ctypes
+import os
+
+from .build import LIB as _LIB_PATH
+
+RMC_OK, RMC_EINVAL, RMC_EALIGN, RMC_ENOMEM, RMC_ENUMERIC, RMC_ETIMEOUT, RMC_ECUDA, RMC_PENDING = range(8)
+RMC_GAUSSIAN, RMC_SRHT, RMC_COUNTSKETCH = 0, 1, 2
+RMC_FP32, RMC_TF32, RMC_BF16 = 0, 1, 2
+
+KIND = {"gaussian": RMC_GAUSSIAN, "srht": RMC_SRHT, "countsketch": RMC_COUNTSKETCH}
+PREC = {"fp32": RMC_FP32, "tf32": RMC_TF32, "bf16": RMC_BF16}
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError("librmc.so is not built (expected at %s); run __graft_entry__.build()" % _LIB_PATH)
+
+lib = ctypes.CDLL(_LIB_PATH)
+
+_p, _i64, _u64, _u32, _int, _sz = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                   ctypes.c_int, ctypes.c_size_t)
+_SIGS = {
+    "rmc_create": [ctypes.POINTER(_p), _p, _sz],
+    "rmc_destroy": [_p],
+    "rmc_set_stream": [_p, _p],
+    "rmc_sync": [_p],
+    "rmc_workspace_bytes": [_p, ctypes.POINTER(_sz)],
+    "rmc_sketch": [_p, _p, _i64, _i64, _i64, _i64, _int, _u64, _int, _p, _i64],
+    "rmc_lsr_sketch": [_p, _p, _i64, _i64, _i64, _p, _i64, _int, _u64, _int, _p],
+    "rmc_rsvd": [_p, _p, _i64, _i64, _i64, _int, _int, _int, _u64, _int, _p, _i64, _p, _p, _i64],
+    "rmc_philox": [_p, _u64, _u32, _u32, _u64, _i64, _p],
+    "rmc_gaussian_matrix": [_p, _u64, _u32, _i64, _i64, _p, _i64],
+    "rmc_countsketch_hash": [_p, _u64, _u32, _i64, _i64, _p, _p],
+    "rmc_srht_sample": [_p, _u64, _u32, _i64, _i64, _p],
+    "rmc_cholqr2": [_p, _p, _i64, _i64, _i64, _p],
+    "rmc_svd_wide": [_p, _p, _i64, _i64, _i64, _p, _p, _p, _i64],
+    "rmc_matmul_an": [_p, _p, _i64, _i64, _i64, _p, _i64, _i64, _int, _p, _i64],
+    "rmc_matmul_at": [_p, _p, _i64, _i64, _i64, _p, _i64, _i64, _int, _p, _i64],
+}
+_SIGS.update({
+    "rmc_profile_begin": [_p],
+    "rmc_profile_read": [_p, _int, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)],
+    "rmc_profile_end": [_p],
+    "rmc_launch_counter": [ctypes.POINTER(_u64)],
+})
+K_COUNTSKETCH, K_SRHT, K_SRHT_REDUCE, K_GAUSSIAN, K_MATMUL_AN, K_MATMUL_AT, K_GRAM, K_SMALL = range(8)
+for _name, _args in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+lib.rmc_status_string.argtypes = [ctypes.c_int]
+lib.rmc_status_string.restype = ctypes.c_char_p
+
+
+class RmcError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (where, lib.rmc_status_string(status).decode(), status))
+
+
+def _check(status, where):
+    if status != RMC_OK:
+        raise RmcError(status, where)
+
+
+class Context:
+    """An rmc_ctx bound to a device; follows the current torch stream at every call."""
+
+    def __init__(self, budget_bytes=0):
+        import torch
+        self.device = torch.cuda.current_device()
+        self.handle = _p()
+        stream = torch.cuda.current_stream().cuda_stream
+        _check(lib.rmc_create(ctypes.byref(self.handle), _p(stream), _sz(budget_bytes)), "rmc_create")
+        self.stream = stream
+
+    def bind(self):
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+        if stream != self.stream:
+            _check(lib.rmc_set_stream(self.handle, _p(stream)), "rmc_set_stream")
+            self.stream = stream
+        return self.handle
+
+    def close(self):
+        if self.handle:
+            lib.rmc_destroy(self.handle)
+            self.handle = _p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_contexts = {}
+
+
+def context():
+    import torch
+    dev = torch.cuda.current_device()
+    if dev not in _contexts:
+        _contexts[dev] = Context()
+    return _contexts[dev]
+
+
+def _ptr(t):
+    return _p(t.data_ptr())
+
+
+def _mat(t, name):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float32 and t.dim() == 2 and t.stride(1) == 1):
+        raise ValueError("%s must be a CUDA float32 matrix with unit column stride" % name)
+    return t
+
+
+def _kind(kind):
+    return KIND[kind] if isinstance(kind, str) else int(kind)
+
+
+def _prec(prec):
+    return PREC[prec] if isinstance(prec, str) else int(prec)
+
+
+def rmc_sync():
+    """Wait for the context's stream; raise RmcError for a device-detected error."""
+    _check(lib.rmc_sync(context().bind()), "rmc_sync")
+
+
+def rmc_workspace_bytes():
+    out = _sz()
+    _check(lib.rmc_workspace_bytes(context().bind(), ctypes.byref(out)), "rmc_workspace_bytes")
+    return out.value
+
+
+def rmc_sketch(A, s, kind, seed, prec="fp32", out=None):
+    """C = S^T A (s x n)."""
+    import torch
+    _mat(A, "A")
+    m, n = A.shape
+    C = out if out is not None else torch.empty(s, n, device=A.device, dtype=torch.float32)
+    _check(lib.rmc_sketch(context().bind(), _ptr(A), m, n, A.stride(0), s, _kind(kind), seed, _prec(prec),
+                          _ptr(C), C.stride(0)), "rmc_sketch")
+    return C
+
+
+def rmc_lsr_sketch(A, b, s, kind, seed, prec="fp32", out=None):
+    """x = argmin ||S^T A x - S^T b|| (FP64, n entries)."""
+    import torch
+    _mat(A, "A")
+    m, n = A.shape
+    if not (b.is_cuda and b.dtype == torch.float32 and b.is_contiguous() and b.numel() == m):
+        raise ValueError("b must be a contiguous CUDA float32 vector of length m")
+    x = out if out is not None else torch.empty(n, device=A.device, dtype=torch.float64)
+    _check(lib.rmc_lsr_sketch(context().bind(), _ptr(A), m, n, A.stride(0), _ptr(b), s, _kind(kind), seed,
+                              _prec(prec), _ptr(x)), "rmc_lsr_sketch")
+    return x
+
+
+def rmc_rsvd(A, k, p, q, seed, prec="fp32"):
+    """U (m x k), sigma (k), V (n x k) of the randomized k-SVD with l = k + p and q power iterations."""
+    import torch
+    _mat(A, "A")
+    m, n = A.shape
+    U = torch.empty(m, k, device=A.device, dtype=torch.float32)
+    sigma = torch.empty(k, device=A.device, dtype=torch.float32)
+    V = torch.empty(n, k, device=A.device, dtype=torch.float32)
+    _check(lib.rmc_rsvd(context().bind(), _ptr(A), m, n, A.stride(0), k, p, q, seed, _prec(prec), _ptr(U),
+                        U.stride(0), _ptr(sigma), _ptr(V), V.stride(0)), "rmc_rsvd")
+    return U, sigma, V
+
+
+def rmc_philox(seed, stream, instance, first, count):
+    """Philox4x32-10 words: int64 tensor (count, 4) holding the unsigned 32-bit words."""
+    import torch
+    out = torch.empty(count, 4, device="cuda", dtype=torch.int32)
+    _check(lib.rmc_philox(context().bind(), seed, stream, instance, first, count, _ptr(out)), "rmc_philox")
+    return out.to(torch.int64) & 0xFFFFFFFF
+
+
+def rmc_gaussian_matrix(seed, instance, rows, cols):
+    import torch
+    out = torch.empty(rows, cols, device="cuda", dtype=torch.float32)
+    _check(lib.rmc_gaussian_matrix(context().bind(), seed, instance, rows, cols, _ptr(out), cols),
+           "rmc_gaussian_matrix")
+    return out
+
+
+def rmc_countsketch_hash(seed, instance, m, s):
+    import torch
+    bucket = torch.empty(m, device="cuda", dtype=torch.int32)
+    sign = torch.empty(m, device="cuda", dtype=torch.float32)
+    _check(lib.rmc_countsketch_hash(context().bind(), seed, instance, m, s, _ptr(bucket), _ptr(sign)),
+           "rmc_countsketch_hash")
+    return bucket, sign
+
+
+def rmc_srht_sample(seed, instance, N, s):
+    import torch
+    idx = torch.empty(s, device="cuda", dtype=torch.int64)
+    _check(lib.rmc_srht_sample(context().bind(), seed, instance, N, s, _ptr(idx)), "rmc_srht_sample")
+    return idx
+
+
+def rmc_cholqr2(Y, want_r=True):
+    """In place: Y <- Q; returns R (l x l FP64) when want_r."""
+    import torch
+    _mat(Y, "Y")
+    m, l = Y.shape
+    R = torch.empty(l, l, device=Y.device, dtype=torch.float64) if want_r else None
+    _check(lib.rmc_cholqr2(context().bind(), _ptr(Y), m, l, Y.stride(0), _ptr(R) if want_r else None),
+           "rmc_cholqr2")
+    return R
+
+
+def rmc_svd_wide(B):
+    """B (l x n, l <= n) = Ub diag(sigma) Vb^T."""
+    import torch
+    _mat(B, "B")
+    l, n = B.shape
+    Ub = torch.empty(l, l, device=B.device, dtype=torch.float32)
+    sigma = torch.empty(l, device=B.device, dtype=torch.float32)
+    Vb = torch.empty(n, l, device=B.device, dtype=torch.float32)
+    _check(lib.rmc_svd_wide(context().bind(), _ptr(B), l, n, B.stride(0), _ptr(Ub), _ptr(sigma), _ptr(Vb),
+                            Vb.stride(0)), "rmc_svd_wide")
+    return Ub, sigma, Vb
+
+
+def rmc_matmul_an(A, X, prec="fp32"):
+    """Y = A X."""
+    import torch
+    _mat(A, "A")
+    _mat(X, "X")
+    m, n = A.shape
+    l = X.shape[1]
+    Y = torch.empty(m, l, device=A.device, dtype=torch.float32)
+    _check(lib.rmc_matmul_an(context().bind(), _ptr(A), m, n, A.stride(0), _ptr(X), l, X.stride(0), _prec(prec),
+                             _ptr(Y), Y.stride(0)), "rmc_matmul_an")
+    return Y
+
+
+def rmc_matmul_at(A, X, prec="fp32"):
+    """W = X^T A."""
+    import torch
+    _mat(A, "A")
+    _mat(X, "X")
+    m, n = A.shape
+    l = X.shape[1]
+    W = torch.empty(l, n, device=A.device, dtype=torch.float32)
+    _check(lib.rmc_matmul_at(context().bind(), _ptr(A), m, n, A.stride(0), _ptr(X), l, X.stride(0), _prec(prec),
+                             _ptr(W), W.stride(0)), "rmc_matmul_at")
+    return W
+
+
+def rmc_profile_begin():
+    _check(lib.rmc_profile_begin(context().bind()), "rmc_profile_begin")
+
+
+def rmc_profile_read(tag):
+    """(launches, total device milliseconds) of one kernel tag since rmc_profile_begin."""
+    n, ms = _i64(), ctypes.c_double()
+    _check(lib.rmc_profile_read(context().bind(), tag, ctypes.byref(n), ctypes.byref(ms)), "rmc_profile_read")
+    return n.value, ms.value
+
+
+def rmc_profile_end():
+    _check(lib.rmc_profile_end(context().bind()), "rmc_profile_end")
+
+
+def rmc_launch_counter():
+    out = _u64()
+    _check(lib.rmc_launch_counter(ctypes.byref(out)), "rmc_launch_counter")
+    return out.value

@@ -1,0 +1,695 @@
+// Dense building blocks of the randomized SVD and of the least-squares solve:
+//  - the FP32 (CUDA-core) products with A: Y = A X and W = X^T A (split-K over the rows of A),
+//  - CholeskyQR2 (Gram matrix accumulated in FP64 from exact FP32 products, FP64 Cholesky, triangular apply),
+//  - the small SVD by one-sided Jacobi on the l x l triangular factor,
+//  - the FP64 solve of the sketched least-squares problem.
+#include <cmath>
+
+#include "rmc_internal.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------------------------ FP32 SIMT GEMMs
+constexpr int GT = 64;   // output tile edge
+constexpr int GK = 16;   // reduction step
+
+// Y (m x l) = A (m x n) X (n x l).  256 threads, 4 x 4 outputs each.
+__global__ void __launch_bounds__(256) matmul_an_kernel(const float *__restrict__ A, int64_t m, int64_t n,
+                                                        int64_t lda, const float *__restrict__ X, int64_t l,
+                                                        int64_t ldx, float *__restrict__ Y, int64_t ldy) {
+  __shared__ float As[GK][GT + 4];
+  __shared__ float Xs[GK][GT + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t row0 = (int64_t)blockIdx.y * GT, col0 = (int64_t)blockIdx.x * GT;
+  float acc[4][4] = {};
+  for (int64_t k0 = 0; k0 < n; k0 += GK) {
+    for (int e = tid; e < GT * GK; e += 256) {
+      const int r = e / GK, kk = e % GK;                 // A tile: 64 rows x 16 k
+      const int64_t gr = row0 + r, gk = k0 + kk;
+      As[kk][r] = (gr < m && gk < n) ? A[gr * lda + gk] : 0.f;
+      const int kx = e / GT, c = e % GT;                 // X tile: 16 k x 64 cols
+      const int64_t gkx = k0 + kx, gc = col0 + c;
+      Xs[kx][c] = (gkx < n && gc < l) ? X[gkx * ldx + gc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      float a[4], x[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = Xs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], x[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+      if (r < m && c < l) Y[r * ldy + c] = acc[i][j];
+    }
+}
+
+// Partial W_split (l x n) = X[rows of split]^T A[rows of split]; X is m x l.
+__global__ void __launch_bounds__(256) matmul_at_kernel(const float *__restrict__ A, int64_t m, int64_t n,
+                                                        int64_t lda, const float *__restrict__ X, int64_t l,
+                                                        int64_t ldx, int64_t rows_per_split,
+                                                        float *__restrict__ out, int64_t ldo,
+                                                        int64_t split_stride) {
+  __shared__ float Xs[GK][GT + 4];
+  __shared__ float As[GK][GT + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t lrow0 = (int64_t)blockIdx.y * GT, col0 = (int64_t)blockIdx.x * GT;
+  const int64_t r_begin = (int64_t)blockIdx.z * rows_per_split;
+  const int64_t r_end = min(m, r_begin + rows_per_split);
+  float acc[4][4] = {};
+  for (int64_t k0 = r_begin; k0 < r_end; k0 += GK) {
+    for (int e = tid; e < GT * GK; e += 256) {
+      const int kk = e / GT, c = e % GT;
+      const int64_t gk = k0 + kk;
+      const bool ok = gk < r_end;
+      Xs[kk][c] = (ok && lrow0 + c < l) ? X[gk * ldx + lrow0 + c] : 0.f;
+      As[kk][c] = (ok && col0 + c < n) ? A[gk * lda + col0 + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      float x[4], a[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[i] = Xs[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a[j] = As[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(x[i], a[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float *o = out + (int64_t)blockIdx.z * split_stride;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t r = lrow0 + ty + 16 * i, c = col0 + tx + 16 * j;
+      if (r < l && c < n) o[r * ldo + c] = acc[i][j];
+    }
+}
+
+// W = sum over splits of the partials, in split order (deterministic).
+__global__ void sum_splits_kernel(const float *__restrict__ part, int splits, int64_t rows, int64_t cols,
+                                  float *__restrict__ W, int64_t ldw) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int t = 0; t < splits; ++t) s += part[t * total + e];
+    W[(e / cols) * ldw + e % cols] = s;
+  }
+}
+
+// ------------------------------------------------------------------------------------- FP64 Gram matrix
+constexpr int GRAM_T = 32;
+
+// Partial Gram of one chunk of rows for one 32 x 32 tile pair (ti <= tj): products of FP32 values are exact in
+// FP64, and the sums are FP64.
+__global__ void __launch_bounds__(256) gram_f64_kernel(const float *__restrict__ Y, int64_t m, int l, int64_t ldy,
+                                                       int64_t rows_per_chunk, double *__restrict__ part) {
+  __shared__ double As[GRAM_T][GRAM_T + 1];
+  __shared__ double Bs[GRAM_T][GRAM_T + 1];
+  // decode the tile pair
+  int p = blockIdx.x, ti = 0;
+  const int T = (l + GRAM_T - 1) / GRAM_T;
+  while (p >= T - ti) { p -= T - ti; ++ti; }
+  const int tj = ti + p;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_chunk;
+  const int64_t r_end = min(m, r_begin + rows_per_chunk);
+  double acc00 = 0, acc01 = 0, acc10 = 0, acc11 = 0;
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += GRAM_T) {
+    for (int e = tid; e < GRAM_T * GRAM_T; e += 256) {
+      const int rr = e / GRAM_T, cc = e % GRAM_T;
+      const int64_t r = r0 + rr;
+      const int ca = ti * GRAM_T + cc, cb = tj * GRAM_T + cc;
+      As[rr][cc] = (r < r_end && ca < l) ? (double)Y[r * ldy + ca] : 0.0;
+      Bs[rr][cc] = (r < r_end && cb < l) ? (double)Y[r * ldy + cb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < GRAM_T; ++rr) {
+      const double a0 = As[rr][ty], a1 = As[rr][ty + 16], b0 = Bs[rr][tx], b1 = Bs[rr][tx + 16];
+      acc00 = fma(a0, b0, acc00);
+      acc01 = fma(a0, b1, acc01);
+      acc10 = fma(a1, b0, acc10);
+      acc11 = fma(a1, b1, acc11);
+    }
+    __syncthreads();
+  }
+  double *o = part + (int64_t)blockIdx.y * l * l;
+  const int i0 = ti * GRAM_T + ty, i1 = i0 + 16, j0 = tj * GRAM_T + tx, j1 = j0 + 16;
+  if (i0 < l && j0 < l) o[i0 * l + j0] = acc00;
+  if (i0 < l && j1 < l) o[i0 * l + j1] = acc01;
+  if (i1 < l && j0 < l) o[i1 * l + j0] = acc10;
+  if (i1 < l && j1 < l) o[i1 * l + j1] = acc11;
+}
+
+__global__ void gram_reduce_kernel(const double *__restrict__ part, int chunks, int l, double *__restrict__ G) {
+  const int total = l * l;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int i = e / l, j = e % l;
+    if (i / GRAM_T > j / GRAM_T) continue;      // lower tiles are mirrored below
+    double s = 0;
+    for (int c = 0; c < chunks; ++c) s += part[(int64_t)c * total + e];
+    G[i * l + j] = s;
+    if (i / GRAM_T < j / GRAM_T) G[j * l + i] = s;
+  }
+}
+
+// ------------------------------------------------------------------------ FP64 Cholesky (one block)
+// G (l x l, symmetric) is overwritten by the upper factor R with G = R^T R; the strict lower triangle is
+// zeroed.  A non-positive or non-finite pivot reports RMC_ENUMERIC and sets *fail.
+__global__ void __launch_bounds__(1024) cholesky_kernel(double *G, int l, int *status, int *fail) {
+  __shared__ double piv;
+  __shared__ int bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < l; ++j) {
+    if (tid == 0) {
+      const double d = G[j * l + j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+      } else {
+        piv = sqrt(d);
+        G[j * l + j] = piv;
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double r = piv;
+    for (int i = j + 1 + tid; i < l; i += blockDim.x) G[j * l + i] /= r;
+    __syncthreads();
+    for (int i = j + 1 + warp; i < l; i += nwarps) {
+      const double gi = G[j * l + i];
+      for (int k = i + lane; k < l; k += 32) G[i * l + k] = fma(-gi, G[j * l + k], G[i * l + k]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < l * l; e += blockDim.x)
+    if (e / l > e % l) G[e] = 0.0;
+  if (tid == 0) {
+    if (bad) rmc_report(status, RMC_ENUMERIC);
+    if (fail) *fail = bad;
+  }
+}
+
+// Rinv = R^-1 (upper triangular), one thread per column, FP64; also an FP32 copy for the apply.
+__global__ void tri_inverse_kernel(const double *R, int l, double *Rinv, float *Rinv32) {
+  for (int j = threadIdx.x; j < l; j += blockDim.x) {
+    for (int i = j + 1; i < l; ++i) Rinv[i * l + j] = 0.0;
+    Rinv[j * l + j] = 1.0 / R[j * l + j];
+    for (int i = j - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int k = i + 1; k <= j; ++k) s = fma(R[i * l + k], Rinv[k * l + j], s);
+      Rinv[i * l + j] = -s / R[i * l + i];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) Rinv32[e] = (float)Rinv[e];
+}
+
+// C = A B for upper-triangular l x l FP64 matrices (the R of CholeskyQR2 is R2 R1).
+__global__ void tri_mul_kernel(const double *A, const double *B, int l, double *C) {
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e / l, j = e % l;
+    double s = 0.0;
+    for (int k = i; k <= j; ++k) s = fma(A[i * l + k], B[k * l + j], s);
+    C[e] = (i <= j) ? s : 0.0;
+  }
+}
+
+// ------------------------------------------------------------- row block times a small matrix (in place)
+// out[r, 0:lo] = in[r, 0:li] M (M li x lo, row stride ldm, FP32), 32 rows per block.  in and out may alias:
+// every block reads its rows into shared memory before writing them.
+constexpr int RB = 32;
+
+__global__ void __launch_bounds__(256) rowblock_mul_kernel(const float *in, int64_t m, int li, int64_t ldi,
+                                                           const float *__restrict__ M, int lo, int64_t ldm,
+                                                           float *out, int64_t ldo) {
+  extern __shared__ float Ys[];  // RB x li
+  const int64_t r0 = (int64_t)blockIdx.x * RB;
+  for (int e = threadIdx.x; e < RB * li; e += blockDim.x) {
+    const int rr = e / li, c = e % li;
+    Ys[e] = (r0 + rr < m) ? in[(r0 + rr) * ldi + c] : 0.f;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;  // warp w: rows 4w .. 4w+3
+  for (int c0 = 0; c0 < lo; c0 += 32 * 4) {
+    float acc[4][4] = {};
+    for (int k = 0; k < li; ++k) {
+      float mv[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int c = c0 + lane + 32 * t;
+        mv[t] = (c < lo) ? M[(int64_t)k * ldm + c] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float y = Ys[(4 * warp + i) * li + k];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) acc[i][t] = fmaf(y, mv[t], acc[i][t]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t r = r0 + 4 * warp + i;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int c = c0 + lane + 32 * t;
+        if (r < m && c < lo) out[r * ldo + c] = acc[i][t];
+      }
+    }
+  }
+}
+
+__global__ void transpose_kernel(const float *__restrict__ in, int64_t rows, int64_t cols, int64_t ldi,
+                                 float *__restrict__ out, int64_t ldo) {
+  __shared__ float tile[32][33];
+  const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = by + k, c = bx + threadIdx.x;
+    if (r < rows && c < cols) tile[k][threadIdx.x] = in[r * ldi + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t c = bx + k, r = by + threadIdx.x;
+    if (r < rows && c < cols) out[c * ldo + r] = tile[threadIdx.x][k];
+  }
+}
+
+// ------------------------------------------------------------------- one-sided Jacobi SVD (one block)
+// W (l x l, column-major in global memory) is rotated until its columns are mutually orthogonal; V accumulates
+// the rotations.  Round-robin ordering: in each of the l'-1 rounds (l' = l rounded up to even) the l'/2
+// disjoint column pairs are rotated in parallel, one warp per pair.  Rotation as in the textbook one-sided
+// (Hestenes) method: zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)).
+template <typename T>
+__global__ void __launch_bounds__(1024) jacobi_kernel(T *W, T *V, int l, T tol, int max_sweeps, int *status) {
+  __shared__ int rotated;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) V[e] = (e / l == e % l) ? T(1) : T(0);
+  const int lp = (l + 1) & ~1;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int round = 0; round < lp - 1; ++round) {
+      for (int pr = warp; pr < lp / 2; pr += nwarps) {
+        // round-robin pairing: position 0 fixed, positions 1..lp-1 rotate
+        const int a = pr, b = lp - 1 - pr;
+        auto pos = [&](int x) { return x == 0 ? 0 : 1 + (x - 1 + round) % (lp - 1); };
+        int p = pos(a), q = pos(b);
+        if (p > q) { const int t = p; p = q; q = t; }
+        if (q >= l) continue;  // the padding column of an odd l
+        T *wp = W + (int64_t)p * l, *wq = W + (int64_t)q * l;
+        T alpha = 0, beta = 0, gamma = 0;
+        for (int r = lane; r < l; r += 32) {
+          const T x = wp[r], y = wq[r];
+          alpha += x * x;
+          beta += y * y;
+          gamma += x * y;
+        }
+        for (int o = 16; o; o >>= 1) {
+          alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+          beta += __shfl_xor_sync(0xffffffffu, beta, o);
+          gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
+        }
+        if (gamma == T(0) || fabs(gamma) <= tol * sqrt(alpha * beta)) continue;
+        const T zeta = (beta - alpha) / (T(2) * gamma);
+        const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+        const T c = T(1) / sqrt(T(1) + t * t), s = c * t;
+        for (int r = lane; r < l; r += 32) {
+          const T x = wp[r], y = wq[r];
+          wp[r] = c * x - s * y;
+          wq[r] = s * x + c * y;
+        }
+        T *vp = V + (int64_t)p * l, *vq = V + (int64_t)q * l;
+        for (int r = lane; r < l; r += 32) {
+          const T x = vp[r], y = vq[r];
+          vp[r] = c * x - s * y;
+          vq[r] = s * x + c * y;
+        }
+        if (lane == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  if (sweep == max_sweeps && threadIdx.x == 0) rmc_report(status, RMC_ENUMERIC);
+}
+
+// After Jacobi on the triangular factor R of B^T (B^T = Q2 R, R = W V^T column-wise, sigma_j = ||w_j||):
+//   Ub[:, rank(j)] = V[:, j]           (left singular vectors of B, l x l, row-major)
+//   M[:, rank(j)]  = w_j / sigma_j     (so that Vb = Q2 M)
+//   sigma[rank(j)] = sigma_j, descending (ties by index).
+template <typename T>
+__global__ void jacobi_finish_kernel(const T *W, const T *V, int l, float *Ub, float *M, float *sigma) {
+  extern __shared__ double sg[];
+  for (int j = threadIdx.x; j < l; j += blockDim.x) {
+    double s = 0;
+    for (int r = 0; r < l; ++r) s += (double)W[(int64_t)j * l + r] * (double)W[(int64_t)j * l + r];
+    sg[j] = sqrt(s);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < l; j += blockDim.x) {
+    int rank = 0;
+    for (int u = 0; u < l; ++u) rank += (sg[u] > sg[j]) || (sg[u] == sg[j] && u < j);
+    sigma[rank] = (float)sg[j];
+    const double inv = sg[j] > 0 ? 1.0 / sg[j] : 0.0;
+    for (int r = 0; r < l; ++r) {
+      Ub[r * l + rank] = (float)V[(int64_t)j * l + r];
+      M[r * l + rank] = (float)(W[(int64_t)j * l + r] * inv);
+    }
+  }
+}
+
+// R (row-major FP64, upper) -> column-major working copy of type T.
+template <typename T>
+__global__ void to_colmajor_kernel(const double *R, int l, T *W) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < l * l; e += gridDim.x * blockDim.x) {
+    const int i = e / l, j = e % l;
+    W[(int64_t)j * l + i] = (T)R[e];
+  }
+}
+
+// ---------------------------------------------------------------- rsvd tail: signs, U = Q Ub[:, :k], V
+// For column i < k: the entry of largest magnitude of Vb[:, i] (first one on ties) is made positive.
+__global__ void sign_fix_kernel(const float *Vb, int64_t n, int64_t ldvb, const float *Ub, int l, int k,
+                                float *Msigned, float *V, int64_t ldv, const float *sg, float *sigma) {
+  __shared__ float best[1024];
+  __shared__ int64_t where[1024];
+  const int i = blockIdx.x;
+  float b = -1.f;
+  int64_t w = 0;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+    const float v = fabsf(Vb[r * ldvb + i]);
+    if (v > b) { b = v; w = r; }
+  }
+  best[threadIdx.x] = b;
+  where[threadIdx.x] = w;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (threadIdx.x < o) {
+      const float b2 = best[threadIdx.x + o];
+      const int64_t w2 = where[threadIdx.x + o];
+      if (b2 > best[threadIdx.x] || (b2 == best[threadIdx.x] && w2 < where[threadIdx.x])) {
+        best[threadIdx.x] = b2;
+        where[threadIdx.x] = w2;
+      }
+    }
+    __syncthreads();
+  }
+  const float sgn = Vb[where[0] * ldvb + i] < 0.f ? -1.f : 1.f;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) V[r * ldv + i] = sgn * Vb[r * ldvb + i];
+  for (int r = threadIdx.x; r < l; r += blockDim.x) Msigned[r * k + i] = sgn * Ub[r * l + i];
+  if (threadIdx.x == 0) sigma[i] = sg[i];
+}
+
+// ------------------------------------------------------------------------ least-squares back substitution
+// x = R11^-1 r12 where R ((n+1) x (n+1), upper) is the Cholesky factor of the augmented Gram matrix.
+__global__ void lsr_backsub_kernel(const double *R, int n, double *x, const int *fail) {
+  extern __shared__ double y[];
+  const int lda = n + 1;
+  if (fail && *fail) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = nan("");
+    return;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = R[i * lda + n];
+  __syncthreads();
+  for (int i = n - 1; i >= 0; --i) {
+    const double xi = y[i] / R[i * lda + i];
+    __syncthreads();
+    for (int k = threadIdx.x; k < i; k += blockDim.x) y[k] = fma(-R[k * lda + i], xi, y[k]);
+    if (threadIdx.x == 0) x[i] = xi;
+    __syncthreads();
+  }
+}
+
+__global__ void copy_column_kernel(const float *v, int64_t s, float *W, int64_t ldw, int64_t col) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s; i += (int64_t)gridDim.x * blockDim.x)
+    W[i * ldw + col] = v[i];
+}
+
+// ----------------------------------------------------------------------------------------- host helpers
+
+int gram_chunks(int64_t m, int l, int num_sms) {
+  const int T = (l + GRAM_T - 1) / GRAM_T;
+  const int pairs = T * (T + 1) / 2;
+  int64_t chunks = (2 * (int64_t)num_sms + pairs - 1) / pairs;
+  const int64_t max_chunks = (m + 255) / 256;
+  if (chunks > max_chunks) chunks = max_chunks;
+  if (chunks < 1) chunks = 1;
+  return (int)chunks;
+}
+
+size_t gram_ws(int64_t m, int l, int num_sms) {
+  return sizeof(double) * (size_t)gram_chunks(m, l, num_sms) * l * l;
+}
+
+// G (l x l FP64) = Y^T Y.
+int launch_gram(rmc_ctx *ctx, const float *Y, int64_t m, int l, int64_t ldy, double *G, double *part) {
+  const int T = (l + GRAM_T - 1) / GRAM_T;
+  const int pairs = T * (T + 1) / 2;
+  const int chunks = gram_chunks(m, l, ctx->num_sms);
+  int64_t rows = (m + chunks - 1) / chunks;
+  rows = (rows + GRAM_T - 1) / GRAM_T * GRAM_T;
+  {
+    RmcProf prof(ctx, RMC_K_GRAM);
+    gram_f64_kernel<<<dim3(pairs, chunks), 256, 0, ctx->stream>>>(Y, m, l, ldy, rows, part);
+  }
+  rmc_note_launch(2);
+  gram_reduce_kernel<<<rmc_blocks((int64_t)l * l, 256, 1024), 256, 0, ctx->stream>>>(part, chunks, l, G);
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
+int launch_rowblock(cudaStream_t st, const float *in, int64_t m, int li, int64_t ldi, const float *M, int lo,
+                    int64_t ldm, float *out, int64_t ldo) {
+  const size_t smem = sizeof(float) * RB * li;
+  if (smem > 48 * 1024)
+    RMC_TRY_CUDA(cudaFuncSetAttribute(rowblock_mul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  rowblock_mul_kernel<<<rmc_blocks(m, RB), 256, smem, st>>>(in, m, li, ldi, M, lo, ldm, out, ldo);
+  rmc_note_launch();
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------- matmuls
+
+static int matmul_at_splits(int64_t m, int64_t n, int64_t l, int num_sms) {
+  const int64_t tiles = ((l + GT - 1) / GT) * ((n + GT - 1) / GT);
+  int64_t splits = (2 * (int64_t)num_sms + tiles - 1) / tiles;
+  const int64_t max_splits = (m + 1023) / 1024;
+  if (splits > max_splits) splits = max_splits;
+  if (splits < 1) splits = 1;
+  return (int)splits;
+}
+
+int rmc_tc_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
+                     int64_t ldx, float *Y, int64_t ldy, void *ws);
+int rmc_tc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
+                     int64_t ldx, float *W, int64_t ldw, void *ws);
+size_t rmc_tc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, int num_sms);
+
+size_t rmc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, int prec, int num_sms) {
+  if (prec == RMC_TF32) return rmc_tc_matmul_ws(m, n, l, which, num_sms);
+  if (which == 0) return 0;
+  const int splits = matmul_at_splits(m, n, l, num_sms);
+  return splits > 1 ? sizeof(float) * (size_t)splits * l * n : 0;
+}
+
+int rmc_launch_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
+                         int64_t ldx, int prec, float *Y, int64_t ldy, void *ws) {
+  if (prec == RMC_TF32) return rmc_tc_matmul_an(ctx, A, m, n, lda, X, l, ldx, Y, ldy, ws);
+  dim3 grid((unsigned)((l + GT - 1) / GT), (unsigned)((m + GT - 1) / GT));
+  {
+    RmcProf prof(ctx, RMC_K_MATMUL_AN);
+    matmul_an_kernel<<<grid, 256, 0, ctx->stream>>>(A, m, n, lda, X, l, ldx, Y, ldy);
+  }
+  rmc_note_launch();
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
+int rmc_launch_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
+                         int64_t ldx, int prec, float *W, int64_t ldw, void *ws) {
+  if (prec == RMC_TF32) return rmc_tc_matmul_at(ctx, A, m, n, lda, X, l, ldx, W, ldw, ws);
+  const int splits = matmul_at_splits(m, n, l, ctx->num_sms);
+  int64_t rows = (m + splits - 1) / splits;
+  rows = (rows + GK - 1) / GK * GK;
+  dim3 grid((unsigned)((n + GT - 1) / GT), (unsigned)((l + GT - 1) / GT), (unsigned)splits);
+  if (splits == 1) {
+    RmcProf prof(ctx, RMC_K_MATMUL_AT);
+    matmul_at_kernel<<<grid, 256, 0, ctx->stream>>>(A, m, n, lda, X, l, ldx, rows, W, ldw, 0);
+    rmc_note_launch();
+  } else {
+    float *part = static_cast<float *>(ws);
+    {
+      RmcProf prof(ctx, RMC_K_MATMUL_AT);
+      matmul_at_kernel<<<grid, 256, 0, ctx->stream>>>(A, m, n, lda, X, l, ldx, rows, part, n, l * n);
+    }
+    rmc_note_launch(2);
+    sum_splits_kernel<<<rmc_blocks(l * n, 256, 4096), 256, 0, ctx->stream>>>(part, splits, l, n, W, ldw);
+  }
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
+int rmc_launch_transpose(cudaStream_t st, const float *in, int64_t rows, int64_t cols, int64_t ldi, float *out,
+                         int64_t ldo) {
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(in, rows, cols, ldi, out, ldo);
+  rmc_note_launch();
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
+// ------------------------------------------------------------------------------------------ CholeskyQR2
+
+size_t rmc_cholqr2_ws(int64_t m, int64_t l, int num_sms) {
+  WsCarve w;
+  w.take<double>(l * l);        // G
+  w.take<double>(l * l);        // Rinv
+  w.take<float>(l * l);         // Rinv32
+  w.take<double>(l * l);        // R1
+  w.take<int>(4);
+  w.take<char>(gram_ws(m, (int)l, num_sms));
+  return w.off;
+}
+
+int rmc_launch_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l_, int64_t ldy, double *R, void *ws) {
+  const int l = (int)l_;
+  cudaStream_t st = ctx->stream;
+  WsCarve w;
+  w.base = static_cast<char *>(ws);
+  double *G = w.take<double>(l * l);
+  double *Rinv = w.take<double>(l * l);
+  float *Rinv32 = w.take<float>(l * l);
+  double *R1 = w.take<double>(l * l);
+  int *fail = w.take<int>(4);
+  double *part = reinterpret_cast<double *>(w.take<char>(gram_ws(m, l, ctx->num_sms)));
+  for (int pass = 0; pass < 2; ++pass) {
+    RMC_TRY(launch_gram(ctx, Y, m, l, ldy, G, part));
+    {
+      RmcProf prof(ctx, RMC_K_SMALL);
+      cholesky_kernel<<<1, 1024, 0, st>>>(G, l, ctx->d_status, fail);
+      tri_inverse_kernel<<<1, 256, 0, st>>>(G, l, Rinv, Rinv32);
+    }
+    rmc_note_launch(2);
+    RMC_LAUNCH_CHECK();
+    RMC_TRY(launch_rowblock(st, Y, m, l, ldy, Rinv32, l, l, Y, ldy));
+    if (R) {
+      if (pass == 0) RMC_TRY_CUDA(cudaMemcpyAsync(R1, G, sizeof(double) * l * l, cudaMemcpyDeviceToDevice, st));
+      else {
+        tri_mul_kernel<<<1, 1024, 0, st>>>(G, R1, l, R);
+        rmc_note_launch();
+      }
+    }
+  }
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
+// ------------------------------------------------------------------------------------------- small SVD
+
+static bool jacobi_in_fp64(int l) { return l <= 32; }
+
+size_t rmc_svd_wide_ws(int64_t l, int64_t n, int num_sms) {
+  WsCarve w;
+  w.take<float>(n * l);        // Bt -> Q2
+  w.take<double>(l * l);       // R
+  w.take<double>(l * l);       // W
+  w.take<double>(l * l);       // V
+  w.take<float>(l * l);        // M
+  const size_t head = w.off;
+  return head + 256 + rmc_cholqr2_ws(n, l, num_sms);
+}
+
+int rmc_launch_svd_wide(rmc_ctx *ctx, const float *B, int64_t l_, int64_t n, int64_t ldb, float *Ub, float *sigma,
+                        float *Vb, int64_t ldv, void *ws) {
+  const int l = (int)l_;
+  cudaStream_t st = ctx->stream;
+  WsCarve w;
+  w.base = static_cast<char *>(ws);
+  float *Bt = w.take<float>(n * l);
+  double *R = w.take<double>(l * l);
+  double *W = w.take<double>(l * l);
+  double *V = w.take<double>(l * l);
+  float *M = w.take<float>(l * l);
+  void *rest = static_cast<char *>(ws) + ((w.off + 255) & ~size_t(255));
+  RMC_TRY(rmc_launch_transpose(st, B, l, n, ldb, Bt, l));                    // B^T, n x l
+  RMC_TRY(rmc_launch_cholqr2(ctx, Bt, n, l, l, R, rest));                    // B^T = Q2 R
+  RmcProf prof(ctx, RMC_K_SMALL);
+  rmc_note_launch(3);
+  if (jacobi_in_fp64(l)) {
+    to_colmajor_kernel<double><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, W);
+    jacobi_kernel<double><<<1, 1024, 0, st>>>(W, V, l, 8 * 2.220446049250313e-16 * sqrt((double)l), 60,
+                                               ctx->d_status);
+    jacobi_finish_kernel<double><<<1, 256, sizeof(double) * l, st>>>(W, V, l, Ub, M, sigma);
+  } else {
+    float *Wf = reinterpret_cast<float *>(W), *Vf = reinterpret_cast<float *>(V);
+    to_colmajor_kernel<float><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, Wf);
+    jacobi_kernel<float><<<1, 1024, 0, st>>>(Wf, Vf, l, 4 * 1.1920929e-7f * sqrtf((float)l), 60, ctx->d_status);
+    jacobi_finish_kernel<float><<<1, 256, sizeof(double) * l, st>>>(Wf, Vf, l, Ub, M, sigma);
+  }
+  RMC_LAUNCH_CHECK();
+  return launch_rowblock(st, Bt, n, l, l, M, l, l, Vb, ldv);                 // Vb = Q2 M
+}
+
+int rmc_launch_rsvd_finish(rmc_ctx *ctx, const float *Q, int64_t m, int64_t l, const float *Ub, const float *sg,
+                           const float *Vb, int64_t n, int k, float *U, int64_t ldu, float *sigma, float *V,
+                           int64_t ldv, void *ws) {
+  float *Ms = static_cast<float *>(ws);  // Ub[:, :k] with the column signs applied, l x k
+  sign_fix_kernel<<<k, 1024, 0, ctx->stream>>>(Vb, n, l, Ub, (int)l, k, Ms, V, ldv, sg, sigma);
+  rmc_note_launch();
+  RMC_LAUNCH_CHECK();
+  return launch_rowblock(ctx->stream, Q, m, (int)l, l, Ms, k, k, U, ldu);
+}
+
+// ------------------------------------------------------------------------------------ least-squares solve
+
+size_t rmc_lsr_solve_ws(int64_t s, int64_t n, int num_sms) {
+  WsCarve w;
+  w.take<double>((n + 1) * (n + 1));
+  w.take<int>(4);
+  w.take<char>(gram_ws(s, (int)n + 1, num_sms));
+  return w.off;
+}
+
+int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n, int64_t ldsa, const float *Sb,
+                         double *x, void *ws) {
+  // SA is s x (n+1) with ldsa >= n+1; column n receives Sb first.
+  cudaStream_t st = ctx->stream;
+  const int l = (int)n + 1;
+  WsCarve w;
+  w.base = static_cast<char *>(ws);
+  double *G = w.take<double>((size_t)l * l);
+  int *fail = w.take<int>(4);
+  double *part = reinterpret_cast<double *>(w.take<char>(gram_ws(s, l, ctx->num_sms)));
+  copy_column_kernel<<<rmc_blocks(s, 256, 1024), 256, 0, st>>>(Sb, s, const_cast<float *>(SA), ldsa, n);
+  RMC_TRY(launch_gram(ctx, SA, s, l, ldsa, G, part));
+  {
+    RmcProf prof(ctx, RMC_K_SMALL);
+    cholesky_kernel<<<1, 1024, 0, st>>>(G, l, ctx->d_status, fail);
+    lsr_backsub_kernel<<<1, 1024, sizeof(double) * n, st>>>(G, (int)n, x, fail);
+  }
+  rmc_note_launch(3);
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}

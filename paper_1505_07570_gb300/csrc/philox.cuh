@@ -1,0 +1,72 @@
+// Philox4x32-10 on the device (Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy as 1, 2,
+// 3", SC'11) and the draws the sketches take from it.  The stream layout is the one stated in rmc.h.
+#pragma once
+#include <stdint.h>
+
+namespace rmc {
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;  // round multipliers of the published generator
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;  // Weyl key increments
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+enum : uint32_t { kStreamGaussian = 0, kStreamSrhtSign = 1, kStreamCountSketch = 2, kStreamSrhtKey = 3 };
+
+// Ten rounds of the Philox S-P network on one 128-bit counter block.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 philox_block(uint64_t seed, uint32_t stream, uint32_t instance, uint64_t index) {
+  return philox10(make_uint4((uint32_t)index, (uint32_t)(index >> 32), stream, instance), (uint32_t)seed,
+                  (uint32_t)(seed >> 32));
+}
+
+// ((w >> 9) + 1/2) * 2^-23: exact in FP32, strictly inside (0, 1).
+__device__ __forceinline__ float unit_f32(uint32_t w) {
+  return __fmaf_rn((float)(w >> 9), 1.1920928955078125e-7f, 5.9604644775390625e-8f);
+}
+
+// Box-Muller pair from two words: r = sqrt(-2 ln u_a), (r cos 2 pi u_b, r sin 2 pi u_b).
+__device__ __forceinline__ float2 box_muller(uint32_t wa, uint32_t wb) {
+  const float r = sqrtf(-2.0f * logf(unit_f32(wa)));
+  float sn, cs;
+  sincospif(2.0f * unit_f32(wb), &sn, &cs);  // 2 u_b is exact, so the angle carries no extra rounding
+  return make_float2(r * cs, r * sn);
+}
+
+// The four normals of Gaussian block `index` (columns 4t .. 4t+3 of one row).
+__device__ __forceinline__ float4 gaussian4(uint64_t seed, uint32_t instance, uint64_t index) {
+  const uint4 w = philox_block(seed, kStreamGaussian, instance, index);
+  const float2 a = box_muller(w.x, w.y);
+  const float2 b = box_muller(w.z, w.w);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
+__device__ __forceinline__ float srht_sign(uint64_t seed, uint32_t instance, uint64_t row) {
+  const uint4 w = philox_block(seed, kStreamSrhtSign, instance, row);
+  return (w.x >> 31) ? -1.0f : 1.0f;
+}
+
+// Count-sketch hash: bucket in [0, s) (high half of word0 * s), sign from bit 31 of word 1.
+__device__ __forceinline__ void cs_hash(uint64_t seed, uint32_t instance, uint64_t row, uint32_t s,
+                                        uint32_t *bucket, float *sign) {
+  const uint4 w = philox_block(seed, kStreamCountSketch, instance, row);
+  *bucket = __umulhi(w.x, s);
+  *sign = (w.y >> 31) ? -1.0f : 1.0f;
+}
+
+__device__ __forceinline__ uint64_t srht_key(uint64_t seed, uint32_t instance, uint64_t j) {
+  const uint4 w = philox_block(seed, kStreamSrhtKey, instance, j);
+  return ((uint64_t)w.x << 32) | w.y;
+}
+
+}  // namespace rmc

@@ -1,0 +1,136 @@
+// Internal declarations shared by the library's translation units: the context, workspace carving, the
+// device status word, and the launchers each .cu file provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/rmc.h"
+
+struct RmcProfRec {
+  int tag;
+  cudaEvent_t start, stop;
+};
+
+struct rmc_ctx {
+  cudaStream_t stream;
+  size_t budget;        // cap on workspace bytes
+  void *ws;             // device workspace (stream-ordered allocation)
+  size_t ws_bytes;
+  int *d_status;        // device status word: 0 or the first RMC_E* a kernel reported
+  int *h_status;        // pinned host copy
+  int device;
+  int num_sms;
+  // measurement hooks
+  bool prof;
+  int prof_used, prof_cap;
+  RmcProfRec *prof_recs;
+  int64_t prof_launches[RMC_K_NTAGS];
+  double prof_ms[RMC_K_NTAGS];
+};
+
+// Count kernel launches (process-wide).
+void rmc_note_launch(int count = 1);
+
+// Bracket one launch with CUDA events when the context is profiling.
+struct RmcProf {
+  rmc_ctx *ctx;
+  int rec;
+  RmcProf(rmc_ctx *c, int tag);
+  ~RmcProf();
+};
+
+#define RMC_TRY_CUDA(expr)                                   \
+  do {                                                       \
+    cudaError_t e_ = (expr);                                 \
+    if (e_ != cudaSuccess) { (void)cudaGetLastError(); return RMC_ECUDA; } \
+  } while (0)
+
+#define RMC_TRY(expr)                                        \
+  do { int r_ = (expr); if (r_ != RMC_OK) return r_; } while (0)
+
+#define RMC_LAUNCH_CHECK() RMC_TRY_CUDA(cudaGetLastError())
+
+// Make sure the context holds at least `bytes` of workspace (grows stream-ordered, never shrinks).
+int rmc_ws_reserve(rmc_ctx *ctx, size_t bytes);
+
+// Bump allocator over the workspace: carve once without a base to learn the total, reserve, then carve again
+// with the real base in the same order.
+struct WsCarve {
+  size_t off = 0;
+  char *base = nullptr;
+  template <typename T> T *take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// Device-side error report: the first error wins.
+__device__ __forceinline__ void rmc_report(int *status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+static inline unsigned rmc_blocks(int64_t work, int per_block, int64_t cap = 1 << 30) {
+  int64_t b = (work + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+// ---------------------------------------------------------------------------------------- launchers
+// rng.cu
+int rmc_launch_philox(cudaStream_t st, uint64_t seed, uint32_t stream_id, uint32_t instance, uint64_t first,
+                      int64_t count, uint32_t *out);
+int rmc_launch_gaussian(cudaStream_t st, uint64_t seed, uint32_t instance, int64_t rows, int64_t cols,
+                        float *out, int64_t ld, float scale);
+int rmc_launch_gaussian_t(cudaStream_t st, uint64_t seed, uint32_t instance, int64_t rows, int64_t cols,
+                          float *out_t, int64_t ld_t, float scale);
+int rmc_launch_cs_hash(cudaStream_t st, uint64_t seed, uint32_t instance, int64_t m, int64_t s,
+                       int32_t *bucket, float *sign);
+size_t rmc_srht_sample_ws(int64_t N);
+int rmc_launch_srht_sample(rmc_ctx *ctx, uint64_t seed, uint32_t instance, int64_t N, int64_t s, int64_t *idx,
+                           void *ws);
+
+// countsketch.cu
+size_t rmc_countsketch_ws(int64_t m, int64_t s);
+int rmc_launch_countsketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b,
+                           int64_t s, uint64_t seed, uint32_t instance, float *C, int64_t ldc, float *Cb,
+                           void *ws);
+
+// srht.cu
+size_t rmc_srht_ws(int64_t m, int64_t n_total, int64_t s);
+int rmc_launch_srht(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b,
+                    int64_t s, uint64_t seed, uint32_t instance, float *C, int64_t ldc, float *Cb, void *ws);
+
+// gaussian.cu
+size_t rmc_gauss_ws(int64_t m, int64_t n_total, int64_t s, int prec, int num_sms);
+int rmc_launch_gauss_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b,
+                            int64_t s, uint64_t seed, uint32_t instance, int prec, float *C, int64_t ldc,
+                            float *Cb, void *ws);
+
+// dense.cu
+size_t rmc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, int prec, int num_sms);
+int rmc_launch_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X,
+                         int64_t l, int64_t ldx, int prec, float *Y, int64_t ldy, void *ws);
+int rmc_launch_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X,
+                         int64_t l, int64_t ldx, int prec, float *W, int64_t ldw, void *ws);
+size_t rmc_cholqr2_ws(int64_t m, int64_t l, int num_sms);
+int rmc_launch_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l, int64_t ldy, double *R, void *ws);
+size_t rmc_svd_wide_ws(int64_t l, int64_t n, int num_sms);
+int rmc_launch_svd_wide(rmc_ctx *ctx, const float *B, int64_t l, int64_t n, int64_t ldb, float *Ub,
+                        float *sigma, float *Vb, int64_t ldv, void *ws);
+size_t rmc_lsr_solve_ws(int64_t s, int64_t n, int num_sms);
+int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n, int64_t ldsa, const float *Sb,
+                         double *x, void *ws);
+
+int rmc_launch_transpose(cudaStream_t st, const float *in, int64_t rows, int64_t cols, int64_t ldi, float *out,
+                         int64_t ldo);
+int rmc_launch_rsvd_finish(rmc_ctx *ctx, const float *Q, int64_t m, int64_t l, const float *Ub, const float *sg,
+                           const float *Vb, int64_t n, int k, float *U, int64_t ldu, float *sigma, float *V,
+                           int64_t ldv, void *ws);
+
+// tc_gemm.cu (tcgen05 tensor-core kernels)
+int rmc_tc_available(void);

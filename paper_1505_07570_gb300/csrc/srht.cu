@@ -1,0 +1,305 @@
+// SRHT (Sec. 3.2.2, row orientation): C = (1/sqrt(s)) P^T H_N D A_pad.
+//
+// The N-point Walsh-Hadamard transform factors over the bits of the row index: with i = (i1, i2), r = (r1, r2)
+// and N = N1 * N2, (H_N)[r, i] = (H_N1)[r1, i1] (H_N2)[r2, i2].  So
+//     C[r] = (1/sqrt(s)) sum_{i1} (H_N1)[r1, i1] T[i1, r2],   T[i1, r2] = sum_{i2} (H_N2)[r2, i2] g_i A[i],
+// and only the r2 that occur among the s sampled rows are needed.
+//
+// Stage 1 (one thread-block cluster per block of N2 = 4096 * C consecutive rows and per 4-column slab):
+//   each CTA loads 4096 rows x 4 columns straight into registers with the sign flip applied, transforms its
+//   12 low index bits in three register phases of four bits separated by two shared-memory transposes, and
+//   the cluster then combines the C CTAs (the top index bits of i2) for the needed r2 only, reading the
+//   peers' shared memory over DSMEM.  The result T[i1, slot(r2), slab] goes to a small buffer.
+// Stage 2: C[r] = (1/sqrt(s)) sum over the N1 blocks of +-T[i1, slot(r2)], one thread per (row, 4 columns).
+// A is read once; the intermediate holds N1 * |R2| rows, a small fraction of A when N2 >> s.
+#include <cooperative_groups.h>
+
+#include "rmc_internal.cuh"
+#include "philox.cuh"
+
+namespace cg = cooperative_groups;
+using namespace rmc;
+
+namespace {
+
+constexpr int kRowsCta = 4096;   // rows transformed by one CTA (12 index bits)
+constexpr int kThreads = 256;    // 16 rows x 4 columns per thread
+constexpr int kMaxCluster = 8;
+
+// shared-memory slot of local row r: XOR the low 3 bits with bits 4..6 (conflict-free float4 phases)
+__device__ __forceinline__ int swz(int r) { return r ^ ((r >> 4) & 7); }
+
+__device__ __forceinline__ void bfly(float4 &a, float4 &b) {
+  const float4 x = a, y = b;
+  a = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+  b = make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
+}
+
+// 16-point transform over the register index (4 bits).
+__device__ __forceinline__ void fwht16(float4 (&v)[16]) {
+#pragma unroll
+  for (int h = 1; h < 16; h <<= 1)
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if ((j & h) == 0) bfly(v[j], v[j | h]);
+}
+
+__device__ __forceinline__ float4 load_slab(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda,
+                                            const float *__restrict__ b, int64_t row, int64_t c0, bool vec) {
+  float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (row >= m) return x;
+  const float *ar = A + row * lda;
+  if (vec && c0 + 3 < n) return __ldg(reinterpret_cast<const float4 *>(ar + c0));
+  float t[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t c = c0 + k;
+    t[k] = (c < n) ? __ldg(ar + c) : ((c == n && b) ? __ldg(b + row) : 0.f);
+  }
+  return make_float4(t[0], t[1], t[2], t[3]);
+}
+
+// D as packed bits: bit (i mod 32) of word i / 32 set means g_i = -1.
+__global__ void srht_signs_kernel(uint64_t seed, uint32_t instance, int64_t m, uint32_t *bits) {
+  const int64_t words = (m + 31) / 32;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~int64_t(31); base < words * 32;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + (threadIdx.x & 31);
+    const bool neg = i < m && srht_sign(seed, instance, (uint64_t)i) < 0.f;
+    const uint32_t word = __ballot_sync(0xffffffffu, neg);
+    if ((threadIdx.x & 31) == 0) bits[base / 32] = word;
+  }
+}
+
+// grid: x = slab * C + rank (cluster of C along x), y = i1.  T out: [N1][umax][slabs] float4, rows u < *U valid.
+__global__ void __launch_bounds__(kThreads) srht_stage1_kernel(const float *__restrict__ A, int64_t m, int64_t n,
+                                                                int64_t lda, const float *__restrict__ b,
+                                                                const uint32_t *__restrict__ sign_bits, int csize,
+                                                                const uint32_t *__restrict__ r2_list,
+                                                                const int *__restrict__ U_ptr, int64_t umax,
+                                                                int64_t slabs, float4 *__restrict__ T, bool vec) {
+  extern __shared__ float4 sm[];   // kRowsCta float4, swizzled
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int64_t slab = blockIdx.x / csize;
+  const int64_t i1 = blockIdx.y;
+  const int64_t N2 = (int64_t)kRowsCta * csize;
+  const int64_t row_base = i1 * N2 + (int64_t)rank * kRowsCta;
+  const int t = threadIdx.x;
+  const int64_t c0 = slab * 4;
+
+  // phase 1: rows t*16 + j, transform bits 0..3
+  float4 v[16];
+  const int64_t row16 = row_base + t * 16;
+  const uint32_t gw = row16 < m ? __ldg(sign_bits + row16 / 32) >> (row16 & 31) : 0u;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int64_t row = row16 + j;
+    float4 x = load_slab(A, m, n, lda, b, row, c0, vec);
+    if ((gw >> j) & 1u) x = make_float4(-x.x, -x.y, -x.z, -x.w);
+    v[j] = x;
+  }
+  fwht16(v);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) sm[swz(t * 16 + j)] = v[j];
+  __syncthreads();
+  // phase 2: bits 4..7 in registers; thread owns bits 0..3 and 8..11
+  {
+    const int lo = t & 15, hi = t >> 4;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = sm[swz(lo | (j << 4) | (hi << 8))];
+    fwht16(v);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) sm[swz(lo | (j << 4) | (hi << 8))] = v[j];
+  }
+  __syncthreads();
+  // phase 3: bits 8..11 in registers; thread owns bits 0..7
+  {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = sm[swz(t | (j << 8))];
+    fwht16(v);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) sm[swz(t | (j << 8))] = v[j];
+  }
+  // every CTA of the cluster has its 4096-point transform in shared memory
+  cluster.sync();
+  // combine over the cluster (index bits 12.. of i2) for the needed r2, split across the cluster's CTAs
+  float4 *Tout = T + i1 * umax * slabs;
+  const int U = *U_ptr;
+  for (int u = rank + csize * t; u < U; u += csize * kThreads) {
+    const uint32_t r2 = r2_list[u];
+    const int lo = (int)(r2 & (kRowsCta - 1));
+    const int hi = (int)(r2 >> 12);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c = 0; c < csize; ++c) {
+      const float4 *peer = cluster.map_shared_rank(sm, c);
+      const float4 x = peer[swz(lo)];
+      const float sg = (__popc(hi & c) & 1) ? -1.f : 1.f;
+      acc = make_float4(fmaf(sg, x.x, acc.x), fmaf(sg, x.y, acc.y), fmaf(sg, x.z, acc.z), fmaf(sg, x.w, acc.w));
+    }
+    Tout[(int64_t)u * slabs + slab] = acc;
+  }
+  // keep this CTA's shared memory alive until every peer has read it
+  cluster.sync();
+}
+
+// C[k, :] for sampled row r = idx[k]: (1/sqrt(s)) sum_{i1} (-1)^popc(r1 & i1) T[i1, slot(r2)].
+__global__ void srht_stage2_kernel(const float4 *__restrict__ T, int64_t N1, int64_t umax, int64_t slabs,
+                                   const int64_t *__restrict__ idx, int64_t s, const uint32_t *__restrict__ slot,
+                                   int64_t N2, float scale, int64_t n, float *__restrict__ C, int64_t ldc,
+                                   float *__restrict__ Cb) {
+  const int64_t total = s * slabs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e / slabs, sl = e - k * slabs;
+    const int64_t r = idx[k];
+    const int64_t r1 = r / N2;
+    const uint32_t u = slot[r % N2];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t i1 = 0; i1 < N1; ++i1) {
+      const float4 x = T[(i1 * umax + u) * slabs + sl];
+      const float sg = (__popcll(r1 & i1) & 1) ? -1.f : 1.f;
+      acc = make_float4(fmaf(sg, x.x, acc.x), fmaf(sg, x.y, acc.y), fmaf(sg, x.z, acc.z), fmaf(sg, x.w, acc.w));
+    }
+    const float out[4] = {acc.x * scale, acc.y * scale, acc.z * scale, acc.w * scale};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t c = sl * 4 + q;
+      if (c < n) C[k * ldc + c] = out[q];
+      else if (c == n && Cb) Cb[k] = out[q];
+    }
+  }
+}
+
+// Distinct low parts r2 = idx & (N2 - 1) of the sample: mark, then compact in one block (N2 <= 32768).
+__global__ void srht_mark_r2_kernel(const int64_t *idx, int64_t s, int64_t N2, uint32_t *mark) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < s; k += (int64_t)gridDim.x * blockDim.x)
+    mark[idx[k] & (N2 - 1)] = 1u;
+}
+
+__global__ void __launch_bounds__(1024) srht_compact_r2_kernel(const uint32_t *mark, int64_t N2, uint32_t *slot,
+                                                               uint32_t *list, int *U_out) {
+  __shared__ uint32_t part[1024];
+  const int per = (int)((N2 + 1023) / 1024);
+  const int lo = threadIdx.x * per;
+  uint32_t c = 0;
+  for (int k = 0; k < per; ++k)
+    if (lo + k < N2) c += mark[lo + k];
+  part[threadIdx.x] = c;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const uint32_t y = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += y;
+    __syncthreads();
+  }
+  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int k = 0; k < per; ++k) {
+    const int64_t r = lo + k;
+    if (r < N2 && mark[r]) {
+      slot[r] = run;
+      list[run] = (uint32_t)r;
+      ++run;
+    }
+  }
+  if (threadIdx.x == 1023) *U_out = (int)part[1023];
+}
+
+struct SrhtPlan {
+  int64_t N, N2, N1, slabs;
+  int csize;
+};
+
+SrhtPlan srht_plan(int64_t m, int64_t ntot) {
+  SrhtPlan p;
+  p.N = 1;
+  while (p.N < m) p.N <<= 1;
+  int64_t c = p.N / kRowsCta;
+  if (c < 1) c = 1;
+  if (c > kMaxCluster) c = kMaxCluster;
+  p.csize = (int)c;
+  p.N2 = (int64_t)kRowsCta * c;
+  p.N1 = p.N > p.N2 ? p.N / p.N2 : 1;
+  p.slabs = (ntot + 3) / 4;
+  return p;
+}
+
+struct SrhtBufs {
+  int64_t *idx;
+  uint32_t *sign_bits;
+  uint32_t *mark, *slot, *list;
+  int *U;
+  float4 *T;
+  void *sample_ws;
+};
+
+SrhtBufs srht_carve(WsCarve &w, const SrhtPlan &p, int64_t s) {
+  SrhtBufs b;
+  b.idx = w.take<int64_t>(s);
+  b.sign_bits = w.take<uint32_t>(p.N / 32 + 1);
+  b.mark = w.take<uint32_t>(p.N2);
+  b.slot = w.take<uint32_t>(p.N2);
+  b.list = w.take<uint32_t>(p.N2);
+  b.U = w.take<int>(4);
+  const int64_t umax = s < p.N2 ? s : p.N2;
+  b.T = w.take<float4>(p.N1 * umax * p.slabs);
+  b.sample_ws = w.take<char>(rmc_srht_sample_ws(p.N));
+  return b;
+}
+
+}  // namespace
+
+size_t rmc_srht_ws(int64_t m, int64_t ntot, int64_t s) {
+  WsCarve w;
+  srht_carve(w, srht_plan(m, ntot), s);
+  return w.off;
+}
+
+int rmc_launch_srht(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b, int64_t s,
+                    uint64_t seed, uint32_t instance, float *C, int64_t ldc, float *Cb, void *ws) {
+  cudaStream_t st = ctx->stream;
+  const int64_t ntot = n + (b ? 1 : 0);
+  const SrhtPlan p = srht_plan(m, ntot);
+  WsCarve w;
+  w.base = static_cast<char *>(ws);
+  const SrhtBufs bf = srht_carve(w, p, s);
+
+  RMC_TRY(rmc_launch_srht_sample(ctx, seed, instance, p.N, s, bf.idx, bf.sample_ws));
+  RMC_TRY_CUDA(cudaMemsetAsync(bf.mark, 0, sizeof(uint32_t) * p.N2, st));
+  srht_mark_r2_kernel<<<rmc_blocks(s, 256, 1024), 256, 0, st>>>(bf.idx, s, p.N2, bf.mark);
+  srht_compact_r2_kernel<<<1, 1024, 0, st>>>(bf.mark, p.N2, bf.slot, bf.list, bf.U);
+  srht_signs_kernel<<<rmc_blocks(m, 256, 4096), 256, 0, st>>>(seed, instance, m, bf.sign_bits);
+  rmc_note_launch(3);
+  RMC_LAUNCH_CHECK();
+  const int64_t umax = s < p.N2 ? s : p.N2;
+
+  const bool vec = (lda % 4 == 0) && (reinterpret_cast<uintptr_t>(A) % 16 == 0);
+  const size_t smem = sizeof(float4) * kRowsCta;
+  RMC_TRY_CUDA(cudaFuncSetAttribute(srht_stage1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(p.slabs * p.csize), (unsigned)p.N1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = p.csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  rmc_note_launch(2);
+  {
+    RmcProf prof(ctx, RMC_K_SRHT);
+    RMC_TRY_CUDA(cudaLaunchKernelEx(&cfg, srht_stage1_kernel, A, m, n, lda, b, (const uint32_t *)bf.sign_bits,
+                                    p.csize, (const uint32_t *)bf.list, (const int *)bf.U, umax, p.slabs, bf.T,
+                                    vec));
+  }
+  const float scale = 1.0f / sqrtf((float)s);
+  RmcProf prof(ctx, RMC_K_SRHT_REDUCE);
+  srht_stage2_kernel<<<rmc_blocks(s * p.slabs, 256, 65536), 256, 0, st>>>(bf.T, p.N1, umax, p.slabs, bf.idx, s,
+                                                                            bf.slot, p.N2, scale, n, C, ldc, Cb);
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}

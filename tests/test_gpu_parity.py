@@ -1,0 +1,204 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, step by step and end to end.
+
+Tolerances (from the stated targets): hashes, signs, sample indices and Philox words bit-exact; FP32 sketches
+within 1e-5 relative Frobenius error; rsvd top-k singular values within 1e-4 relative error and
+||A - U S V^T||_F within 1% of the oracle's.
+"""
+import numpy as np
+import pytest
+
+from oracle import linalg, lsr, philox, rsvd, sketch
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def R():
+    import paper_1505_07570_gb300 as rmc
+    return rmc
+
+
+def relfro(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+# ------------------------------------------------------------------------------------------------ a1 draws
+
+@pytest.mark.parametrize("stream,instance,first,count", [(0, 0, 0, 1000), (2, 7, 2**32 - 3, 17), (3, 1, 123456789, 4096)])
+def test_philox_words_bit_exact(R, stream, instance, first, count):
+    seed = 0x0123456789ABCDEF
+    got = R.rmc_philox(seed, stream, instance, first, count).cpu().numpy().astype(np.uint64)
+    ref = philox.draw(np.arange(first, first + count, dtype=np.uint64), stream, seed, instance).astype(np.uint64)
+    np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("rows,cols", [(33, 7), (512, 256), (5, 1)])
+def test_gaussian_matrix(R, rows, cols):
+    got = R.rmc_gaussian_matrix(99, 3, rows, cols).cpu().numpy()
+    ref = philox.gaussian_matrix(99, rows, cols, instance=3)
+    np.testing.assert_allclose(got, ref, rtol=2e-6, atol=2e-6)
+
+
+@pytest.mark.parametrize("m,s", [(1000, 7), (4096, 256), (3, 1), (70000, 4096)])
+def test_countsketch_hash_bit_exact(R, m, s):
+    b, g = R.rmc_countsketch_hash(5, 0, m, s)
+    rb, rg = philox.countsketch_hash(5, m, s)
+    np.testing.assert_array_equal(b.cpu().numpy(), rb)
+    np.testing.assert_array_equal(g.cpu().numpy(), rg)
+
+
+@pytest.mark.parametrize("N,s", [(16, 16), (16, 1), (2048, 256), (1 << 16, 1000), (1 << 20, 4096), (1000, 999)])
+def test_srht_sample_bit_exact(R, N, s):
+    got = R.rmc_srht_sample(77, 0, N, s).cpu().numpy()
+    np.testing.assert_array_equal(got, philox.srht_sample(77, N, s))
+
+
+# ------------------------------------------------------------------------------------------ a2-a4 sketches
+
+SKETCH_CASES = [
+    # (m, n, s, lda_pad): the small low-rank workload, ragged sizes, leading dimension > n, tiny corners
+    (2048, 512, 256, 0),
+    (1000, 37, 100, 3),
+    (4097, 65, 300, 0),
+    (5000, 1, 17, 0),
+    (1, 4, 1, 0),
+    (70000, 20, 128, 4),
+]
+
+
+@pytest.mark.parametrize("kind", ["countsketch", "srht", "gaussian"])
+@pytest.mark.parametrize("m,n,s,pad", SKETCH_CASES)
+def test_sketch_parity(R, kind, m, n, s, pad):
+    A = workloads.gaussian(m, n, seed=m + n)
+    if m == 2048 and n == 512:
+        A = workloads.lowrank()
+    if kind == "srht" and s > sketch.next_pow2(m):
+        pytest.skip("s > N")
+    Ad = torch.zeros(m, n + pad, device="cuda")
+    Ad[:, :n] = dev(A)
+    C = R.rmc_sketch(Ad[:, :n], s, kind, seed=11)
+    R.rmc_sync()
+    ref = sketch.sketch(A, s, kind, 11)
+    assert relfro(C.cpu().numpy(), ref) < 1e-5
+
+
+def test_countsketch_deterministic(R):
+    A = dev(workloads.gaussian(50000, 64, seed=1))
+    C1 = R.rmc_sketch(A, 512, "countsketch", 3).clone()
+    C2 = R.rmc_sketch(A, 512, "countsketch", 3)
+    R.rmc_sync()
+    assert torch.equal(C1, C2)
+
+
+def test_srht_full_sample_orthogonal(R):
+    """s = N: the SRHT is orthogonal, column norms are preserved."""
+    A = workloads.gaussian(4096, 8, seed=4)
+    C = R.rmc_sketch(dev(A), 4096, "srht", 1)
+    R.rmc_sync()
+    np.testing.assert_allclose(np.linalg.norm(C.cpu().numpy(), axis=0), np.linalg.norm(A, axis=0), rtol=1e-5)
+
+
+def test_invalid_arguments(R):
+    A = torch.zeros(100, 10, device="cuda")
+    for args in [(A, 0, "gaussian", 1), (A, 129, "srht", 1)]:
+        with pytest.raises(R.RmcError) as e:
+            R.rmc_sketch(*args)
+        assert e.value.status == R.RMC_EINVAL
+
+
+# --------------------------------------------------------------------------------------------- a10 LSR
+
+@pytest.mark.parametrize("kind", ["countsketch", "srht", "gaussian"])
+@pytest.mark.parametrize("m,n,s", [(4000, 20, 200), (3000, 7, 3000), (20000, 64, 1024)])
+def test_lsr_parity(R, kind, m, n, s):
+    A, b, _ = workloads.tall_lsr_numpy(m, n, seed=m + n)
+    if kind == "srht" and s > sketch.next_pow2(m):
+        pytest.skip("s > N")
+    x = R.rmc_lsr_sketch(dev(A), dev(b), s, kind, seed=5)
+    R.rmc_sync()
+    xo = lsr.lsr_sketch(A, b, s, kind, 5)
+    assert relfro(x.cpu().numpy(), xo) < 1e-4
+    xs = lsr.lsr_exact(A, b)
+    assert lsr.residual_ratio(A, b, x.cpu().numpy(), xs) <= lsr.residual_ratio(A, b, xo, xs) * (1 + 1e-5)
+
+
+def test_lsr_noise_free_exact(R):
+    A, _, xt = workloads.tall_lsr_numpy(5000, 12, seed=3, noise_std=0.0)
+    b = (A.astype(np.float64) @ xt).astype(np.float32)
+    x = R.rmc_lsr_sketch(dev(A), dev(b), 400, "countsketch", 9)
+    R.rmc_sync()
+    assert relfro(x.cpu().numpy(), xt) < 1e-5
+
+
+# -------------------------------------------------------------------------------- a5-a9 rsvd and its steps
+
+@pytest.mark.parametrize("m,n,l", [(2048, 512, 20), (1000, 300, 33), (70000, 200, 120)])
+def test_matmuls(R, m, n, l):
+    A = workloads.gaussian(m, n, 1)
+    X1 = workloads.gaussian(n, l, 2)
+    X2 = workloads.gaussian(m, l, 3)
+    Y = R.rmc_matmul_an(dev(A), dev(X1))
+    W = R.rmc_matmul_at(dev(A), dev(X2))
+    R.rmc_sync()
+    A64 = A.astype(np.float64)
+    assert relfro(Y.cpu().numpy(), A64 @ X1) < 1e-5
+    assert relfro(W.cpu().numpy(), X2.astype(np.float64).T @ A64) < 1e-5
+
+
+@pytest.mark.parametrize("m,l", [(2048, 20), (5000, 33), (65536, 120), (300, 256)])
+def test_cholqr2(R, m, l):
+    Y = workloads.gaussian(m, l, 7) * np.linspace(1, 100, l).astype(np.float32)
+    Yd = dev(Y)
+    Rg = R.rmc_cholqr2(Yd)
+    R.rmc_sync()
+    Q = Yd.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(l), atol=5e-6)
+    assert relfro(Q @ Rg.cpu().numpy(), Y) < 1e-5
+    _, Rh = linalg.householder_qr(Y.astype(np.float64))
+    Rh = Rh * np.sign(np.diag(Rh))[:, None]
+    assert relfro(Rg.cpu().numpy(), Rh) < 1e-5
+
+
+@pytest.mark.parametrize("l,n", [(20, 512), (24, 100), (120, 4000)])
+def test_svd_wide(R, l, n):
+    B = workloads.gaussian(l, n, 8) * np.linspace(0.1, 10, l).astype(np.float32)[:, None]
+    Ub, s, Vb = R.rmc_svd_wide(dev(B))
+    R.rmc_sync()
+    _, so, _ = linalg.jacobi_svd(B.astype(np.float64))
+    np.testing.assert_allclose(s.cpu().numpy(), so, rtol=1e-5)
+    rec = (Ub.cpu().numpy().astype(np.float64) * s.cpu().numpy()) @ Vb.cpu().numpy().T
+    # l > 32 rotates in FP32 (orthogonality tolerance 4 eps sqrt(l)), l <= 32 in FP64
+    assert relfro(rec, B) < (3e-5 if l > 32 else 1e-5)
+
+
+def test_rsvd_lowrank_workload(R):
+    """The small workload: 2048 x 512, sigma_i = 0.9^i + noise, k = 10, p = 10, q = 2."""
+    A = workloads.lowrank()
+    U, s, V = R.rmc_rsvd(dev(A), 10, 10, 2, seed=0)
+    R.rmc_sync()
+    Uo, so, Vo, _ = rsvd.rsvd(A, 10, 10, 2, 0)
+    np.testing.assert_allclose(s.cpu().numpy(), so, rtol=1e-4)
+    A64 = A.astype(np.float64)
+    err = np.linalg.norm(A64 - (U.cpu().numpy() * s.cpu().numpy()) @ V.cpu().numpy().T)
+    erro = np.linalg.norm(A64 - (Uo * so) @ Vo.T)
+    assert abs(err - erro) <= 0.01 * erro
+    # same singular subspaces (the spectrum is well separated at the top)
+    assert np.all(np.abs(np.sum(U.cpu().numpy() * Uo, axis=0)) > 0.999)
+
+
+@pytest.mark.parametrize("q", [0, 1])
+def test_rsvd_exact_rank(R, q):
+    """A rank-k matrix is recovered (Sec. 5.2 derivation: range(A Omega) = range(A)) up to FP32 rounding."""
+    A = workloads.exact_rank(3000, 400, 8, seed=2, sigma=np.linspace(5, 1, 8))
+    U, s, V = R.rmc_rsvd(dev(A), 8, 0, q, seed=4)
+    R.rmc_sync()
+    np.testing.assert_allclose(s.cpu().numpy(), np.linspace(5, 1, 8), rtol=1e-4)
