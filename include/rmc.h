@@ -52,6 +52,7 @@ extern "C" {
 #define RMC_ETIMEOUT  5   /* a bounded device-side wait expired                                          */
 #define RMC_ECUDA     6   /* a CUDA runtime call or kernel launch failed                                 */
 #define RMC_PENDING   7   /* request not finished yet                                                    */
+#define RMC_ESCRATCH  8   /* the call needs more than the fixed scratch of rmc_countsketch_noalloc       */
 
 /* ----------------------------------------------------------------------------------- sketch kinds */
 #define RMC_GAUSSIAN     0   /* S = G / sqrt(s), G iid N(0,1)                                Sec. 3.2.1 */
@@ -188,6 +189,32 @@ int rmc_profile_end(rmc_ctx *ctx);
 
 /* Number of kernels this library has launched in the process so far (all contexts). */
 int rmc_launch_counter(uint64_t *launches);
+
+/* ------------------------------------------------------------------ count sketch without allocation */
+
+/* Bytes of the fixed device scratch array behind rmc_countsketch_noalloc. */
+#define RMC_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Count sketch C = S^T A (s x n, ldc), the same operator and result as rmc_sketch(..., RMC_COUNTSKETCH, ...),
+ * for callers that must not allocate device memory at call time: a serving loop that reserves all of its
+ * HBM up front and keeps allocation (which can synchronise the device) off its request path, or a host
+ * framework whose device memory belongs to its own allocator.  Such a caller cannot use a context either,
+ * since rmc_create allocates.  The paper has no counterpart; this is a deployment form of Algorithm 3.1.
+ *
+ * Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.  The sorting scratch lives in
+ * one file-scope __device__ array of RMC_NOALLOC_SCRATCH_BYTES (32 MiB), which every GPU that loads the
+ * library holds until the process exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current); make that first call before any stream capture.
+ * All calls share the one array and it keeps the previous call's contents (the counters are cleared on
+ * the stream before use), so calls whose work overlaps on the GPU -- on different streams, or from
+ * different host threads -- race on it and must be serialised by the caller.
+ *   cuda_stream: the cudaStream_t to enqueue on (NULL = legacy default stream), on the current device.
+ *   A, C: device pointers as for rmc_sketch (A m x n, lda >= n; C s x n, ldc >= n).
+ * Returns RMC_OK once enqueued; RMC_EINVAL for bad arguments; RMC_ESCRATCH when the call would need more
+ * than RMC_NOALLOC_SCRATCH_BYTES (about 8 m + 4 s ceil(m / 1024) bytes; e.g. m = 2^20 rows fit up to
+ * s = 4096); RMC_ECUDA if the address lookup or a launch fails.  Nothing is enqueued on error. */
+int rmc_countsketch_noalloc(void *cuda_stream, const float *A, int64_t m, int64_t n, int64_t lda, int64_t s,
+                            uint64_t seed, float *C, int64_t ldc);
 
 #ifdef __cplusplus
 }

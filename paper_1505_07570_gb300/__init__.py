@@ -50,7 +50,10 @@ _SIGS.update({
     "rmc_profile_read": [_p, _int, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)],
     "rmc_profile_end": [_p],
     "rmc_launch_counter": [ctypes.POINTER(_u64)],
+    "rmc_countsketch_noalloc": [_p, _p, _i64, _i64, _i64, _i64, _u64, _p, _i64],
 })
+RMC_ESCRATCH = 8
+RMC_NOALLOC_SCRATCH_BYTES = 32 << 20
 K_COUNTSKETCH, K_SRHT, K_SRHT_REDUCE, K_GAUSSIAN, K_MATMUL_AN, K_MATMUL_AT, K_GRAM, K_SMALL = range(8)
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -281,3 +284,16 @@ def rmc_launch_counter():
     out = _u64()
     _check(lib.rmc_launch_counter(ctypes.byref(out)), "rmc_launch_counter")
     return out.value
+
+
+def rmc_countsketch_noalloc(A, s, seed, out=None):
+    """Count sketch through the entry point that allocates no device memory (for callers that cannot
+    allocate at call time); enqueued on the current torch stream.  ``out`` (s x n) must be supplied by the
+    caller to keep the call allocation-free; a new tensor is made when it is None."""
+    import torch
+    _mat(A, "A")
+    m, n = A.shape
+    C = out if out is not None else torch.empty(s, n, device=A.device, dtype=torch.float32)
+    _check(lib.rmc_countsketch_noalloc(_p(torch.cuda.current_stream().cuda_stream), _ptr(A), m, n, A.stride(0),
+                                       s, seed, _ptr(C), C.stride(0)), "rmc_countsketch_noalloc")
+    return C

@@ -113,6 +113,7 @@ const char *rmc_status_string(int status) {
     case RMC_ETIMEOUT: return "a bounded device wait expired";
     case RMC_ECUDA: return "CUDA runtime error";
     case RMC_PENDING: return "pending";
+    case RMC_ESCRATCH: return "needs more than the fixed scratch of the no-allocation entry point";
     default: return "unknown status";
   }
 }

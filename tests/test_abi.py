@@ -42,7 +42,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_status_strings(lib):
     lib.rmc_status_string.restype = ctypes.c_char_p
     seen = set()
-    for code in range(8):
+    for code in range(9):
         s = lib.rmc_status_string(code)
         assert s and s not in seen
         seen.add(s)
