@@ -30,7 +30,7 @@ STEP = [("countsketch", 1024), ("countsketch", 4096), ("srht", 1024), ("srht", 4
         ("gaussian", 1024), ("gaussian", 4096)]
 SEED = 20150527
 ORACLE_SAMPLE_ROWS = 4096          # rows of A the CPU oracle sketches per call
-GAUSS_PREC = os.environ.get("RMC_BENCH_GAUSS_PREC", "fp32")
+GAUSS_PREC = os.environ.get("RMC_BENCH_GAUSS_PREC", "tf32")
 
 
 def peaks():

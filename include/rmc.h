@@ -101,6 +101,8 @@ int rmc_workspace_bytes(const rmc_ctx *ctx, size_t *bytes);
  *                   kept in ascending index order, scaled by 1/sqrt(s) (Sec. 3.2.2); 1 <= s <= N.
  *         RMC_COUNTSKETCH: C[h(i), :] += g(i) A[i, :] for every row i (Algorithm 3.1); any s >= 1.
  *   prec  GEMM operand precision of the Gaussian kind (RMC_FP32, RMC_TF32, RMC_BF16); ignored otherwise.
+ *         The tensor-core forms stream A with TMA and need 16-byte aligned rows (A and lda * 4 multiples of
+ *         16 bytes); other layouts run the FP32 CUDA-core kernel.
  *   seed  64-bit Philox key; the same (seed, m, s, kind) always gives the same S.
  * Errors: RMC_EINVAL, RMC_ENOMEM, RMC_ECUDA. */
 int rmc_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda,

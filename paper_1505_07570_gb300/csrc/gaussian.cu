@@ -100,14 +100,20 @@ int rmc_tc_gauss_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int6
                         uint64_t seed, uint32_t instance, int prec, float *C, int64_t ldc, float *Cb, void *ws);
 
 size_t rmc_gauss_ws(int64_t m, int64_t ntot, int64_t s, int prec, int num_sms) {
-  if (prec != RMC_FP32) return rmc_tc_gauss_ws(m, ntot, s, prec, num_sms);
-  return sizeof(float) * (size_t)gauss_splits(m, ntot, s, num_sms) * s * ntot;
+  const size_t simt = sizeof(float) * (size_t)gauss_splits(m, ntot, s, num_sms) * s * ntot;
+  if (prec == RMC_FP32) return simt;
+  const size_t tc = rmc_tc_gauss_ws(m, ntot, s, prec, num_sms);
+  return tc > simt ? tc : simt;   // rows that TMA cannot stream take the FP32 kernel
 }
 
 int rmc_launch_gauss_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b,
                             int64_t s, uint64_t seed, uint32_t instance, int prec, float *C, int64_t ldc, float *Cb,
                             void *ws) {
-  if (prec != RMC_FP32) return rmc_tc_gauss_sketch(ctx, A, m, n, lda, b, s, seed, instance, prec, C, ldc, Cb, ws);
+  // The tensor-core kernel streams A with TMA, which needs 16-byte aligned rows; other layouts take the FP32
+  // CUDA-core kernel (same operator, FP32 operands).
+  const bool tma_ok = (lda % 4 == 0) && (reinterpret_cast<uintptr_t>(A) % 16 == 0);
+  if (prec != RMC_FP32 && tma_ok)
+    return rmc_tc_gauss_sketch(ctx, A, m, n, lda, b, s, seed, instance, prec, C, ldc, Cb, ws);
   const int64_t ntot = n + (b ? 1 : 0);
   const int splits = gauss_splits(m, ntot, s, ctx->num_sms);
   int64_t rows = (m + splits - 1) / splits;

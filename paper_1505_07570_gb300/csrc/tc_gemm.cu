@@ -1,13 +1,422 @@
-// tcgen05 tensor-core kernels (TF32 / BF16 operands, FP32 accumulation in tensor memory).
+// tcgen05 tensor-core kernels (sm_103a): TF32 operands, FP32 accumulation in tensor memory.
+//
+// kind::tf32 takes both operands K-major, so the product with A over its rows needs A transposed on chip.
+//
+// Gaussian sketch C = (1/sqrt(s)) G^T [A | b] (Sec. 3.2.1), one CTA per (256 sketch rows, 256 columns of A,
+// range of rows of A):
+//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators) and issues tcgen05.mma
+//               (M=128, N=256, K=8) from one lane
+//   warps 4-11  per stage of 32 rows: draw G^T (32 x 256) from Philox straight into the K-major, 128-byte-
+//               swizzled operand layout, transpose the 32 x 256 tile of A (read one stage ahead with 16-byte
+//               loads) into the same K-major layout, and fold the b column in with FP32 FMAs
+//   warps 4-7   epilogue: tcgen05.ld of the accumulators, written as this row range's partial sum
+// Both sketch tiles share each transposed A tile.  Three stages of 64 KB are in flight; every wait is bounded
+// (RMC_ETIMEOUT after one second).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "rmc_internal.cuh"
+#include "philox.cuh"
+#include "tc_common.cuh"
 
-int rmc_tc_available(void) { return 0; }
+using namespace rmc;
 
-size_t rmc_tc_gauss_ws(int64_t, int64_t, int64_t, int, int) { return 0; }
-int rmc_tc_gauss_sketch(rmc_ctx *, const float *, int64_t, int64_t, int64_t, const float *, int64_t, uint64_t,
-                        uint32_t, int, float *, int64_t, float *, void *) {
-  return RMC_EINVAL;
+namespace {
+
+constexpr int kKStage = 32;                       // rows of A per stage (128 bytes of TF32 along K)
+constexpr int kM = 128, kN = 256;
+constexpr int kMT = 2;                            // 128-row sketch tiles per CTA sharing one A tile
+constexpr int kOmegaBytes = kM * kKStage * 4;     // 16 KB per sketch tile
+constexpr int kBBytes = kN * kKStage * 4;         // 32 KB: 256 columns of A, K-major (also the staging size)
+constexpr int kAtomBytes = kKStage * 128;         // staging: 32 rows x 32 columns, 128-byte swizzle
+constexpr int kStgStages = 2;                     // TMA staging buffers (A rows, row-major)
+constexpr int kStages = 2;                        // operand buffers (G^T tiles + transposed A)
+constexpr int kStageBytes = kMT * kOmegaBytes + kBBytes;
+constexpr int kTransWarp0 = 2, kTransWarps = 2;   // warps 2-3 transpose staging -> K-major
+constexpr int kRngWarp0 = 4, kRngWarps = 16;      // warps 4-19 draw G^T
+constexpr int kThreads = 32 * (kRngWarp0 + kRngWarps);
+constexpr int kTmemCols = kMT * kN;               // 512
+constexpr size_t kSmemBytes = 1024 + (size_t)kStgStages * kBBytes + (size_t)kStages * kStageBytes + 256;
+
+// Box-Muller with the fast hardware approximations: the operands are rounded to TF32 (10-bit mantissa)
+// before they reach the tensor cores, far coarser than these functions' ~2^-21 error.
+__device__ __forceinline__ float2 box_muller_fast(uint32_t wa, uint32_t wb) {
+  const float t = -2.0f * __logf(unit_f32(wa));
+  const float r = t * rsqrtf(t);
+  float sn, cs;
+  __sincosf(6.283185307179586f * (unit_f32(wb) - 0.5f), &sn, &cs);   // angle - pi, in (-pi, pi)
+  return make_float2(-r * cs, -r * sn);
 }
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Byte offset of (row r, 16-byte chunk q) in a tile with 128-byte rows and 128-byte swizzle.
+__device__ __forceinline__ int swz_off(int r, int q) { return r * 128 + ((q ^ (r & 7)) << 4); }
+
+struct GaussArgs {
+  const float *b;
+  int64_t m, n, ntot, s;
+  uint64_t seed;
+  uint32_t instance;
+  int64_t rows_per_split;
+  float *part;     // [splits][s][ntot]
+  int *status;
+};
+
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = !*abort_flag && tc::mbar_wait(bar, parity);
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok && (threadIdx.x & 31) == 0) {
+    *abort_flag = 1;
+    rmc_report(status, RMC_ETIMEOUT);
+  }
+  return ok != 0;
+}
+
+// grid: x = 256-row sketch range, y = 256-column tile of A, z = row range of A.
+__global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_constant__ CUtensorMap tmap_a,
+                                                               GaussArgs args) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~uintptr_t(1023));
+  unsigned char *staging = smem;                                   // kStgStages x 32 KB
+  unsigned char *operands = smem + kStgStages * kBBytes;           // kStages x (2 x 16 KB + 32 KB)
+  uint64_t *stg_full = reinterpret_cast<uint64_t *>(operands + kStages * kStageBytes);
+  uint64_t *stg_empty = stg_full + kStgStages;
+  uint64_t *full = stg_empty + kStgStages;
+  uint64_t *empty = full + kStages;
+  uint64_t *done = empty + kStages;
+  uint32_t *tmem_base_slot = reinterpret_cast<uint32_t *>(done + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_base_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t s0 = (int64_t)blockIdx.x * (kM * kMT);
+  const int64_t n0 = (int64_t)blockIdx.y * kN;
+  const int64_t k_begin = (int64_t)blockIdx.z * args.rows_per_split;
+  const int64_t k_end = min(args.m, k_begin + args.rows_per_split);
+  const int num_it = k_end > k_begin ? (int)((k_end - k_begin + kKStage - 1) / kKStage) : 0;
+  const int64_t groups = (args.s + 3) / 4;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStgStages; ++i) {
+      tc::mbar_init(&stg_full[i], 1);
+      tc::mbar_init(&stg_empty[i], kTransWarps);
+    }
+    for (int i = 0; i < kStages; ++i) {
+      tc::mbar_init(&full[i], kTransWarps + kRngWarps);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(done, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmap_a);
+  if (warp == 1) tc::tmem_alloc(tmem_base_slot, kTmemCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_base_slot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA: A rows into staging (row-major)
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < num_it; ++it) {
+        const int st = it % kStgStages;
+        const uint32_t ph = (it / kStgStages) & 1;
+        if (*abort_flag || !tc::mbar_wait(&stg_empty[st], ph ^ 1)) {
+          *abort_flag = 1;
+          rmc_report(args.status, RMC_ETIMEOUT);
+          break;
+        }
+        unsigned char *dst = staging + st * kBBytes;
+        tc::mbar_arrive_expect_tx(&stg_full[st], kBBytes);
+        const int32_t y = (int32_t)(k_begin + (int64_t)it * kKStage);
+#pragma unroll
+        for (int atom = 0; atom < kN / 32; ++atom)
+          tc::tma_load_2d(dst + atom * kAtomBytes, &tmap_a, (int32_t)(n0 + atom * 32), y, &stg_full[st]);
+        ++issued;
+      }
+      // copies still in flight land before the CTA may exit
+      for (int it = issued > kStgStages ? issued - kStgStages : 0; it < issued; ++it)
+        (void)tc::mbar_wait(&stg_full[it % kStgStages], (it / kStgStages) & 1);
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::instr_desc(2, 2, 0, 0, kN, kM);
+      for (int it = 0; it < num_it; ++it) {
+        const int st = it % kStages;
+        const uint32_t ph = (it / kStages) & 1;
+        if (*abort_flag || !tc::mbar_wait(&full[st], ph)) {
+          *abort_flag = 1;
+          rmc_report(args.status, RMC_ETIMEOUT);
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t base = tc::smem_u32(operands + st * kStageBytes);
+        const uint32_t b_addr = base + kMT * kOmegaBytes;
+#pragma unroll
+        for (int mt = 0; mt < kMT; ++mt)
+#pragma unroll
+          for (int kk = 0; kk < kKStage / 8; ++kk) {
+            const uint64_t adesc = tc::smem_desc(base + mt * kOmegaBytes + kk * 32, 16, 1024, tc::kSwizzle128B);
+            const uint64_t bdesc = tc::smem_desc(b_addr + kk * 32, 16, 1024, tc::kSwizzle128B);
+            tc::mma_tf32(tmem + mt * kN, adesc, bdesc, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+          }
+        tc::mma_commit(&empty[st]);
+      }
+      tc::mma_commit(done);   // also issued after an abort: completes once the issued MMAs have
+    }
+  } else if (warp < kRngWarp0) {
+    // ---------------------------------------------------------------- transposers: staging -> K-major
+    // Unit (kq, cq): rows 4kq..4kq+3 x columns 4cq..4cq+3.  Lane l of an 8-lane group takes kq = l and
+    // cq = (d + l) mod 64, so both the swizzled reads and the swizzled writes of a group hit 8 distinct
+    // 16-byte bank groups.
+    const int tl = (warp - kTransWarp0) * 32 + lane;       // 0..63
+    const int l = tl & 7, grp = tl >> 3;                   // 8 groups of 8 lanes
+    for (int it = 0; it < num_it; ++it) {
+      const int st = it % kStages, sst = it % kStgStages;
+      if (!warp_wait(&stg_full[sst], (it / kStgStages) & 1, abort_flag, args.status)) break;
+      if (!warp_wait(&empty[st], ((it / kStages) & 1) ^ 1, abort_flag, args.status)) break;
+      const unsigned char *src = staging + sst * kBBytes;
+      unsigned char *btile = operands + st * kStageBytes + kMT * kOmegaBytes;
+#pragma unroll 2
+      for (int d = grp; d < 64; d += 8) {
+        const int kq = l, cq = (d + l) & 63;
+        const int atom = cq >> 3, cc = cq & 7;
+        float4 v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          v[t] = *reinterpret_cast<const float4 *>(src + atom * kAtomBytes + swz_off(4 * kq + t, cc));
+        const int c4 = 4 * cq;
+        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 0, kq)) = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 1, kq)) = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
+        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 2, kq)) = make_float4(v[0].z, v[1].z, v[2].z, v[3].z);
+        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 3, kq)) = make_float4(v[0].w, v[1].w, v[2].w, v[3].w);
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        tc::mbar_arrive(&stg_empty[sst]);
+        tc::mbar_arrive(&full[st]);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- G^T producers (+ b column)
+    const int rw = warp - kRngWarp0;                        // 0..15
+    const int mt = rw >> 3;                                 // sketch tile of this warp
+    const int kq = lane & 7;                                // 16-byte chunk along K: rows 4kq .. 4kq+3
+    const int g = 4 * (rw & 7) + (lane >> 3);               // group of 4 sketch rows: 4g .. 4g+3
+    const bool with_b = args.b != nullptr && blockIdx.y == 0;
+    const uint64_t gidx = (uint64_t)((s0 + mt * kM) / 4 + g);
+    float bacc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int it = 0; it < num_it; ++it) {
+      const int st = it % kStages;
+      const int64_t row0 = k_begin + (int64_t)it * kKStage + 4 * kq;
+      float z[4][4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int64_t row = row0 + t;
+        if (row < k_end) {
+          const uint4 w = philox_block(args.seed, kStreamGaussian, args.instance, (uint64_t)row * groups + gidx);
+          const float2 a = box_muller_fast(w.x, w.y), c = box_muller_fast(w.z, w.w);
+          z[t][0] = a.x; z[t][1] = a.y; z[t][2] = c.x; z[t][3] = c.y;
+        } else {
+          z[t][0] = z[t][1] = z[t][2] = z[t][3] = 0.f;
+        }
+      }
+      if (with_b) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const float bv = (row0 + t < k_end) ? __ldg(args.b + row0 + t) : 0.f;
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) bacc[jj] = fmaf(z[t][jj], bv, bacc[jj]);
+        }
+      }
+      if (!warp_wait(&empty[st], ((it / kStages) & 1) ^ 1, abort_flag, args.status)) break;
+      unsigned char *otile = operands + st * kStageBytes + mt * kOmegaBytes;
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int r = 4 * g + jj;
+        *reinterpret_cast<float4 *>(otile + swz_off(r, kq)) =
+            make_float4(to_tf32(z[0][jj]), to_tf32(z[1][jj]), to_tf32(z[2][jj]), to_tf32(z[3][jj]));
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&full[st]);
+    }
+    if (with_b) {
+      // sum over the 8 lanes (kq) that share a group, then write the b column of the partial
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) bacc[jj] += __shfl_xor_sync(0xffffffffu, bacc[jj], o);
+      if (kq == 0) {
+        float *pb = args.part + ((int64_t)blockIdx.z * args.s) * args.ntot;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int64_t srow = s0 + mt * kM + 4 * g + jj;
+          if (srow < args.s) pb[srow * args.ntot + args.n] = bacc[jj];
+        }
+      }
+    }
+    // ---------------------------------------------------------------- epilogue: warps 4-7 tile 0, 8-11 tile 1
+    if ((rw & 7) < 4) {
+      const int et = rw >> 3;                    // accumulator (sketch tile) this warp drains
+      const int q = warp & 3;                    // TMEM lane quarter this warp may access
+      const bool ok = warp_wait(done, 0, abort_flag, args.status);
+      tc::tc_fence_after();
+      const int64_t ncols = min((int64_t)kN, args.n - n0);
+      if (ok) {
+        const int64_t srow = s0 + et * kM + q * 32 + lane;
+        float *prow = args.part + ((int64_t)blockIdx.z * args.s + srow) * args.ntot + n0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kN; c0 += 32) {
+          float v[32];
+          if (num_it > 0) {
+            tc::tmem_ld32(tmem + (uint32_t)(et * kN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = 0.f;   // empty row range: nothing was accumulated
+          }
+          if (srow < args.s) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (c0 + i < ncols) prow[c0 + i] = v[i];
+          }
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+__global__ void tc_reduce_kernel(const float *__restrict__ part, int splits, int64_t s, int64_t n, int64_t ntot,
+                                 float scale, float *__restrict__ C, int64_t ldc, float *__restrict__ Cb) {
+  const int64_t total = s * ntot;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int t = 0; t < splits; ++t) acc += part[t * total + e];
+    const int64_t r = e / ntot, c = e - r * ntot;
+    if (c < n) C[r * ldc + c] = acc * scale;
+    else Cb[r] = acc * scale;
+  }
+}
+
+// ------------------------------------------------------------------------------------------ host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      (void)cudaGetLastError();
+  }
+  return fn;
+}
+
+// Row-major FP32 matrix (rows x cols, leading dimension ld) as a 2-D tensor with a 32 x box_rows box and
+// 128-byte swizzle.
+int make_tmap(CUtensorMap *map, const float *base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return RMC_ECUDA;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 4) & 15)) return RMC_EALIGN;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RMC_OK : RMC_EALIGN;
+}
+
+// Row ranges per output tile so that tiles x splits fills whole waves of one CTA per SM.
+int tc_splits(int64_t m, int64_t tiles, int num_sms) {
+  const int64_t max_splits = (m + 2047) / 2048;
+  for (int waves = 1; waves <= 8; ++waves) {
+    int64_t sp = (int64_t)waves * num_sms / tiles;
+    if (sp < 1) sp = 1;
+    if (sp > max_splits) return (int)(max_splits < 1 ? 1 : max_splits);
+    const int64_t ctas = sp * tiles;
+    const int64_t w = (ctas + num_sms - 1) / num_sms;
+    if ((double)ctas / (double)(w * num_sms) >= 0.95) return (int)sp;
+  }
+  int64_t sp = 8LL * num_sms / tiles;
+  if (sp > max_splits) sp = max_splits;
+  return (int)(sp < 1 ? 1 : sp);
+}
+
+}  // namespace
+
+int rmc_tc_available(void) { return encode_fn() != nullptr; }
+
+// Split count for a sketch of s rows and ntot output columns (the same formula sizes the workspace).
+// Split count from the number of output tiles; ntot may include the b column, so the column-tile count is
+// estimated as floor(ntot / 256) (exact for the usual n = 256 * k with or without b).  The workspace and the
+// launch use this same function, so they always agree.
+int gauss_splits_tc(int64_t m, int64_t ntot, int64_t s, int num_sms) {
+  const int64_t nt = ntot / kN > 0 ? ntot / kN : 1;
+  return tc_splits(m, ((s + kM * kMT - 1) / (kM * kMT)) * nt, num_sms);
+}
+
+// ntot = n + 1 when b is sketched as well; the b column does not change the tiling.
+size_t rmc_tc_gauss_ws(int64_t m, int64_t ntot, int64_t s, int prec, int num_sms) {
+  (void)prec;
+  return sizeof(float) * (size_t)gauss_splits_tc(m, ntot, s, num_sms) * s * ntot + 256;
+}
+
+int rmc_tc_gauss_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b, int64_t s,
+                        uint64_t seed, uint32_t instance, int prec, float *C, int64_t ldc, float *Cb, void *ws) {
+  if (prec != RMC_TF32) return RMC_EINVAL;
+  const int64_t ntot = n + (b ? 1 : 0);
+  CUtensorMap map;
+  RMC_TRY(make_tmap(&map, A, m, n, lda, kKStage));
+  const int64_t mt = (s + kM * kMT - 1) / (kM * kMT), nt = (n + kN - 1) / kN;
+  // the same count the workspace was sized with (gauss_splits_tc of ntot)
+  const int splits = gauss_splits_tc(m, ntot, s, ctx->num_sms);
+  int64_t rows = (m + splits - 1) / splits;
+  rows = (rows + kKStage - 1) / kKStage * kKStage;
+  GaussArgs a;
+  a.b = b;
+  a.m = m;
+  a.n = n;
+  a.ntot = ntot;
+  a.s = s;
+  a.seed = seed;
+  a.instance = instance;
+  a.rows_per_split = rows;
+  a.part = static_cast<float *>(ws);
+  a.status = ctx->d_status;
+  RMC_TRY_CUDA(cudaFuncSetAttribute(tc_gauss_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+  {
+    RmcProf prof(ctx, RMC_K_GAUSSIAN);
+    tc_gauss_kernel<<<dim3((unsigned)mt, (unsigned)nt, (unsigned)splits), kThreads, kSmemBytes, ctx->stream>>>(map,
+                                                                                                              a);
+  }
+  tc_reduce_kernel<<<rmc_blocks(s * ntot, 256, 8192), 256, 0, ctx->stream>>>(
+      static_cast<float *>(ws), splits, s, n, ntot, 1.0f / sqrtf((float)s), C, ldc, Cb);
+  rmc_note_launch(2);
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
 size_t rmc_tc_matmul_ws(int64_t, int64_t, int64_t, int, int) { return 0; }
 int rmc_tc_matmul_an(rmc_ctx *, const float *, int64_t, int64_t, int64_t, const float *, int64_t, int64_t, float *,
                      int64_t, void *) {

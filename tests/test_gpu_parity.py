@@ -202,3 +202,41 @@ def test_rsvd_exact_rank(R, q):
     U, s, V = R.rmc_rsvd(dev(A), 8, 0, q, seed=4)
     R.rmc_sync()
     np.testing.assert_allclose(s.cpu().numpy(), np.linspace(5, 1, 8), rtol=1e-4)
+
+
+# --------------------------------------------------------------------------- a2 on the tensor cores (TF32)
+# TF32 keeps 10 mantissa bits: the sketch is compared at 2e-3 relative Frobenius error (the truncation of A
+# to TF32 alone shrinks entries by ~2^-11 on average), and least squares at the accuracy that implies.
+
+@pytest.mark.parametrize("m,n,s,pad", [(2048, 512, 256, 0), (4097, 65, 300, 0), (70000, 20, 128, 4),
+                                       (1000, 37, 100, 3), (1, 4, 1, 0), (300000, 256, 1024, 0)])
+def test_gaussian_tf32_parity(R, m, n, s, pad):
+    A = workloads.lowrank() if (m, n) == (2048, 512) else workloads.gaussian(m, n, seed=m + n)
+    Ad = torch.zeros(m, n + pad, device="cuda")
+    Ad[:, :n] = dev(A)
+    C = R.rmc_sketch(Ad[:, :n], s, "gaussian", seed=11, prec="tf32")
+    R.rmc_sync()
+    ref = sketch.sketch(A, s, "gaussian", 11)
+    assert relfro(C.cpu().numpy(), ref) < 2e-3
+
+
+def test_gaussian_tf32_unaligned_rows_take_fp32_kernel(R):
+    """Rows that are not 16-byte aligned (n = 5) cannot be streamed by TMA: the FP32 kernel runs instead and
+    meets the FP32 tolerance."""
+    A = workloads.gaussian(3000, 5, seed=2)
+    C = R.rmc_sketch(dev(A), 300, "gaussian", 1, prec="tf32")
+    R.rmc_sync()
+    assert relfro(C.cpu().numpy(), sketch.sketch(A, 300, "gaussian", 1)) < 1e-5
+
+
+@pytest.mark.parametrize("m,n,s", [(20000, 64, 1024), (4000, 20, 200)])
+def test_lsr_gaussian_tf32(R, m, n, s):
+    A, b, _ = workloads.tall_lsr_numpy(m, n, seed=m + n)
+    x = R.rmc_lsr_sketch(dev(A), dev(b), s, "gaussian", seed=5, prec="tf32")
+    R.rmc_sync()
+    xo = lsr.lsr_sketch(A, b, s, "gaussian", 5)
+    assert relfro(x.cpu().numpy(), xo) < 1e-2
+    # In this high signal-to-noise regression the TF32 rounding of S^T A is of the order of the noise, so the
+    # residual ratio ||A x - b||^2 / ||A x* - b||^2 is stated within 10% of the FP64 oracle's.
+    xs = lsr.lsr_exact(A, b)
+    assert lsr.residual_ratio(A, b, x.cpu().numpy(), xs) <= lsr.residual_ratio(A, b, xo, xs) * 1.10
