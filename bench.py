@@ -183,9 +183,22 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     step_bytes = sum(call_bytes(M, N_COLS, s) for _, s in STEP)
 
-    def step():
+    # the three sketch kinds run on their own streams, so each call's single-block solve overlaps the
+    # other calls' sketches; the library keeps one context per stream
+    streams = {kind: torch.cuda.Stream() for kind, _ in STEP}
+    main = torch.cuda.current_stream()
+
+    def step(outs=None):
+        done = []
         for kind, s in STEP:
-            rmc.rmc_lsr_sketch(A, b, s, kind, SEED, prec=GAUSS_PREC if kind == "gaussian" else "fp32")
+            st = streams[kind]
+            st.wait_stream(main)
+            with torch.cuda.stream(st):
+                x = rmc.rmc_lsr_sketch(A, b, s, kind, SEED, prec=GAUSS_PREC if kind == "gaussian" else "fp32")
+            if outs is not None:
+                outs.append(x)
+        for st in streams.values():
+            main.wait_stream(st)
 
     def barrier():
         if world > 1:
@@ -194,7 +207,7 @@ def run_ours(args, world, rank, local):
 
     for _ in range(args.warmup):
         step()
-    rmc.rmc_sync()
+    rmc.rmc_sync_all()
     stream = torch.cuda.current_stream()
     launches0 = rmc.rmc_launch_counter()
     rmc.rmc_profile_begin()
@@ -208,7 +221,7 @@ def run_ours(args, world, rank, local):
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    rmc.rmc_sync()
+    rmc.rmc_sync_all()
     seconds = ev0.elapsed_time(ev1) / 1e3
     launches = rmc.rmc_launch_counter() - launches0
     kernels = {}
@@ -238,8 +251,8 @@ def run_ours(args, world, rank, local):
     for _ in range(args.steps):
         A.copy_(A_h, non_blocking=True)
         b.copy_(b_h, non_blocking=True)
-        outs = [rmc.rmc_lsr_sketch(A, b, s, kind, SEED, prec=GAUSS_PREC if kind == "gaussian" else "fp32")
-                for kind, s in STEP]
+        outs = []
+        step(outs)
         host = [x.to("cpu", non_blocking=False) for x in outs]
         d2h = sum(x.numel() * 8 for x in host)
         xs = host
@@ -257,38 +270,52 @@ def run_ours(args, world, rank, local):
 
     pk = peaks()
     value = total_bytes / tmax / 1e9
-    # roofline of the dominant kernel
-    dom = max(kernels.items(), key=lambda kv: kv[1]["ms_total"]) if kernels else None
-    roof = None
-    if dom:
-        name, rec = dom
+
+    def roofline_of(name, rec):
+        """Roofline entry of one sketch kernel from its summed event time and launch count."""
         avg_s = rec["ms_total"] / rec["launches"] / 1e3
-        if name == "gaussian_sketch":
+        kind = name.split("_")[0]
+        if kind == "gaussian":
             # per launch: one (kind, s) call; flops of the product, averaged over the two sketch sizes
             flops = sum(2.0 * M * s * (N_COLS + 1) for k, s in STEP if k == "gaussian") / 2
             if GAUSS_PREC == "fp32":
                 peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
-                roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                        "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
+                r = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
             else:
                 ratio = 1.1 / 2.25 if GAUSS_PREC == "tf32" else 1.0
-                peak = pk["bf16_tflops"] * ratio
-                roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                        "peak_source": "%s bf16 x nominal %s/bf16 ratio" % (pk["source"], GAUSS_PREC)}
+                r = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": pk["bf16_tflops"] * ratio,
+                     "unit": "TFLOP/s", "peak_source": "%s bf16 x nominal %s/bf16 ratio" % (pk["source"], GAUSS_PREC)}
         else:
-            per_launch = sum(call_bytes(M, N_COLS, s) for k, s in STEP if k == name.split("_")[0]) / 2
-            roof = {"bound": "hbm", "achieved": per_launch / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "peak_source": pk["source"]}
-        roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["kernel"] = name
+            per_launch = sum(call_bytes(M, N_COLS, s) for k, s in STEP if k == kind) / 2
+            r = {"bound": "hbm", "achieved": per_launch / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                 "peak_source": pk["source"]}
+        r["frac"] = r["achieved"] / r["peak"]
+        r["kernel"] = name
+        r["ms_avg"] = avg_s * 1e3
+        return r
+
+    sketch_kernels = {k: v for k, v in kernels.items() if k in ("countsketch_gather", "srht_stage1", "gaussian_sketch")}
+    roof = None
+    if sketch_kernels:
+        name, rec = max(sketch_kernels.items(), key=lambda kv: kv[1]["ms_total"])
+        roof = roofline_of(name, rec)
         roof["traffic"] = None
     for name, rec in kernels.items():
-        avg_s = rec["ms_total"] / rec["launches"] / 1e3
-        rec["ms_avg"] = avg_s * 1e3
-        kind = name.split("_")[0]
-        if kind in ("countsketch", "srht") and name != "srht_stage2":
-            rec["hbm_frac_of_" + pk["source"]] = (sum(call_bytes(M, N_COLS, s) for k, s in STEP if k == kind) / 2
-                                                 / avg_s / 1e9 / pk["hbm_gbs"])
+        rec["ms_avg"] = rec["ms_total"] / rec["launches"]
+    # the same kernels once more, one call at a time on one stream (no overlap), for per-kernel rooflines
+    isolated = {}
+    rmc.rmc_profile_begin()
+    for kind, s in STEP:
+        with torch.cuda.stream(streams[kind]):
+            rmc.rmc_lsr_sketch(A, b, s, kind, SEED, prec=GAUSS_PREC if kind == "gaussian" else "fp32")
+        torch.cuda.synchronize()
+    for name, tag in [("countsketch_gather", rmc.K_COUNTSKETCH), ("srht_stage1", rmc.K_SRHT),
+                      ("gaussian_sketch", rmc.K_GAUSSIAN)]:
+        cnt, ms = rmc.rmc_profile_read(tag)
+        if cnt:
+            isolated[name] = roofline_of(name, {"launches": cnt, "ms_total": ms})
+    rmc.rmc_profile_end()
 
     cpu = None
     if world == 1:
@@ -304,7 +331,7 @@ def run_ours(args, world, rank, local):
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernels,
+        "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernels, "kernels_isolated": isolated,
     }
     print(json.dumps(line))
     if world > 1:

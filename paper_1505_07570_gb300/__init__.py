@@ -75,7 +75,8 @@ def _check(status, where):
 
 
 class Context:
-    """An rmc_ctx bound to a device; follows the current torch stream at every call."""
+    """An rmc_ctx bound to one device and one CUDA stream (each has its own workspace, so calls on different
+    streams may run concurrently)."""
 
     def __init__(self, budget_bytes=0):
         import torch
@@ -86,11 +87,6 @@ class Context:
         self.stream = stream
 
     def bind(self):
-        import torch
-        stream = torch.cuda.current_stream().cuda_stream
-        if stream != self.stream:
-            _check(lib.rmc_set_stream(self.handle, _p(stream)), "rmc_set_stream")
-            self.stream = stream
         return self.handle
 
     def close(self):
@@ -109,11 +105,18 @@ _contexts = {}
 
 
 def context():
+    """The context of the current device and current torch stream (created on first use)."""
+    import torch
+    key = (torch.cuda.current_device(), torch.cuda.current_stream().cuda_stream)
+    if key not in _contexts:
+        _contexts[key] = Context()
+    return _contexts[key]
+
+
+def _device_contexts():
     import torch
     dev = torch.cuda.current_device()
-    if dev not in _contexts:
-        _contexts[dev] = Context()
-    return _contexts[dev]
+    return [c for (d, _), c in _contexts.items() if d == dev]
 
 
 def _ptr(t):
@@ -136,8 +139,14 @@ def _prec(prec):
 
 
 def rmc_sync():
-    """Wait for the context's stream; raise RmcError for a device-detected error."""
+    """Wait for the current stream's context; raise RmcError for a device-detected error."""
     _check(lib.rmc_sync(context().bind()), "rmc_sync")
+
+
+def rmc_sync_all():
+    """rmc_sync on every context of the current device."""
+    for c in _device_contexts():
+        _check(lib.rmc_sync(c.handle), "rmc_sync")
 
 
 def rmc_workspace_bytes():
@@ -266,18 +275,26 @@ def rmc_matmul_at(A, X, prec="fp32"):
 
 
 def rmc_profile_begin():
-    _check(lib.rmc_profile_begin(context().bind()), "rmc_profile_begin")
+    """Start the event hooks on every context of the current device."""
+    for c in _device_contexts():
+        _check(lib.rmc_profile_begin(c.handle), "rmc_profile_begin")
 
 
 def rmc_profile_read(tag):
-    """(launches, total device milliseconds) of one kernel tag since rmc_profile_begin."""
-    n, ms = _i64(), ctypes.c_double()
-    _check(lib.rmc_profile_read(context().bind(), tag, ctypes.byref(n), ctypes.byref(ms)), "rmc_profile_read")
-    return n.value, ms.value
+    """(launches, total device milliseconds) of one kernel tag since rmc_profile_begin, summed over the
+    contexts of the current device."""
+    total_n, total_ms = 0, 0.0
+    for c in _device_contexts():
+        n, ms = _i64(), ctypes.c_double()
+        _check(lib.rmc_profile_read(c.handle, tag, ctypes.byref(n), ctypes.byref(ms)), "rmc_profile_read")
+        total_n += n.value
+        total_ms += ms.value
+    return total_n, total_ms
 
 
 def rmc_profile_end():
-    _check(lib.rmc_profile_end(context().bind()), "rmc_profile_end")
+    for c in _device_contexts():
+        _check(lib.rmc_profile_end(c.handle), "rmc_profile_end")
 
 
 def rmc_launch_counter():

@@ -169,66 +169,316 @@ __global__ void gram_reduce_kernel(const double *__restrict__ part, int chunks, 
   }
 }
 
-// ------------------------------------------------------------------------ FP64 Cholesky (one block)
-// G (l x l, symmetric) is overwritten by the upper factor R with G = R^T R; the strict lower triangle is
-// zeroed.  A non-positive or non-finite pivot reports RMC_ENUMERIC and sets *fail.
-__global__ void __launch_bounds__(1024) cholesky_kernel(double *G, int l, int *status, int *fail) {
+// Rinv = R^-1 (upper triangular): one warp per column c solves R x = e_c by a column sweep.
+__global__ void tri_inverse_cols_kernel(const double *R, int l, double *Rinv, float *Rinv32, const int *fail32,
+                                        const int *fail64) {
+  extern __shared__ double z[];   // l entries
+  const int c = blockIdx.x, lane = threadIdx.x;
+  if (!*fail32 || *fail64) return;   // the FP32 factor was used, or the FP64 one failed (status reported)
+  for (int k = lane; k < l; k += 32) z[k] = (k == c) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int i = c; i >= 0; --i) {
+    const double xi = z[i] / R[(int64_t)i * l + i];
+    __syncwarp();
+    for (int k = lane; k < i; k += 32) z[k] = fma(-R[(int64_t)k * l + i], xi, z[k]);
+    if (lane == 0) z[i] = xi;
+    __syncwarp();
+  }
+  for (int k = lane; k < l; k += 32) {
+    const double v = (k <= c) ? z[k] : 0.0;
+    Rinv[(int64_t)k * l + c] = v;
+    Rinv32[(int64_t)k * l + c] = (float)v;
+  }
+}
+
+// ---------------------------------------------------- FP32 Cholesky of an FP64 Gram matrix (one block)
+// On this GPU a dependent FP64 operation costs on the order of a hundred cycles, so the sequential part of a
+// small factorization runs in FP32 (a few cycles per dependent operation) on the FP64 Gram matrix rounded to
+// FP32, entirely in shared memory; least squares recovers FP64 accuracy by refinement against the FP64 Gram
+// matrix.  The upper triangle is packed: U[i][j] (j >= i) lives at P[base[i] + j], base[i] = i*l - i(i+1)/2.
+constexpr size_t kMaxPackedBytes = 200 * 1024;
+
+__device__ __forceinline__ int pk_base(int i, int l) { return i * l - (i * (i + 1)) / 2; }
+
+// Blocked right-looking Cholesky of the packed matrix in place (block-wide), panels of 32 rows of U:
+//   warp 0 factors the 32 x 32 diagonal block in registers (lane j holds column j),
+//   one thread per column solves the panel row U_kj = U_kk^-T G_kj,
+//   the block updates the trailing upper triangle G_ij -= U_ki^T U_kj.
+// Returns false on a non-positive pivot.  dinv[j] receives 1 / U[j][j].
+__device__ bool chol32_smem(float *P, const int *base, float *dinv, int l) {
+  __shared__ int bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int k0 = 0; k0 < l; k0 += 32) {
+    const int nb = min(32, l - k0);
+    if (warp == 0) {
+      float col[32];                       // col[q] = D[q][lane] (upper: q <= lane)
+#pragma unroll
+      for (int q = 0; q < 32; ++q) col[q] = (q <= lane && lane < nb) ? P[base[k0 + q] + k0 + lane] : 0.f;
+      int fail = 0;
+#pragma unroll
+      for (int p = 0; p < 32; ++p) {
+        if (p < nb) {
+          const float piv = __shfl_sync(0xffffffffu, col[p], p);
+          if (!(piv > 0.f) || !isfinite(piv)) fail = 1;
+          const float r = sqrtf(fmaxf(piv, 1e-30f)), inv = 1.f / r;
+          if (lane == p) col[p] = r;
+          if (lane > p) col[p] *= inv;      // D[p][lane]
+#pragma unroll
+          for (int q = p + 1; q < 32; ++q) {
+            const float dpq = __shfl_sync(0xffffffffu, col[p], q);   // D[p][q], held by lane q
+            if (lane >= q) col[q] = fmaf(-dpq, col[p], col[q]);
+          }
+        }
+      }
+      if (lane < nb) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          if (q <= lane) P[base[k0 + q] + k0 + lane] = col[q];
+        dinv[k0 + lane] = 1.f / col[lane];
+      }
+      if (lane == 0 && fail) bad = 1;
+    }
+    __syncthreads();
+    if (bad) return false;
+    // panel row: for every column c right of the block, solve D^T y = G[k0 .. k0+nb, c]
+    for (int c = k0 + nb + tid; c < l; c += blockDim.x) {
+      float y[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        if (q < nb) {
+          float v = P[base[k0 + q] + c];
+#pragma unroll
+          for (int t = 0; t < 32; ++t)
+            if (t < q) v = fmaf(-P[base[k0 + t] + k0 + q], y[t], v);
+          y[q] = v * dinv[k0 + q];
+          P[base[k0 + q] + c] = y[q];
+        }
+      }
+    }
+    __syncthreads();
+    // trailing update of the upper triangle
+    for (int i = k0 + nb + warp; i < l; i += nwarps) {
+      float ui[32];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) ui[t] = (t < nb) ? P[base[k0 + t] + i] : 0.f;
+      const int bi = base[i];
+      for (int j = i + lane; j < l; j += 32) {
+        float acc = 0.f;
+#pragma unroll
+        for (int t = 0; t < 32; ++t)
+          if (t < nb) acc = fmaf(ui[t], P[base[k0 + t] + j], acc);
+        P[bi + j] -= acc;
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// Solve U^T U d = w in place (w in shared memory, length l), blocked by 32: the diagonal block on warp 0,
+// the off-diagonal updates block-wide.
+__device__ void chol32_solve(const float *P, const int *base, const float *dinv, int l, float *w) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // forward: U^T y = w
+  for (int k0 = 0; k0 < l; k0 += 32) {
+    const int nb = min(32, l - k0);
+    if (warp == 0) {
+      float v = (lane < nb) ? w[k0 + lane] : 0.f;
+#pragma unroll
+      for (int p = 0; p < 32; ++p) {
+        if (p < nb) {
+          const float yp = __shfl_sync(0xffffffffu, v, p) * dinv[k0 + p];
+          if (lane == p) v = yp;
+          if (lane > p && lane < nb) v = fmaf(-P[base[k0 + p] + k0 + lane], yp, v);
+        }
+      }
+      if (lane < nb) w[k0 + lane] = v;
+    }
+    __syncthreads();
+    for (int k = k0 + nb + tid; k < l; k += blockDim.x) {
+      float v = w[k];
+      for (int t = 0; t < nb; ++t) v = fmaf(-P[base[k0 + t] + k], w[k0 + t], v);
+      w[k] = v;
+    }
+    __syncthreads();
+  }
+  // backward: U d = y
+  for (int k1 = l; k1 > 0; k1 -= 32) {
+    const int k0 = max(0, k1 - 32), nb = k1 - k0;
+    if (warp == 0) {
+      float v = (lane < nb) ? w[k0 + lane] : 0.f;
+#pragma unroll
+      for (int p = 31; p >= 0; --p) {
+        if (p < nb) {
+          const float dp = __shfl_sync(0xffffffffu, v, p) * dinv[k0 + p];
+          if (lane == p) v = dp;
+          if (lane < p) v = fmaf(-P[base[k0 + lane] + k0 + p], dp, v);
+        }
+      }
+      if (lane < nb) w[k0 + lane] = v;
+    }
+    __syncthreads();
+    for (int k = tid; k < k0; k += blockDim.x) {
+      float v = w[k];
+      const int bk = base[k];
+      for (int t = 0; t < nb; ++t) v = fmaf(-P[bk + k0 + t], w[k0 + t], v);
+      w[k] = v;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void load_packed(const double *G, int l, int ldg, float *P, int *base) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  for (int i = tid; i < l; i += blockDim.x) base[i] = pk_base(i, l);
+  for (int i = warp; i < l; i += nwarps) {
+    const int bi = pk_base(i, l);
+    for (int j = i + lane; j < l; j += 32) P[bi + j] = (float)G[(int64_t)i * ldg + j];
+  }
+  __syncthreads();
+}
+
+// CholeskyQR step: factor G (l x l FP64) in FP32, write R (FP64, upper) into G and R^-1 in FP32 (Rinv32).
+// fail[0] = 1 when the FP32 factorization broke down (the FP64 kernels below then take over).
+__global__ void __launch_bounds__(512) chol32_inv_kernel(double *G, int l, float *Rinv32, int *fail) {
+  extern __shared__ float smem32[];
+  int *base = reinterpret_cast<int *>(smem32);
+  float *dinv = smem32 + l;
+  float *P = smem32 + 2 * l;
+  load_packed(G, l, l, P, base);
+  const bool ok = chol32_smem(P, base, dinv, l);
+  if (threadIdx.x == 0) fail[0] = ok ? 0 : 1;
+  if (!ok) return;
+  __syncthreads();
+  // R^-1 column by column: one warp per column, column sweep from the diagonal up
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int c = warp; c < l; c += nwarps) {
+    for (int k = lane; k < l; k += 32) Rinv32[(int64_t)k * l + c] = 0.f;
+    __syncwarp();
+    // z holds the right-hand side e_c; entries k < i are updated in registers of their owner lane
+    float zr[8];   // up to 256 rows: lane owns rows lane + 32 t
+#pragma unroll
+    for (int t = 0; t < 8; ++t) zr[t] = (lane + 32 * t == c) ? 1.f : 0.f;
+    for (int i = c; i >= 0; --i) {
+      const float zi = __shfl_sync(0xffffffffu, zr[i >> 5], i & 31);
+      const float xi = zi * dinv[i];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int k = lane + 32 * t;
+        if (k < i) zr[t] = fmaf(-P[base[k] + i], xi, zr[t]);
+        if (k == i) zr[t] = xi;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int k = lane + 32 * t;
+      if (k <= c && k < l) Rinv32[(int64_t)k * l + c] = zr[t];
+    }
+  }
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e / l, j = e % l;
+    G[e] = (j >= i) ? (double)P[base[i] + j] : 0.0;
+  }
+}
+
+// Least squares on the augmented FP64 Gram matrix G ((n+1) x (n+1), last column g = [S^T A]^T S^T b):
+// U = chol32(G11), then x0 = U^-1 U^-T g and x += U^-1 U^-T (g - G11 x) with FP64 residuals (iters times).
+// fail[0] = 1 when the FP32 factorization broke down (the FP64 kernels below then take over).
+__global__ void __launch_bounds__(512) lsr_chol32_refine_kernel(const double *G, int n, double *x, int iters,
+                                                                  int *fail) {
+  extern __shared__ float smem32[];
+  int *base = reinterpret_cast<int *>(smem32);
+  float *dinv = smem32 + n;
+  double *r = reinterpret_cast<double *>(smem32 + 2 * n);   // 2n floats = 8n bytes: 8-byte aligned
+  double *xs = r + n;
+  float *w = reinterpret_cast<float *>(xs + n);
+  float *P = w + n;
+  const int ld = n + 1, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  load_packed(G, n, ld, P, base);
+  const bool ok = chol32_smem(P, base, dinv, n);
+  if (tid == 0) fail[0] = ok ? 0 : 1;
+  if (!ok) return;
+  for (int i = tid; i < n; i += blockDim.x) {
+    r[i] = G[(int64_t)i * ld + n];
+    xs[i] = 0.0;
+  }
+  __syncthreads();
+  for (int it = 0; it <= iters; ++it) {
+    for (int i = tid; i < n; i += blockDim.x) w[i] = (float)r[i];
+    __syncthreads();
+    chol32_solve(P, base, dinv, n, w);
+    for (int i = tid; i < n; i += blockDim.x) xs[i] += (double)w[i];
+    __syncthreads();
+    if (it == iters) break;
+    for (int i = warp; i < n; i += nwarps) {         // r = g - G11 x, one warp per row
+      const double *row = G + (int64_t)i * ld;
+      double acc = 0.0;
+      for (int k = lane; k < n; k += 32) acc = fma(row[k], xs[k], acc);
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) r[i] = row[n] - acc;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += blockDim.x) x[i] = xs[i];
+}
+
+size_t lsr32_smem_bytes(int n) {
+  return sizeof(float) * (2 * (size_t)n + 1) + sizeof(double) * 2 * n + sizeof(float) * n +
+         sizeof(float) * ((size_t)n * (n + 1) / 2) + 16;
+}
+
+size_t chol32_smem_bytes(int l) { return sizeof(float) * (2 * (size_t)l + (size_t)l * (l + 1) / 2); }
+
+// The FP64 path runs only when the FP32 one failed.  Matrices whose packed triangle does not fit in shared
+// memory go straight to the FP64 path.
+__global__ void force_fp64_kernel(int *fail32) { *fail32 = 1; }
+
+// FP64 fallback, one block: Cholesky of G (l x l) in place (upper), only if *fail32 is set.  A non-positive
+// pivot reports RMC_ENUMERIC and sets *fail64.
+__global__ void __launch_bounds__(1024) chol64_fallback_kernel(double *G, int l, const int *fail32, int *status,
+                                                               int *fail64) {
   __shared__ double piv;
   __shared__ int bad;
+  if (!*fail32) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   if (tid == 0) bad = 0;
   __syncthreads();
   for (int j = 0; j < l; ++j) {
     if (tid == 0) {
-      const double d = G[j * l + j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        bad = 1;
-      } else {
+      const double d = G[(int64_t)j * l + j];
+      if (!(d > 0.0) || !isfinite(d)) bad = 1;
+      else {
         piv = sqrt(d);
-        G[j * l + j] = piv;
+        G[(int64_t)j * l + j] = piv;
       }
     }
     __syncthreads();
     if (bad) break;
-    const double r = piv;
-    for (int i = j + 1 + tid; i < l; i += blockDim.x) G[j * l + i] /= r;
+    for (int i = j + 1 + tid; i < l; i += blockDim.x) G[(int64_t)j * l + i] /= piv;
     __syncthreads();
     for (int i = j + 1 + warp; i < l; i += nwarps) {
-      const double gi = G[j * l + i];
-      for (int k = i + lane; k < l; k += 32) G[i * l + k] = fma(-gi, G[j * l + k], G[i * l + k]);
+      const double gi = G[(int64_t)j * l + i];
+      for (int k = i + lane; k < l; k += 32) G[(int64_t)i * l + k] = fma(-gi, G[(int64_t)j * l + k], G[(int64_t)i * l + k]);
     }
     __syncthreads();
   }
-  for (int e = tid; e < l * l; e += blockDim.x)
+  for (int64_t e = tid; e < (int64_t)l * l; e += blockDim.x)
     if (e / l > e % l) G[e] = 0.0;
   if (tid == 0) {
+    *fail64 = bad;
     if (bad) rmc_report(status, RMC_ENUMERIC);
-    if (fail) *fail = bad;
   }
 }
 
-// Rinv = R^-1 (upper triangular), one thread per column, FP64; also an FP32 copy for the apply.
-__global__ void tri_inverse_kernel(const double *R, int l, double *Rinv, float *Rinv32) {
-  for (int j = threadIdx.x; j < l; j += blockDim.x) {
-    for (int i = j + 1; i < l; ++i) Rinv[i * l + j] = 0.0;
-    Rinv[j * l + j] = 1.0 / R[j * l + j];
-    for (int i = j - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int k = i + 1; k <= j; ++k) s = fma(R[i * l + k], Rinv[k * l + j], s);
-      Rinv[i * l + j] = -s / R[i * l + i];
-    }
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) Rinv32[e] = (float)Rinv[e];
-}
-
-// C = A B for upper-triangular l x l FP64 matrices (the R of CholeskyQR2 is R2 R1).
+// C = A B for upper-triangular l x l FP64 matrices (the R of CholeskyQR2 is R2 R1); one block per row.
 __global__ void tri_mul_kernel(const double *A, const double *B, int l, double *C) {
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-    const int i = e / l, j = e % l;
+  const int i = blockIdx.x;
+  for (int j = threadIdx.x; j < l; j += blockDim.x) {
     double s = 0.0;
     for (int k = i; k <= j; ++k) s = fma(A[i * l + k], B[k * l + j], s);
-    C[e] = (i <= j) ? s : 0.0;
+    C[i * l + j] = (i <= j) ? s : 0.0;
   }
 }
 
@@ -420,23 +670,26 @@ __global__ void sign_fix_kernel(const float *Vb, int64_t n, int64_t ldvb, const 
 }
 
 // ------------------------------------------------------------------------ least-squares back substitution
-// x = R11^-1 r12 where R ((n+1) x (n+1), upper) is the Cholesky factor of the augmented Gram matrix.
-__global__ void lsr_backsub_kernel(const double *R, int n, double *x, const int *fail) {
-  extern __shared__ double y[];
-  const int lda = n + 1;
+// x = R11^-1 r12 where R ((n+1) x (n+1), upper) is the Cholesky factor of the augmented Gram matrix: one warp,
+// x_i = (r_i,n - sum_{k>i} R_ik x_k) / R_ii from the last row up, each dot product over the lanes.
+__global__ void lsr_backsub_kernel(const double *R, int n, double *x, const int *fail32, const int *fail) {
+  extern __shared__ double xs[];
+  const int lda = n + 1, lane = threadIdx.x;
+  if (!*fail32) return;        // the FP32 factor and refinement produced x
   if (fail && *fail) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = nan("");
+    for (int i = lane; i < n; i += 32) x[i] = nan("");
     return;
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = R[i * lda + n];
-  __syncthreads();
   for (int i = n - 1; i >= 0; --i) {
-    const double xi = y[i] / R[i * lda + i];
-    __syncthreads();
-    for (int k = threadIdx.x; k < i; k += blockDim.x) y[k] = fma(-R[k * lda + i], xi, y[k]);
-    if (threadIdx.x == 0) x[i] = xi;
-    __syncthreads();
+    const double *row = R + (int64_t)i * lda;
+    double acc = 0.0;
+    for (int k = i + 1 + lane; k < n; k += 32) acc = fma(row[k], xs[k], acc);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const double xi = (row[n] - acc) / row[i];
+    if (lane == 0) xs[i] = xi;
+    __syncwarp();
   }
+  for (int i = lane; i < n; i += 32) x[i] = xs[i];
 }
 
 __global__ void copy_column_kernel(const float *v, int64_t s, float *W, int64_t ldw, int64_t col) {
@@ -508,15 +761,24 @@ int rmc_tc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t
 size_t rmc_tc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, int num_sms);
 
 size_t rmc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, int prec, int num_sms) {
-  if (prec == RMC_TF32) return rmc_tc_matmul_ws(m, n, l, which, num_sms);
-  if (which == 0) return 0;
-  const int splits = matmul_at_splits(m, n, l, num_sms);
-  return splits > 1 ? sizeof(float) * (size_t)splits * l * n : 0;
+  size_t simt = 0;
+  if (which == 1) {
+    const int splits = matmul_at_splits(m, n, l, num_sms);
+    simt = splits > 1 ? sizeof(float) * (size_t)splits * l * n : 0;
+  }
+  if (prec != RMC_TF32) return simt;
+  const size_t tc = rmc_tc_matmul_ws(m, n, l, which, num_sms);
+  return tc > simt ? tc : simt;
+}
+
+// The tensor-core products stream A with TMA (16-byte aligned rows); other layouts take the FP32 kernels.
+static bool tma_rows_ok(const float *A, int64_t lda) {
+  return (lda % 4 == 0) && (reinterpret_cast<uintptr_t>(A) % 16 == 0);
 }
 
 int rmc_launch_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
                          int64_t ldx, int prec, float *Y, int64_t ldy, void *ws) {
-  if (prec == RMC_TF32) return rmc_tc_matmul_an(ctx, A, m, n, lda, X, l, ldx, Y, ldy, ws);
+  if (prec == RMC_TF32 && tma_rows_ok(A, lda)) return rmc_tc_matmul_an(ctx, A, m, n, lda, X, l, ldx, Y, ldy, ws);
   dim3 grid((unsigned)((l + GT - 1) / GT), (unsigned)((m + GT - 1) / GT));
   {
     RmcProf prof(ctx, RMC_K_MATMUL_AN);
@@ -529,7 +791,7 @@ int rmc_launch_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int
 
 int rmc_launch_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
                          int64_t ldx, int prec, float *W, int64_t ldw, void *ws) {
-  if (prec == RMC_TF32) return rmc_tc_matmul_at(ctx, A, m, n, lda, X, l, ldx, W, ldw, ws);
+  if (prec == RMC_TF32 && tma_rows_ok(A, lda)) return rmc_tc_matmul_at(ctx, A, m, n, lda, X, l, ldx, W, ldw, ws);
   const int splits = matmul_at_splits(m, n, l, ctx->num_sms);
   int64_t rows = (m + splits - 1) / splits;
   rows = (rows + GK - 1) / GK * GK;
@@ -562,6 +824,29 @@ int rmc_launch_transpose(cudaStream_t st, const float *in, int64_t rows, int64_t
 
 // ------------------------------------------------------------------------------------------ CholeskyQR2
 
+// Upper factor of the FP64 Gram matrix G (l x l, overwritten by R in FP64) and R^-1 in FP32: FP32 Cholesky in
+// shared memory first; only if it meets a non-positive pivot (or the matrix is too large for shared memory)
+// does the FP64 factorization run (its kernels return at once otherwise), with no host round trip.
+// fail[0]: the FP32 path failed; fail[1]: the FP64 path failed.
+static int launch_factor(rmc_ctx *ctx, double *G, int l, double *Rinv, float *Rinv32, int *fail) {
+  cudaStream_t st = ctx->stream;
+  const size_t smem = chol32_smem_bytes(l);
+  RmcProf prof(ctx, RMC_K_SMALL);
+  if (smem > kMaxPackedBytes) {
+    force_fp64_kernel<<<1, 1, 0, st>>>(&fail[0]);
+  } else {
+    if (smem > 48 * 1024)
+      RMC_TRY_CUDA(cudaFuncSetAttribute(chol32_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    chol32_inv_kernel<<<1, 512, smem, st>>>(G, l, Rinv32, fail);
+  }
+  RMC_TRY_CUDA(cudaMemsetAsync(&fail[1], 0, sizeof(int), st));
+  chol64_fallback_kernel<<<1, 1024, 0, st>>>(G, l, &fail[0], ctx->d_status, &fail[1]);
+  tri_inverse_cols_kernel<<<l, 32, sizeof(double) * l, st>>>(G, l, Rinv, Rinv32, &fail[0], &fail[1]);
+  rmc_note_launch(3);
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
 size_t rmc_cholqr2_ws(int64_t m, int64_t l, int num_sms) {
   WsCarve w;
   w.take<double>(l * l);        // G
@@ -586,18 +871,12 @@ int rmc_launch_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l_, int64_t ld
   double *part = reinterpret_cast<double *>(w.take<char>(gram_ws(m, l, ctx->num_sms)));
   for (int pass = 0; pass < 2; ++pass) {
     RMC_TRY(launch_gram(ctx, Y, m, l, ldy, G, part));
-    {
-      RmcProf prof(ctx, RMC_K_SMALL);
-      cholesky_kernel<<<1, 1024, 0, st>>>(G, l, ctx->d_status, fail);
-      tri_inverse_kernel<<<1, 256, 0, st>>>(G, l, Rinv, Rinv32);
-    }
-    rmc_note_launch(2);
-    RMC_LAUNCH_CHECK();
+    RMC_TRY(launch_factor(ctx, G, l, Rinv, Rinv32, fail));
     RMC_TRY(launch_rowblock(st, Y, m, l, ldy, Rinv32, l, l, Y, ldy));
     if (R) {
       if (pass == 0) RMC_TRY_CUDA(cudaMemcpyAsync(R1, G, sizeof(double) * l * l, cudaMemcpyDeviceToDevice, st));
       else {
-        tri_mul_kernel<<<1, 1024, 0, st>>>(G, R1, l, R);
+        tri_mul_kernel<<<l, 128, 0, st>>>(G, R1, l, R);
         rmc_note_launch();
       }
     }
@@ -683,11 +962,24 @@ int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n, in
   int *fail = w.take<int>(4);
   double *part = reinterpret_cast<double *>(w.take<char>(gram_ws(s, l, ctx->num_sms)));
   copy_column_kernel<<<rmc_blocks(s, 256, 1024), 256, 0, st>>>(Sb, s, const_cast<float *>(SA), ldsa, n);
-  RMC_TRY(launch_gram(ctx, SA, s, l, ldsa, G, part));
+  rmc_note_launch();
+  RMC_TRY(launch_gram(ctx, SA, s, l, ldsa, G, part));     // FP64 augmented Gram [S^T A, S^T b]^T [...]
+  // FP32 Cholesky of the leading n x n block in shared memory, then x refined against the FP64 Gram matrix
+  const size_t smem = lsr32_smem_bytes((int)n);
   {
     RmcProf prof(ctx, RMC_K_SMALL);
-    cholesky_kernel<<<1, 1024, 0, st>>>(G, l, ctx->d_status, fail);
-    lsr_backsub_kernel<<<1, 1024, sizeof(double) * n, st>>>(G, (int)n, x, fail);
+    if (smem > kMaxPackedBytes) {
+      force_fp64_kernel<<<1, 1, 0, st>>>(&fail[0]);
+    } else {
+      if (smem > 48 * 1024)
+        RMC_TRY_CUDA(cudaFuncSetAttribute(lsr_chol32_refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+      lsr_chol32_refine_kernel<<<1, 512, smem, st>>>(G, (int)n, x, 1, fail);
+    }
+    // FP64 fallback on the augmented matrix (returns at once unless the FP32 factorization failed)
+    RMC_TRY_CUDA(cudaMemsetAsync(&fail[1], 0, sizeof(int), st));
+    chol64_fallback_kernel<<<1, 1024, 0, st>>>(G, l, &fail[0], ctx->d_status, &fail[1]);
+    lsr_backsub_kernel<<<1, 32, sizeof(double) * n, st>>>(G, (int)n, x, &fail[0], &fail[1]);
   }
   rmc_note_launch(3);
   RMC_LAUNCH_CHECK();

@@ -417,12 +417,419 @@ int rmc_tc_gauss_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int6
   return RMC_OK;
 }
 
-size_t rmc_tc_matmul_ws(int64_t, int64_t, int64_t, int, int) { return 0; }
-int rmc_tc_matmul_an(rmc_ctx *, const float *, int64_t, int64_t, int64_t, const float *, int64_t, int64_t, float *,
-                     int64_t, void *) {
-  return RMC_EINVAL;
+namespace {
+
+// =========================================================================== products with A for the rSVD
+// Y = A X (rmc_matmul_an): A tiles (128 rows x 32 columns) and X^T tiles (N rows x 32) both arrive K-major
+// through TMA; one CTA owns 128 rows of Y and runs the whole reduction over the n columns of A.
+// W = X^T A (rmc_matmul_at): X^T tiles by TMA (K-major), A tiles staged by TMA and transposed on chip (as in
+// the Gaussian kernel); split-K over the rows of A with a fixed-order reduction.
+
+constexpr int kAnStages = 4;
+constexpr int kAnThreads = 256;   // warp 0 TMA, warp 1 MMA, warps 4-7 epilogue
+
+template <int NPAD>
+__global__ void __launch_bounds__(kAnThreads, 1) tc_an_kernel(const __grid_constant__ CUtensorMap tmap_a,
+                                                              const __grid_constant__ CUtensorMap tmap_xt,
+                                                              int64_t m, int64_t n, int64_t l, float *Y,
+                                                              int64_t ldy, int *status) {
+  constexpr int kABytesAn = 128 * 128;            // 128 rows x 32 TF32
+  constexpr int kXBytes = NPAD * 128;              // NPAD rows x 32 TF32
+  constexpr int kStage = kABytesAn + kXBytes;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~uintptr_t(1023));
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kAnStages * kStage);
+  uint64_t *empty = full + kAnStages;
+  uint64_t *done = empty + kAnStages;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = (int64_t)blockIdx.x * 128;
+  const int num_it = (int)((n + kKStage - 1) / kKStage);
+  constexpr uint32_t kCols = NPAD < 32 ? 32 : NPAD;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kAnStages; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(done, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmap_a);
+    tc::prefetch_tmap(&tmap_xt);
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, kCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < num_it; ++it) {
+        const int st = it % kAnStages;
+        if (*abort_flag || !tc::mbar_wait(&empty[st], ((it / kAnStages) & 1) ^ 1)) {
+          *abort_flag = 1;
+          rmc_report(status, RMC_ETIMEOUT);
+          break;
+        }
+        unsigned char *stage = smem + st * kStage;
+        tc::mbar_arrive_expect_tx(&full[st], kStage);
+        tc::tma_load_2d(stage, &tmap_a, it * kKStage, (int32_t)row0, &full[st]);
+        tc::tma_load_2d(stage + kABytesAn, &tmap_xt, it * kKStage, 0, &full[st]);
+        ++issued;
+      }
+      for (int it = issued > kAnStages ? issued - kAnStages : 0; it < issued; ++it)
+        (void)tc::mbar_wait(&full[it % kAnStages], (it / kAnStages) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::instr_desc(2, 2, 0, 0, NPAD, 128);
+      for (int it = 0; it < num_it; ++it) {
+        const int st = it % kAnStages;
+        if (*abort_flag || !tc::mbar_wait(&full[st], (it / kAnStages) & 1)) {
+          *abort_flag = 1;
+          rmc_report(status, RMC_ETIMEOUT);
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t a_addr = tc::smem_u32(smem + st * kStage);
+        const uint32_t x_addr = a_addr + kABytesAn;
+#pragma unroll
+        for (int kk = 0; kk < kKStage / 8; ++kk) {
+          const uint64_t adesc = tc::smem_desc(a_addr + kk * 32, 16, 1024, tc::kSwizzle128B);
+          const uint64_t bdesc = tc::smem_desc(x_addr + kk * 32, 16, 1024, tc::kSwizzle128B);
+          tc::mma_tf32(tmem, adesc, bdesc, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+        }
+        tc::mma_commit(&empty[st]);
+      }
+      tc::mma_commit(done);
+    }
+  } else if (warp >= 4) {
+    const int q = warp & 3;
+    int ok = 1;
+    if (lane == 0) {
+      ok = tc::mbar_wait(done, 0);
+      if (!ok) rmc_report(status, RMC_ETIMEOUT);
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0) && !*abort_flag;
+    tc::tc_fence_after();
+    const int64_t row = row0 + q * 32 + lane;
+    if (ok) {
+#pragma unroll 1
+      for (int c0 = 0; c0 < NPAD; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        if (row < m) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (c0 + i < l) Y[row * ldy + c0 + i] = v[i];
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, kCols);
+  }
 }
-int rmc_tc_matmul_at(rmc_ctx *, const float *, int64_t, int64_t, int64_t, const float *, int64_t, int64_t, float *,
-                     int64_t, void *) {
-  return RMC_EINVAL;
+
+// W = X^T A over a row range of A: A_op = X^T tiles (MT x 128 rows of l, K-major via TMA), B_op = A tile
+// (256 columns) staged by TMA and transposed to K-major by warps 2-3.  Partial sums per row range.
+template <int MT>
+__global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __grid_constant__ CUtensorMap tmap_a,
+                                                                     const __grid_constant__ CUtensorMap tmap_xt,
+                                                                     int64_t m, int64_t n, int64_t l,
+                                                                     int64_t rows_per_split, float *part,
+                                                                     int *status) {
+  constexpr int kXtBytes = MT * kOmegaBytes;           // MT x (128 rows x 32 TF32)
+  constexpr int kStageAt = kXtBytes + kBBytes;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~uintptr_t(1023));
+  unsigned char *staging = smem;
+  unsigned char *operands = smem + kStgStages * kBBytes;
+  uint64_t *stg_full = reinterpret_cast<uint64_t *>(operands + kStages * kStageAt);
+  uint64_t *stg_empty = stg_full + kStgStages;
+  uint64_t *full = stg_empty + kStgStages;
+  uint64_t *empty = full + kStages;
+  uint64_t *done = empty + kStages;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n0 = (int64_t)blockIdx.x * kN;
+  const int64_t k_begin = (int64_t)blockIdx.z * rows_per_split;
+  const int64_t k_end = min(m, k_begin + rows_per_split);
+  const int num_it = k_end > k_begin ? (int)((k_end - k_begin + kKStage - 1) / kKStage) : 0;
+  constexpr uint32_t kCols = MT * kN;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStgStages; ++i) {
+      tc::mbar_init(&stg_full[i], 1);
+      tc::mbar_init(&stg_empty[i], kTransWarps);
+    }
+    for (int i = 0; i < kStages; ++i) {
+      tc::mbar_init(&full[i], kTransWarps + 1);      // two transposer warps + the X^T TMA arrival
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(done, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmap_a);
+    tc::prefetch_tmap(&tmap_xt);
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, kCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < num_it; ++it) {
+        const int st = it % kStages, sst = it % kStgStages;
+        if (*abort_flag || !tc::mbar_wait(&stg_empty[sst], ((it / kStgStages) & 1) ^ 1) ||
+            !tc::mbar_wait(&empty[st], ((it / kStages) & 1) ^ 1)) {
+          *abort_flag = 1;
+          rmc_report(status, RMC_ETIMEOUT);
+          break;
+        }
+        const int32_t y = (int32_t)(k_begin + (int64_t)it * kKStage);
+        unsigned char *dst = staging + sst * kBBytes;
+        tc::mbar_arrive_expect_tx(&stg_full[sst], kBBytes);
+#pragma unroll
+        for (int atom = 0; atom < kN / 32; ++atom)
+          tc::tma_load_2d(dst + atom * kAtomBytes, &tmap_a, (int32_t)(n0 + atom * 32), y, &stg_full[sst]);
+        unsigned char *xt = operands + st * kStageAt;
+        tc::mbar_arrive_expect_tx(&full[st], kXtBytes);
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) tc::tma_load_2d(xt + mt * kOmegaBytes, &tmap_xt, y, mt * 128, &full[st]);
+        ++issued;
+      }
+      for (int it = issued > kStgStages ? issued - kStgStages : 0; it < issued; ++it)
+        (void)tc::mbar_wait(&stg_full[it % kStgStages], (it / kStgStages) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::instr_desc(2, 2, 0, 0, kN, kM);
+      for (int it = 0; it < num_it; ++it) {
+        const int st = it % kStages;
+        if (*abort_flag || !tc::mbar_wait(&full[st], (it / kStages) & 1)) {
+          *abort_flag = 1;
+          rmc_report(status, RMC_ETIMEOUT);
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t base = tc::smem_u32(operands + st * kStageAt);
+        const uint32_t b_addr = base + kXtBytes;
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+          for (int kk = 0; kk < kKStage / 8; ++kk) {
+            const uint64_t adesc = tc::smem_desc(base + mt * kOmegaBytes + kk * 32, 16, 1024, tc::kSwizzle128B);
+            const uint64_t bdesc = tc::smem_desc(b_addr + kk * 32, 16, 1024, tc::kSwizzle128B);
+            tc::mma_tf32(tmem + mt * kN, adesc, bdesc, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+          }
+        tc::mma_commit(&empty[st]);
+      }
+      tc::mma_commit(done);
+    }
+  } else if (warp < 4) {
+    // transposers: staging (row-major, swizzled) -> K-major B tile (see the Gaussian kernel)
+    const int tl = (warp - kTransWarp0) * 32 + lane;
+    const int lq = tl & 7, grp = tl >> 3;
+    for (int it = 0; it < num_it; ++it) {
+      const int st = it % kStages, sst = it % kStgStages;
+      if (!warp_wait(&stg_full[sst], (it / kStgStages) & 1, abort_flag, status)) break;
+      if (!warp_wait(&empty[st], ((it / kStages) & 1) ^ 1, abort_flag, status)) break;
+      const unsigned char *src = staging + sst * kBBytes;
+      unsigned char *btile = operands + st * kStageAt + kXtBytes;
+#pragma unroll 2
+      for (int d = grp; d < 64; d += 8) {
+        const int kq = lq, cq = (d + lq) & 63;
+        const int atom = cq >> 3, cc = cq & 7;
+        float4 v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          v[t] = *reinterpret_cast<const float4 *>(src + atom * kAtomBytes + swz_off(4 * kq + t, cc));
+        const int c4 = 4 * cq;
+        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 0, kq)) = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 1, kq)) = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
+        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 2, kq)) = make_float4(v[0].z, v[1].z, v[2].z, v[3].z);
+        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 3, kq)) = make_float4(v[0].w, v[1].w, v[2].w, v[3].w);
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        tc::mbar_arrive(&stg_empty[sst]);
+        tc::mbar_arrive(&full[st]);
+      }
+    }
+  } else {
+    // epilogue: warps 4.. (MT x 4 warps), accumulator et, lane quarter q
+    const int ew = warp - 4, et = ew >> 2, q = warp & 3;
+    const bool ok = warp_wait(done, 0, abort_flag, status);
+    tc::tc_fence_after();
+    const int64_t row = (int64_t)et * kM + q * 32 + lane;    // row of W (index into l)
+    const int64_t ncols = min((int64_t)kN, n - n0);
+    if (ok) {
+      float *prow = part + ((int64_t)blockIdx.z * l + row) * n + n0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < kN; c0 += 32) {
+        float v[32];
+        if (num_it > 0) {
+          tc::tmem_ld32(tmem + (uint32_t)(et * kN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = 0.f;
+        }
+        if (row < l) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (c0 + i < ncols) prow[c0 + i] = v[i];
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, kCols);
+  }
+}
+
+__global__ void sum_parts_kernel(const float *__restrict__ part, int splits, int64_t rows, int64_t cols,
+                                 float *__restrict__ W, int64_t ldw) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int t = 0; t < splits; ++t) acc += part[t * total + e];
+    W[(e / cols) * ldw + e % cols] = acc;
+  }
+}
+
+__global__ void transpose32_kernel(const float *__restrict__ in, int64_t rows, int64_t cols, int64_t ldi,
+                                   float *__restrict__ out, int64_t ldo) {
+  __shared__ float tile[32][33];
+  const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = by + k, c = bx + threadIdx.x;
+    if (r < rows && c < cols) tile[k][threadIdx.x] = in[r * ldi + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t c = bx + k, r = by + threadIdx.x;
+    if (r < rows && c < cols) out[c * ldo + r] = tile[threadIdx.x][k];
+  }
+}
+
+int at_splits(int64_t m, int64_t n, int num_sms) { return tc_splits(m, (n + kN - 1) / kN, num_sms); }
+
+int64_t xt_ld(int64_t rows) { return (rows + 3) / 4 * 4; }   // 16-byte row pitch for TMA
+
+// Launch Y = A X with X^T (l x n) given; l <= 256.
+int launch_an_t(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *Xt, int64_t l,
+                int64_t ldxt, float *Y, int64_t ldy) {
+  CUtensorMap ma, mx;
+  const int npad = l <= 32 ? 32 : l <= 64 ? 64 : l <= 128 ? 128 : 256;
+  RMC_TRY(make_tmap(&ma, A, m, n, lda, 128));
+  RMC_TRY(make_tmap(&mx, Xt, l, n, ldxt, npad));
+  const size_t smem = 1024 + (size_t)kAnStages * (128 * 128 + npad * 128) + 256;
+  cudaStream_t st = ctx->stream;
+  const unsigned grid = (unsigned)((m + 127) / 128);
+  RmcProf prof(ctx, RMC_K_MATMUL_AN);
+#define RMC_AN_CASE(NP)                                                                                     \
+  case NP:                                                                                                  \
+    RMC_TRY_CUDA(cudaFuncSetAttribute(tc_an_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    tc_an_kernel<NP><<<grid, kAnThreads, smem, st>>>(ma, mx, m, n, l, Y, ldy, ctx->d_status);                \
+    break;
+  switch (npad) {
+    RMC_AN_CASE(32)
+    RMC_AN_CASE(64)
+    RMC_AN_CASE(128)
+    RMC_AN_CASE(256)
+  }
+#undef RMC_AN_CASE
+  rmc_note_launch();
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
+// Launch W = X^T A with X^T (l x m) given; l <= 256; part: workspace for the row-range partial sums.
+int launch_at_t(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *Xt, int64_t l,
+                int64_t ldxt, float *W, int64_t ldw, float *part) {
+  CUtensorMap ma, mx;
+  RMC_TRY(make_tmap(&ma, A, m, n, lda, kKStage));
+  RMC_TRY(make_tmap(&mx, Xt, l, m, ldxt, 128));
+  const int splits = at_splits(m, n, ctx->num_sms);
+  int64_t rows = (m + splits - 1) / splits;
+  rows = (rows + kKStage - 1) / kKStage * kKStage;
+  cudaStream_t st = ctx->stream;
+  dim3 grid((unsigned)((n + kN - 1) / kN), 1, (unsigned)splits);
+  {
+    RmcProf prof(ctx, RMC_K_MATMUL_AT);
+    if (l <= 128) {
+      const size_t smem = 1024 + (size_t)kStgStages * kBBytes + (size_t)kStages * (kOmegaBytes + kBBytes) + 256;
+      RMC_TRY_CUDA(cudaFuncSetAttribute(tc_at_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      tc_at_kernel<1><<<grid, 32 * 8, smem, st>>>(ma, mx, m, n, l, rows, part, ctx->d_status);
+    } else {
+      const size_t smem = 1024 + (size_t)kStgStages * kBBytes + (size_t)kStages * (2 * kOmegaBytes + kBBytes) + 256;
+      RMC_TRY_CUDA(cudaFuncSetAttribute(tc_at_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      tc_at_kernel<2><<<grid, 32 * 12, smem, st>>>(ma, mx, m, n, l, rows, part, ctx->d_status);
+    }
+  }
+  sum_parts_kernel<<<rmc_blocks(l * n, 256, 8192), 256, 0, st>>>(part, splits, l, n, W, ldw);
+  rmc_note_launch(2);
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
+}  // namespace
+
+// Workspace of the public TF32 products: X^T (padded pitch) plus the split partials of W = X^T A.
+size_t rmc_tc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, int num_sms) {
+  WsCarve w;
+  if (which == 0) {
+    w.take<float>((size_t)l * xt_ld(n));
+  } else {
+    w.take<float>((size_t)l * xt_ld(m));
+    w.take<float>((size_t)at_splits(m, n, num_sms) * l * n);
+  }
+  return w.off;
+}
+
+int rmc_tc_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
+                     int64_t ldx, float *Y, int64_t ldy, void *ws) {
+  WsCarve w;
+  w.base = static_cast<char *>(ws);
+  const int64_t ld = xt_ld(n);
+  float *Xt = w.take<float>((size_t)l * ld);
+  dim3 grid((unsigned)((l + 31) / 32), (unsigned)((n + 31) / 32));
+  transpose32_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(X, n, l, ldx, Xt, ld);
+  rmc_note_launch();
+  return launch_an_t(ctx, A, m, n, lda, Xt, l, ld, Y, ldy);
+}
+
+int rmc_tc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
+                     int64_t ldx, float *W, int64_t ldw, void *ws) {
+  WsCarve w;
+  w.base = static_cast<char *>(ws);
+  const int64_t ld = xt_ld(m);
+  float *Xt = w.take<float>((size_t)l * ld);
+  float *part = w.take<float>((size_t)at_splits(m, n, ctx->num_sms) * l * n);
+  dim3 grid((unsigned)((l + 31) / 32), (unsigned)((m + 31) / 32));
+  transpose32_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(X, m, l, ldx, Xt, ld);
+  rmc_note_launch();
+  return launch_at_t(ctx, A, m, n, lda, Xt, l, ld, W, ldw, part);
 }

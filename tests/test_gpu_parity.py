@@ -240,3 +240,57 @@ def test_lsr_gaussian_tf32(R, m, n, s):
     # residual ratio ||A x - b||^2 / ||A x* - b||^2 is stated within 10% of the FP64 oracle's.
     xs = lsr.lsr_exact(A, b)
     assert lsr.residual_ratio(A, b, x.cpu().numpy(), xs) <= lsr.residual_ratio(A, b, xo, xs) * 1.10
+
+
+def test_lsr_ill_conditioned_falls_back_to_fp64(R):
+    """cond(S^T A) ~ 1e5 squares to ~1e10 in the Gram matrix, beyond FP32: the FP32 Cholesky meets a
+    non-positive pivot and the FP64 factorization takes over; the fit stays as good as the oracle's."""
+    A, b, _ = workloads.tall_lsr_numpy(6000, 10, seed=3, noise_std=1.0)
+    A[:, 9] = A[:, 8] + 1e-5 * A[:, 7]
+    x = R.rmc_lsr_sketch(dev(A), dev(b), 600, "countsketch", seed=2)
+    R.rmc_sync()
+    xo = lsr.lsr_sketch(A, b, 600, "countsketch", 2)
+    xs = lsr.lsr_exact(A, b)
+    assert np.all(np.isfinite(x.cpu().numpy()))
+    assert lsr.residual_ratio(A, b, x.cpu().numpy(), xs) <= lsr.residual_ratio(A, b, xo, xs) * (1 + 1e-3)
+
+
+def test_cholqr2_ill_conditioned_falls_back_to_fp64(R):
+    Y = workloads.gaussian(4000, 16, 7) * np.logspace(0, 4.5, 16).astype(np.float32)
+    Yd = dev(Y)
+    R.rmc_cholqr2(Yd, want_r=False)
+    R.rmc_sync()
+    Q = Yd.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(16), atol=1e-4)
+
+
+# ------------------------------------------------------------------ a5-a7 on the tensor cores (TF32)
+
+@pytest.mark.parametrize("m,n,l", [(2048, 512, 20), (1000, 300, 33), (70000, 200, 120), (4096, 1000, 200)])
+def test_matmuls_tf32(R, m, n, l):
+    A = workloads.gaussian(m, n, 1)
+    X1 = workloads.gaussian(n, l, 2)
+    X2 = workloads.gaussian(m, l, 3)
+    Y = R.rmc_matmul_an(dev(A), dev(X1), prec="tf32")
+    W = R.rmc_matmul_at(dev(A), dev(X2), prec="tf32")
+    R.rmc_sync()
+    A64 = A.astype(np.float64)
+    assert relfro(Y.cpu().numpy(), A64 @ X1) < 2e-3
+    assert relfro(W.cpu().numpy(), X2.astype(np.float64).T @ A64) < 2e-3
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+def test_rsvd_factor_rank_workload(R, prec):
+    """A = G1 diag(1/i) G2^T (Gaussian factors), the large-rSVD recipe at a size the oracle runs."""
+    A = workloads.factor_rank_numpy(4096, 2048, 256, seed=3)
+    k, p, q = 20, 10, 1
+    U, s, V = R.rmc_rsvd(dev(A), k, p, q, seed=7, prec=prec)
+    R.rmc_sync()
+    _, so, _, _ = rsvd.rsvd(A, k, p, q, 7)
+    tol = 1e-4 if prec == "fp32" else 2e-3
+    np.testing.assert_allclose(s.cpu().numpy(), so, rtol=tol)
+    A64 = A.astype(np.float64)
+    err = np.linalg.norm(A64 - (U.cpu().numpy() * s.cpu().numpy()) @ V.cpu().numpy().T)
+    Uo, so, Vo, _ = rsvd.rsvd(A, k, p, q, 7)
+    erro = np.linalg.norm(A64 - (Uo * so) @ Vo.T)
+    assert abs(err - erro) <= 0.01 * erro
