@@ -317,6 +317,11 @@ def run_ours(args, world, rank, local):
             isolated[name] = roofline_of(name, {"launches": cnt, "ms_total": ms})
     rmc.rmc_profile_end()
 
+    rsvd_info = None
+    if world == 1 and not args.no_rsvd:
+        del A_h, b_h
+        rsvd_info = rsvd_measure(torch, rmc)
+
     cpu = None
     if world == 1:
         v, dt, nb, desc = oracle_sample()
@@ -332,6 +337,7 @@ def run_ours(args, world, rank, local):
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernels, "kernels_isolated": isolated,
+        "rsvd": rsvd_info,
     }
     print(json.dumps(line))
     if world > 1:
@@ -340,13 +346,77 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+def run_probe(kind):
+    """One small case of one kernel family, for profiler captures: A 262,144 x 256 (+ b), two warm-up calls,
+    then two timed calls.  Prints one JSON line."""
+    import torch
+    import paper_1505_07570_gb300 as rmc
+    import workloads
+    A, b, _ = workloads.tall_lsr_torch(1 << 18, N_COLS, seed=SEED)
+    if kind == "rsvd":
+        A = workloads.factor_rank_torch(16384, 4096, 512, seed=SEED)
+
+    def once():
+        if kind == "lsr":
+            return rmc.rmc_lsr_sketch(A, b, 1024, "countsketch", SEED)
+        if kind == "rsvd":
+            return rmc.rmc_rsvd(A, 100, 20, 1, SEED, prec="tf32")[1]
+        prec = GAUSS_PREC if kind == "gaussian" else "fp32"
+        return rmc.rmc_sketch(A, 1024, kind, SEED, prec=prec)
+
+    for _ in range(2):
+        once()
+    rmc.rmc_sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(2):
+        out = once()
+    e1.record()
+    rmc.rmc_sync()
+    print(json.dumps({"probe": kind, "ms_per_call": e0.elapsed_time(e1) / 2, "checksum": float(out.double().sum())}))
+    return 0
+
+
+def rsvd_measure(torch, rmc):
+    """The large randomized-SVD workload (A = G1 diag(1/i) G2^T, 65,536 x 16,384, rank 2048; k = 100, p = 20)
+    at q = 0, 1, 2 in FP32 and TF32 operands: device time per call and useful TFLOP/s of the products with A
+    (2q + 2 passes of 2 m n l flops)."""
+    import workloads
+    m, n, k, p = 65536, 16384, 100, 20
+    A = workloads.factor_rank_torch(m, n, 2048, seed=SEED)
+    out = {"workload": "rsvd 65536x16384 rank-2048 sigma_i=1/i, k=100 p=20", "calls": {}}
+    for prec in ["tf32", "fp32"]:
+        for q in [0, 1, 2]:
+            rmc.rmc_rsvd(A, k, p, q, SEED, prec=prec)
+            rmc.rmc_sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3 if prec == "tf32" else 1
+            e0.record()
+            for _ in range(reps):
+                _, sigma, _ = rmc.rmc_rsvd(A, k, p, q, SEED, prec=prec)
+            e1.record()
+            rmc.rmc_sync()
+            ms = e0.elapsed_time(e1) / reps
+            flops = (2 * q + 2) * 2.0 * m * n * (k + p)
+            out["calls"]["%s_q%d" % (prec, q)] = {"ms": ms, "product_tflops": flops / ms / 1e9,
+                                                  "sigma1": float(sigma[0]), "sigma100": float(sigma[-1])}
+    del A
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--probe", choices=["countsketch", "srht", "gaussian", "lsr", "rsvd"], default=None,
+                    help="run one small case of one kernel family (for profiler captures) and exit")
+    ap.add_argument("--no-rsvd", action="store_true", help="skip the large randomized-SVD measurement")
     args = ap.parse_args()
+    if args.probe:
+        return run_probe(args.probe)
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)

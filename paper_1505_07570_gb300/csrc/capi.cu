@@ -230,14 +230,16 @@ int rmc_rsvd(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, in
 
   cudaStream_t st = ctx->stream;
   RMC_TRY(rmc_launch_gaussian(st, seed, 0, n, l, Om, l, 1.0f));                  // Omega, n x l
+  // Intermediate bases only need to be well conditioned (one CholeskyQR pass); the basis that B = Q^T A is
+  // formed with is orthonormalised by CholeskyQR2.
   RMC_TRY(rmc_launch_matmul_an(ctx, A, m, n, lda, Om, l, l, gp, Y, l, scr));      // Y = A Omega
-  RMC_TRY(rmc_launch_cholqr2(ctx, Y, m, l, l, nullptr, scr));                     // Q = orth(Y)
+  RMC_TRY(rmc_launch_cholqr2(ctx, Y, m, l, l, nullptr, scr, q == 0 ? 2 : 1));    // Q = orth(Y)
   for (int it = 0; it < q; ++it) {
     RMC_TRY(rmc_launch_matmul_at(ctx, A, m, n, lda, Y, l, l, gp, B, n, scr));     // B = Q^T A  (l x n)
     RMC_TRY(rmc_launch_transpose(st, B, l, n, n, Z, l));                           // Z = B^T    (n x l)
-    RMC_TRY(rmc_launch_cholqr2(ctx, Z, n, l, l, nullptr, scr));                   // Z = orth(A^T Q)
+    RMC_TRY(rmc_launch_cholqr2(ctx, Z, n, l, l, nullptr, scr, 1));                // Z = orth(A^T Q)
     RMC_TRY(rmc_launch_matmul_an(ctx, A, m, n, lda, Z, l, l, gp, Y, l, scr));     // Y = A Z
-    RMC_TRY(rmc_launch_cholqr2(ctx, Y, m, l, l, nullptr, scr));                   // Q = orth(Y)
+    RMC_TRY(rmc_launch_cholqr2(ctx, Y, m, l, l, nullptr, scr, it == q - 1 ? 2 : 1));  // Q = orth(Y)
   }
   RMC_TRY(rmc_launch_matmul_at(ctx, A, m, n, lda, Y, l, l, gp, B, n, scr));       // B = Q^T A
   RMC_TRY(rmc_launch_svd_wide(ctx, B, l, n, n, Ub, sg, Vb, l, scr));              // B = Ub S Vb^T

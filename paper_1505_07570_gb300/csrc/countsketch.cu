@@ -3,8 +3,9 @@
 // GPU form: rather than scattering every row into C (m * n atomic adds), the rows are first grouped by bucket
 // with a counting sort of the m hashes (a few MB of traffic), and then one warp per bucket gathers its rows and
 // sums them in registers.  A is read exactly once, with whole-row coalesced loads, and C is written once.
-// Within a bucket the rows are summed in increasing row order (the order of Algorithm 3.1): the counting
-// sort is made stable by ranking each row among the rows of its chunk with warp match/ballot operations.
+// The counting sort is stable (rows are ranked within their chunk with warp match operations), so each
+// bucket's rows are visited in increasing row order, and the sums are formed in a fixed order: results are
+// bit-identical from run to run.
 #include "rmc_internal.cuh"
 #include "philox.cuh"
 
@@ -127,21 +128,26 @@ __global__ void __launch_bounds__(kChunk) cs_place_kernel(const uint32_t *code, 
   }
 }
 
-// Pass 4: one warp per bucket sums its rows (in row order) into registers.  Columns are split in blocks of
-// 32 * 4 * NV (float4 loads when the rows are 16-byte aligned); b, when given, is one more column.
+// Pass 4: one block per bucket.  Warp w of the block sums rows w, w + 4, w + 8, ... of the bucket (rows in
+// increasing order within each warp, eight in flight), then the four partial rows are added in warp order
+// through shared memory: deterministic.  Columns are split in blocks of 32 * 4 * NV (float4 loads when the
+// rows are 16-byte aligned); b, when given, is one more column.
+constexpr int kGatherWarps = 4;
+constexpr int kRowsInFlight = 8;
+
 template <int NV, bool VEC>
-__global__ void __launch_bounds__(256) cs_gather_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
-                                                        const float *__restrict__ bvec,
-                                                        const uint32_t *__restrict__ code,
-                                                        const uint32_t *__restrict__ bucket_start,
-                                                        const uint32_t *__restrict__ perm, int64_t s,
-                                                        float *__restrict__ C, int64_t ldc, float *__restrict__ Cb,
-                                                        int64_t col0) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+__global__ void __launch_bounds__(32 * kGatherWarps) cs_gather_kernel(const float *__restrict__ A, int64_t n,
+                                                                      int64_t lda, const float *__restrict__ bvec,
+                                                                      const uint32_t *__restrict__ code,
+                                                                      const uint32_t *__restrict__ bucket_start,
+                                                                      const uint32_t *__restrict__ perm, int64_t s,
+                                                                      float *__restrict__ C, int64_t ldc,
+                                                                      float *__restrict__ Cb, int64_t col0) {
   constexpr int W = VEC ? 4 : 1;               // floats per load
   constexpr int COLS = 32 * W * NV;            // columns per block of this launch
-  for (int64_t bk = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); bk < s; bk += warps) {
+  __shared__ float red[kGatherWarps][COLS + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t bk = blockIdx.x; bk < s; bk += gridDim.x) {
     const uint32_t beg = bucket_start[bk], end = bucket_start[bk + 1];
     float acc[NV][W];
 #pragma unroll
@@ -149,18 +155,19 @@ __global__ void __launch_bounds__(256) cs_gather_kernel(const float *__restrict_
 #pragma unroll
       for (int w = 0; w < W; ++w) acc[v][w] = 0.f;
     float accb = 0.f;
-    for (uint32_t j0 = beg; j0 < end; j0 += 4) {
-      uint32_t row[4];
-      float sg[4];
+    for (uint32_t j0 = beg + warp; j0 < end; j0 += kGatherWarps * kRowsInFlight) {
+      uint32_t row[kRowsInFlight];
+      float sg[kRowsInFlight];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool ok = j0 + u < end;
-        row[u] = ok ? perm[j0 + u] : 0u;
+      for (int u = 0; u < kRowsInFlight; ++u) {
+        const uint32_t j = j0 + kGatherWarps * u;
+        const bool ok = j < end;
+        row[u] = ok ? perm[j] : 0u;
         sg[u] = ok ? ((code[row[u]] & 1u) ? -1.f : 1.f) : 0.f;
       }
-      float val[4][NV][W];
+      float val[kRowsInFlight][NV][W];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kRowsInFlight; ++u) {
         const float *ar = A + (int64_t)row[u] * lda + col0;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -181,7 +188,7 @@ __global__ void __launch_bounds__(256) cs_gather_kernel(const float *__restrict_
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kRowsInFlight; ++u) {
 #pragma unroll
         for (int v = 0; v < NV; ++v)
 #pragma unroll
@@ -189,16 +196,24 @@ __global__ void __launch_bounds__(256) cs_gather_kernel(const float *__restrict_
         if (bvec && lane == 0 && col0 == 0 && sg[u] != 0.f) accb = fmaf(sg[u], __ldg(bvec + row[u]), accb);
       }
     }
-    float *crow = C + bk * ldc + col0;
+    // fixed-order combination of the warps' partial rows
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        const int64_t c = (int64_t)W * (lane + 32 * v) + w;
-        if (col0 + c < n) crow[c] = acc[v][w];
+      for (int w = 0; w < W; ++w) red[warp][W * (lane + 32 * v) + w] = acc[v][w];
+    if (lane == 0) red[warp][COLS] = accb;
+    __syncthreads();
+    for (int c = threadIdx.x; c <= COLS; c += blockDim.x) {
+      float t = 0.f;
+#pragma unroll
+      for (int q = 0; q < kGatherWarps; ++q) t += red[q][c];
+      if (c < COLS) {
+        if (col0 + c < n) C[bk * ldc + col0 + c] = t;
+      } else if (bvec && col0 == 0) {
+        Cb[bk] = t;
       }
-    if (bvec && lane == 0 && col0 == 0) Cb[bk] = accb;
-    (void)COLS;
+    }
+    __syncthreads();
   }
 }
 
@@ -256,20 +271,20 @@ int rmc_launch_countsketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, i
   RmcProf prof(ctx, RMC_K_COUNTSKETCH);
 
   const bool vec = (lda % 4 == 0) && (reinterpret_cast<uintptr_t>(A) % 16 == 0);
-  const unsigned grid = rmc_blocks(s, 8, 64 * ctx->num_sms);
+  const unsigned grid = (unsigned)(s < (int64_t)1 << 30 ? s : (int64_t)1 << 30);
   rmc_note_launch((int)((n + (vec ? 255 : 127)) / (vec ? 256 : 128)));
   if (vec) {
     for (int64_t c0 = 0; c0 < n; c0 += 256) {
       if (n - c0 > 128)
-        cs_gather_kernel<2, true><<<grid, 256, 0, st>>>(A, n, lda, b, bf.code, bf.bucket_start, bf.perm, s, C, ldc,
+        cs_gather_kernel<2, true><<<grid, 32 * kGatherWarps, 0, st>>>(A, n, lda, b, bf.code, bf.bucket_start, bf.perm, s, C, ldc,
                                                         Cb, c0);
       else
-        cs_gather_kernel<1, true><<<grid, 256, 0, st>>>(A, n, lda, b, bf.code, bf.bucket_start, bf.perm, s, C, ldc,
+        cs_gather_kernel<1, true><<<grid, 32 * kGatherWarps, 0, st>>>(A, n, lda, b, bf.code, bf.bucket_start, bf.perm, s, C, ldc,
                                                         Cb, c0);
     }
   } else {
     for (int64_t c0 = 0; c0 < n; c0 += 128)
-      cs_gather_kernel<4, false><<<grid, 256, 0, st>>>(A, n, lda, b, bf.code, bf.bucket_start, bf.perm, s, C, ldc,
+      cs_gather_kernel<4, false><<<grid, 32 * kGatherWarps, 0, st>>>(A, n, lda, b, bf.code, bf.bucket_start, bf.perm, s, C, ldc,
                                                        Cb, c0);
   }
   RMC_LAUNCH_CHECK();

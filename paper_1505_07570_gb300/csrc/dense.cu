@@ -157,6 +157,52 @@ __global__ void __launch_bounds__(256) gram_f64_kernel(const float *__restrict__
   if (i1 < l && j1 < l) o[i1 * l + j1] = acc11;
 }
 
+// Gram matrix with FP32 products summed in FP32 over each 32-row slice and in FP64 across slices (for
+// CholeskyQR2, whose factorization runs in FP32: FP64 products would not be used).
+__global__ void __launch_bounds__(256) gram_f32_kernel(const float *__restrict__ Y, int64_t m, int l, int64_t ldy,
+                                                       int64_t rows_per_chunk, double *__restrict__ part) {
+  __shared__ float As[GRAM_T][GRAM_T + 1];
+  __shared__ float Bs[GRAM_T][GRAM_T + 1];
+  int p = blockIdx.x, ti = 0;
+  const int T = (l + GRAM_T - 1) / GRAM_T;
+  while (p >= T - ti) { p -= T - ti; ++ti; }
+  const int tj = ti + p;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t r_begin = (int64_t)blockIdx.y * rows_per_chunk;
+  const int64_t r_end = min(m, r_begin + rows_per_chunk);
+  double acc00 = 0, acc01 = 0, acc10 = 0, acc11 = 0;
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += GRAM_T) {
+    for (int e = tid; e < GRAM_T * GRAM_T; e += 256) {
+      const int rr = e / GRAM_T, cc = e % GRAM_T;
+      const int64_t r = r0 + rr;
+      const int ca = ti * GRAM_T + cc, cb = tj * GRAM_T + cc;
+      As[rr][cc] = (r < r_end && ca < l) ? Y[r * ldy + ca] : 0.f;
+      Bs[rr][cc] = (r < r_end && cb < l) ? Y[r * ldy + cb] : 0.f;
+    }
+    __syncthreads();
+    float f00 = 0.f, f01 = 0.f, f10 = 0.f, f11 = 0.f;
+#pragma unroll 8
+    for (int rr = 0; rr < GRAM_T; ++rr) {
+      const float a0 = As[rr][ty], a1 = As[rr][ty + 16], b0 = Bs[rr][tx], b1 = Bs[rr][tx + 16];
+      f00 = fmaf(a0, b0, f00);
+      f01 = fmaf(a0, b1, f01);
+      f10 = fmaf(a1, b0, f10);
+      f11 = fmaf(a1, b1, f11);
+    }
+    acc00 += f00;
+    acc01 += f01;
+    acc10 += f10;
+    acc11 += f11;
+    __syncthreads();
+  }
+  double *o = part + (int64_t)blockIdx.y * l * l;
+  const int i0 = ti * GRAM_T + ty, i1 = i0 + 16, j0 = tj * GRAM_T + tx, j1 = j0 + 16;
+  if (i0 < l && j0 < l) o[i0 * l + j0] = acc00;
+  if (i0 < l && j1 < l) o[i0 * l + j1] = acc01;
+  if (i1 < l && j0 < l) o[i1 * l + j0] = acc10;
+  if (i1 < l && j1 < l) o[i1 * l + j1] = acc11;
+}
+
 __global__ void gram_reduce_kernel(const double *__restrict__ part, int chunks, int l, double *__restrict__ G) {
   const int total = l * l;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
@@ -200,77 +246,27 @@ constexpr size_t kMaxPackedBytes = 200 * 1024;
 
 __device__ __forceinline__ int pk_base(int i, int l) { return i * l - (i * (i + 1)) / 2; }
 
-// Blocked right-looking Cholesky of the packed matrix in place (block-wide), panels of 32 rows of U:
-//   warp 0 factors the 32 x 32 diagonal block in registers (lane j holds column j),
-//   one thread per column solves the panel row U_kj = U_kk^-T G_kj,
-//   the block updates the trailing upper triangle G_ij -= U_ki^T U_kj.
-// Returns false on a non-positive pivot.  dinv[j] receives 1 / U[j][j].
+// Right-looking Cholesky of the packed matrix in place (block-wide): for each pivot j, scale row j of U, then
+// update the trailing upper triangle, one warp per row, lanes along the row.  Returns false on a non-positive
+// pivot.  dinv[j] receives 1 / U[j][j].
 __device__ bool chol32_smem(float *P, const int *base, float *dinv, int l) {
-  __shared__ int bad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  if (tid == 0) bad = 0;
-  __syncthreads();
-  for (int k0 = 0; k0 < l; k0 += 32) {
-    const int nb = min(32, l - k0);
-    if (warp == 0) {
-      float col[32];                       // col[q] = D[q][lane] (upper: q <= lane)
-#pragma unroll
-      for (int q = 0; q < 32; ++q) col[q] = (q <= lane && lane < nb) ? P[base[k0 + q] + k0 + lane] : 0.f;
-      int fail = 0;
-#pragma unroll
-      for (int p = 0; p < 32; ++p) {
-        if (p < nb) {
-          const float piv = __shfl_sync(0xffffffffu, col[p], p);
-          if (!(piv > 0.f) || !isfinite(piv)) fail = 1;
-          const float r = sqrtf(fmaxf(piv, 1e-30f)), inv = 1.f / r;
-          if (lane == p) col[p] = r;
-          if (lane > p) col[p] *= inv;      // D[p][lane]
-#pragma unroll
-          for (int q = p + 1; q < 32; ++q) {
-            const float dpq = __shfl_sync(0xffffffffu, col[p], q);   // D[p][q], held by lane q
-            if (lane >= q) col[q] = fmaf(-dpq, col[p], col[q]);
-          }
-        }
-      }
-      if (lane < nb) {
-#pragma unroll
-        for (int q = 0; q < 32; ++q)
-          if (q <= lane) P[base[k0 + q] + k0 + lane] = col[q];
-        dinv[k0 + lane] = 1.f / col[lane];
-      }
-      if (lane == 0 && fail) bad = 1;
+  for (int j = 0; j < l; ++j) {
+    const int bj = base[j];
+    const float d = P[bj + j];
+    if (!(d > 0.f) || !isfinite(d)) return false;   // uniform: every thread read the same pivot
+    const float r = sqrtf(d), inv = 1.f / r;
+    __syncthreads();                                 // everyone has read the pivot before it changes
+    for (int k = j + 1 + tid; k < l; k += blockDim.x) P[bj + k] *= inv;
+    if (tid == 0) {
+      P[bj + j] = r;
+      dinv[j] = inv;
     }
     __syncthreads();
-    if (bad) return false;
-    // panel row: for every column c right of the block, solve D^T y = G[k0 .. k0+nb, c]
-    for (int c = k0 + nb + tid; c < l; c += blockDim.x) {
-      float y[32];
-#pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        if (q < nb) {
-          float v = P[base[k0 + q] + c];
-#pragma unroll
-          for (int t = 0; t < 32; ++t)
-            if (t < q) v = fmaf(-P[base[k0 + t] + k0 + q], y[t], v);
-          y[q] = v * dinv[k0 + q];
-          P[base[k0 + q] + c] = y[q];
-        }
-      }
-    }
-    __syncthreads();
-    // trailing update of the upper triangle
-    for (int i = k0 + nb + warp; i < l; i += nwarps) {
-      float ui[32];
-#pragma unroll
-      for (int t = 0; t < 32; ++t) ui[t] = (t < nb) ? P[base[k0 + t] + i] : 0.f;
+    for (int i = j + 1 + warp; i < l; i += nwarps) {
+      const float gi = P[bj + i];
       const int bi = base[i];
-      for (int j = i + lane; j < l; j += 32) {
-        float acc = 0.f;
-#pragma unroll
-        for (int t = 0; t < 32; ++t)
-          if (t < nb) acc = fmaf(ui[t], P[base[k0 + t] + j], acc);
-        P[bi + j] -= acc;
-      }
+      for (int k = i + lane; k < l; k += 32) P[bi + k] = fmaf(-gi, P[bj + k], P[bi + k]);
     }
     __syncthreads();
   }
@@ -352,29 +348,22 @@ __global__ void __launch_bounds__(512) chol32_inv_kernel(double *G, int l, float
   if (threadIdx.x == 0) fail[0] = ok ? 0 : 1;
   if (!ok) return;
   __syncthreads();
-  // R^-1 column by column: one warp per column, column sweep from the diagonal up
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (int c = warp; c < l; c += nwarps) {
-    for (int k = lane; k < l; k += 32) Rinv32[(int64_t)k * l + c] = 0.f;
-    __syncwarp();
-    // z holds the right-hand side e_c; entries k < i are updated in registers of their owner lane
-    float zr[8];   // up to 256 rows: lane owns rows lane + 32 t
-#pragma unroll
-    for (int t = 0; t < 8; ++t) zr[t] = (lane + 32 * t == c) ? 1.f : 0.f;
+  // R^-1, one thread per column c, rows from the bottom: X[i][c] = (delta_ic - sum_{k>i} U[i][k] X[k][c]) / U[i][i].
+  // A column depends only on itself, so no synchronisation; X lives in Rinv32 (the thread's own column).
+  for (int c = threadIdx.x; c < l; c += blockDim.x) {
+    for (int i = l - 1; i > c; --i) Rinv32[(int64_t)i * l + c] = 0.f;
     for (int i = c; i >= 0; --i) {
-      const float zi = __shfl_sync(0xffffffffu, zr[i >> 5], i & 31);
-      const float xi = zi * dinv[i];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int k = lane + 32 * t;
-        if (k < i) zr[t] = fmaf(-P[base[k] + i], xi, zr[t]);
-        if (k == i) zr[t] = xi;
+      const int bi = base[i];
+      float a0 = (i == c) ? 1.f : 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      int k = i + 1;
+      for (; k + 4 <= c + 1; k += 4) {
+        a0 = fmaf(-P[bi + k], Rinv32[(int64_t)k * l + c], a0);
+        a1 = fmaf(-P[bi + k + 1], Rinv32[(int64_t)(k + 1) * l + c], a1);
+        a2 = fmaf(-P[bi + k + 2], Rinv32[(int64_t)(k + 2) * l + c], a2);
+        a3 = fmaf(-P[bi + k + 3], Rinv32[(int64_t)(k + 3) * l + c], a3);
       }
-    }
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int k = lane + 32 * t;
-      if (k <= c && k < l) Rinv32[(int64_t)k * l + c] = zr[t];
+      for (; k <= c; ++k) a0 = fmaf(-P[bi + k], Rinv32[(int64_t)k * l + c], a0);
+      Rinv32[(int64_t)i * l + c] = ((a0 + a1) + (a2 + a3)) * dinv[i];
     }
   }
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
@@ -602,6 +591,87 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(T *W, T *V, int l, T tol, 
   if (sweep == max_sweeps && threadIdx.x == 0) rmc_report(status, RMC_ENUMERIC);
 }
 
+// Jacobi rotation (c, s) zeroing the inner product of a column pair.
+__device__ __forceinline__ void rotation(double alpha, double beta, double gamma, double &c, double &s) {
+  const double zeta = (beta - alpha) / (2.0 * gamma);
+  const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = c * t;
+}
+__device__ __forceinline__ void rotation(float alpha, float beta, float gamma, float &c, float &s) {
+  // correctly rounded reciprocals and square roots: an approximate rsqrt biases c^2 + s^2 below 1 and the
+  // column norms (the singular values) shrink a little at every one of their ~l x sweeps rotations
+  const float zeta = (beta - alpha) * __frcp_rn(2.f * gamma);
+  const float t = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + __fsqrt_rn(fmaf(zeta, zeta, 1.f)));
+  c = __frcp_rn(__fsqrt_rn(fmaf(t, t, 1.f)));
+  s = c * t;
+}
+
+// The same rotations with W and V held in shared memory (used when 2 l^2 values fit): a pair costs a few
+// hundred cycles instead of global-memory round trips.
+template <typename T>
+__global__ void __launch_bounds__(1024) jacobi_smem_kernel(T *Wg, T *Vg, int l, T tol, int max_sweeps, int *status) {
+  extern __shared__ __align__(16) unsigned char jac_raw[];
+  T *W = reinterpret_cast<T *>(jac_raw);
+  T *V = W + (size_t)l * l;
+  __shared__ int rotated;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    W[e] = Wg[e];
+    V[e] = (e / l == e % l) ? T(1) : T(0);
+  }
+  const int lp = (l + 1) & ~1;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int round = 0; round < lp - 1; ++round) {
+      for (int pr = warp; pr < lp / 2; pr += nwarps) {
+        const int a = pr, b = lp - 1 - pr;
+        int p = a == 0 ? 0 : 1 + (a - 1 + round) % (lp - 1);
+        int q = b == 0 ? 0 : 1 + (b - 1 + round) % (lp - 1);
+        if (p > q) { const int t = p; p = q; q = t; }
+        if (q >= l) continue;
+        T *wp = W + (size_t)p * l, *wq = W + (size_t)q * l;
+        T alpha = 0, beta = 0, gamma = 0;
+        for (int r = lane; r < l; r += 32) {
+          const T x = wp[r], y = wq[r];
+          alpha = fma(x, x, alpha);
+          beta = fma(y, y, beta);
+          gamma = fma(x, y, gamma);
+        }
+        for (int o = 16; o; o >>= 1) {
+          alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+          beta += __shfl_xor_sync(0xffffffffu, beta, o);
+          gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
+        }
+        if (gamma == T(0) || fabs(gamma) <= tol * sqrt(alpha * beta)) continue;
+        T c, sn;
+        rotation(alpha, beta, gamma, c, sn);
+        T *vp = V + (size_t)p * l, *vq = V + (size_t)q * l;
+        for (int r = lane; r < l; r += 32) {
+          const T x = wp[r], y = wq[r];
+          wp[r] = c * x - sn * y;
+          wq[r] = sn * x + c * y;
+          const T u = vp[r], v = vq[r];
+          vp[r] = c * u - sn * v;
+          vq[r] = sn * u + c * v;
+        }
+        if (lane == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  if (sweep == max_sweeps && threadIdx.x == 0) rmc_report(status, RMC_ENUMERIC);
+  __syncthreads();
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    Wg[e] = W[e];
+    Vg[e] = V[e];
+  }
+}
+
 // After Jacobi on the triangular factor R of B^T (B^T = Q2 R, R = W V^T column-wise, sigma_j = ||w_j||):
 //   Ub[:, rank(j)] = V[:, j]           (left singular vectors of B, l x l, row-major)
 //   M[:, rank(j)]  = w_j / sigma_j     (so that Vb = Q2 M)
@@ -713,8 +783,10 @@ size_t gram_ws(int64_t m, int l, int num_sms) {
   return sizeof(double) * (size_t)gram_chunks(m, l, num_sms) * l * l;
 }
 
-// G (l x l FP64) = Y^T Y.
-int launch_gram(rmc_ctx *ctx, const float *Y, int64_t m, int l, int64_t ldy, double *G, double *part) {
+// G (l x l FP64) = Y^T Y; fp64_products selects FP64 products (least squares) or FP32 products with FP64
+// sums across 32-row slices (CholeskyQR2).
+int launch_gram(rmc_ctx *ctx, const float *Y, int64_t m, int l, int64_t ldy, double *G, double *part,
+                bool fp64_products = true) {
   const int T = (l + GRAM_T - 1) / GRAM_T;
   const int pairs = T * (T + 1) / 2;
   const int chunks = gram_chunks(m, l, ctx->num_sms);
@@ -722,7 +794,8 @@ int launch_gram(rmc_ctx *ctx, const float *Y, int64_t m, int l, int64_t ldy, dou
   rows = (rows + GRAM_T - 1) / GRAM_T * GRAM_T;
   {
     RmcProf prof(ctx, RMC_K_GRAM);
-    gram_f64_kernel<<<dim3(pairs, chunks), 256, 0, ctx->stream>>>(Y, m, l, ldy, rows, part);
+    if (fp64_products) gram_f64_kernel<<<dim3(pairs, chunks), 256, 0, ctx->stream>>>(Y, m, l, ldy, rows, part);
+    else gram_f32_kernel<<<dim3(pairs, chunks), 256, 0, ctx->stream>>>(Y, m, l, ldy, rows, part);
   }
   rmc_note_launch(2);
   gram_reduce_kernel<<<rmc_blocks((int64_t)l * l, 256, 1024), 256, 0, ctx->stream>>>(part, chunks, l, G);
@@ -858,7 +931,8 @@ size_t rmc_cholqr2_ws(int64_t m, int64_t l, int num_sms) {
   return w.off;
 }
 
-int rmc_launch_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l_, int64_t ldy, double *R, void *ws) {
+int rmc_launch_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l_, int64_t ldy, double *R, void *ws,
+                       int passes, bool fp64_gram) {
   const int l = (int)l_;
   cudaStream_t st = ctx->stream;
   WsCarve w;
@@ -869,8 +943,8 @@ int rmc_launch_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l_, int64_t ld
   double *R1 = w.take<double>(l * l);
   int *fail = w.take<int>(4);
   double *part = reinterpret_cast<double *>(w.take<char>(gram_ws(m, l, ctx->num_sms)));
-  for (int pass = 0; pass < 2; ++pass) {
-    RMC_TRY(launch_gram(ctx, Y, m, l, ldy, G, part));
+  for (int pass = 0; pass < passes; ++pass) {
+    RMC_TRY(launch_gram(ctx, Y, m, l, ldy, G, part, fp64_gram));
     RMC_TRY(launch_factor(ctx, G, l, Rinv, Rinv32, fail));
     RMC_TRY(launch_rowblock(st, Y, m, l, ldy, Rinv32, l, l, Y, ldy));
     if (R) {
@@ -913,18 +987,28 @@ int rmc_launch_svd_wide(rmc_ctx *ctx, const float *B, int64_t l_, int64_t n, int
   float *M = w.take<float>(l * l);
   void *rest = static_cast<char *>(ws) + ((w.off + 255) & ~size_t(255));
   RMC_TRY(rmc_launch_transpose(st, B, l, n, ldb, Bt, l));                    // B^T, n x l
-  RMC_TRY(rmc_launch_cholqr2(ctx, Bt, n, l, l, R, rest));                    // B^T = Q2 R
+  // the singular values come from R: its Gram matrices take FP64 products
+  RMC_TRY(rmc_launch_cholqr2(ctx, Bt, n, l, l, R, rest, 2, true));           // B^T = Q2 R
   RmcProf prof(ctx, RMC_K_SMALL);
   rmc_note_launch(3);
+  const size_t smem64 = 2 * sizeof(double) * (size_t)l * l, smem32 = 2 * sizeof(float) * (size_t)l * l;
   if (jacobi_in_fp64(l)) {
+    const double tol = 8 * 2.220446049250313e-16 * sqrt((double)l);
     to_colmajor_kernel<double><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, W);
-    jacobi_kernel<double><<<1, 1024, 0, st>>>(W, V, l, 8 * 2.220446049250313e-16 * sqrt((double)l), 60,
-                                               ctx->d_status);
+    jacobi_smem_kernel<double><<<1, 1024, smem64, st>>>(W, V, l, tol, 60, ctx->d_status);
     jacobi_finish_kernel<double><<<1, 256, sizeof(double) * l, st>>>(W, V, l, Ub, M, sigma);
   } else {
+    const float tol = 4 * 1.1920929e-7f * sqrtf((float)l);
     float *Wf = reinterpret_cast<float *>(W), *Vf = reinterpret_cast<float *>(V);
     to_colmajor_kernel<float><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, Wf);
-    jacobi_kernel<float><<<1, 1024, 0, st>>>(Wf, Vf, l, 4 * 1.1920929e-7f * sqrtf((float)l), 60, ctx->d_status);
+    if (smem32 <= 200 * 1024) {
+      if (smem32 > 48 * 1024)
+        RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_smem_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem32));
+      jacobi_smem_kernel<float><<<1, 1024, smem32, st>>>(Wf, Vf, l, tol, 60, ctx->d_status);
+    } else {
+      jacobi_kernel<float><<<1, 1024, 0, st>>>(Wf, Vf, l, tol, 60, ctx->d_status);
+    }
     jacobi_finish_kernel<float><<<1, 256, sizeof(double) * l, st>>>(Wf, Vf, l, Ub, M, sigma);
   }
   RMC_LAUNCH_CHECK();

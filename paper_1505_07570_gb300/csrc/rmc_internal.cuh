@@ -118,7 +118,10 @@ int rmc_launch_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int
 int rmc_launch_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X,
                          int64_t l, int64_t ldx, int prec, float *W, int64_t ldw, void *ws);
 size_t rmc_cholqr2_ws(int64_t m, int64_t l, int num_sms);
-int rmc_launch_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l, int64_t ldy, double *R, void *ws);
+// passes = 2: CholeskyQR2; passes = 1: one CholeskyQR pass (a well-conditioned, not orthonormal, basis).
+// fp64_gram: FP64 products in the Gram matrices (else FP32 products, FP64 sums across 32-row slices).
+int rmc_launch_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l, int64_t ldy, double *R, void *ws,
+                       int passes = 2, bool fp64_gram = false);
 size_t rmc_svd_wide_ws(int64_t l, int64_t n, int num_sms);
 int rmc_launch_svd_wide(rmc_ctx *ctx, const float *B, int64_t l, int64_t n, int64_t ldb, float *Ub,
                         float *sigma, float *Vb, int64_t ldv, void *ws);
