@@ -321,6 +321,9 @@ def run_ours(args, world, rank, local):
     if world == 1 and not args.no_rsvd:
         del A_h, b_h
         rsvd_info = rsvd_measure(torch, rmc)
+    batch_info = None
+    if world == 1 and not args.no_batch:
+        batch_info = batch_measure(torch, rmc)
 
     cpu = None
     if world == 1:
@@ -337,7 +340,7 @@ def run_ours(args, world, rank, local):
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernels, "kernels_isolated": isolated,
-        "rsvd": rsvd_info,
+        "rsvd": rsvd_info, "batch": batch_info,
     }
     print(json.dumps(line))
     if world > 1:
@@ -352,6 +355,10 @@ def run_probe(kind):
     import torch
     import paper_1505_07570_gb300 as rmc
     import workloads
+    if kind == "batch":
+        info = batch_measure(torch, rmc, count=512, m_range=(512, 8192), reps=2)
+        print(json.dumps({"probe": kind, "ms_per_call": info["ms"], "info": info}))
+        return 0
     A, b, _ = workloads.tall_lsr_torch(1 << 18, N_COLS, seed=SEED)
     if kind == "rsvd":
         A = workloads.factor_rank_torch(16384, 4096, 512, seed=SEED)
@@ -405,15 +412,61 @@ def rsvd_measure(torch, rmc):
     return out
 
 
+def batch_measure(torch, rmc, count=4096, m_range=(512, 32768), reps=3):
+    """The batched workload: ``count`` uneven problems (half rsvd k=16 p=8 q=1, half count-sketch least squares
+    with s = 4n; m log-uniform on m_range, n uniform on [16, 256]) in one rmc_batch_run call.  Algorithmic
+    bytes: the passes over A (2q + 2 for rsvd, one over [A, b] for least squares)."""
+    import workloads
+    specs = workloads.batch_specs(count=count, seed=SEED, m_range=m_range)
+    reqs, keep, nbytes = [], [], 0
+    for sp in specs:
+        A, b = workloads.batch_problem_torch(sp)
+        if sp["kind"] == "rsvd":
+            r, o = rmc.rsvd_request(A, sp["k"], sp["p"], sp["q"], sp["seed"])
+            nbytes += (2 + 2 * sp["q"]) * sp["m"] * sp["n"] * 4
+        else:
+            r, o = rmc.lsr_request(A, b, sp["s"], sp["seed"])
+            nbytes += sp["m"] * (sp["n"] + 1) * 4
+        reqs.append(r)
+        keep.append((A, b, o))
+    torch.cuda.synchronize()
+    rmc.rmc_batch_run(reqs)
+    rmc.rmc_sync()
+    launches0 = rmc.rmc_launch_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        rmc.rmc_batch_run(reqs)
+    e1.record()
+    rmc.rmc_sync()
+    ms = e0.elapsed_time(e1) / reps
+    launches = (rmc.rmc_launch_counter() - launches0) / reps
+    rmc.rmc_profile_begin()
+    rmc.rmc_batch_run(reqs)
+    rmc.rmc_sync()
+    _, kms = rmc.rmc_profile_read(rmc.K_BATCH)
+    rmc.rmc_profile_end()
+    hbm = peaks()["hbm_gbs"]
+    out = {"workload": "%d problems: rsvd k=16 p=8 q=1 / countsketch lsr s=4n, m log-uniform %s, n U[16,256]"
+                       % (count, list(m_range)),
+           "ms": ms, "kernel_ms": kms, "problems_per_s": count / ms * 1e3, "bytes": nbytes,
+           "gbs": nbytes / ms / 1e6, "kernel_gbs": nbytes / kms / 1e6, "frac_hbm_of_measured": nbytes / kms / 1e6 / hbm,
+           "launches_per_call": launches}
+    del keep
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--probe", choices=["countsketch", "srht", "gaussian", "lsr", "rsvd"], default=None,
+    ap.add_argument("--probe", choices=["countsketch", "srht", "gaussian", "lsr", "rsvd", "batch"], default=None,
                     help="run one small case of one kernel family (for profiler captures) and exit")
     ap.add_argument("--no-rsvd", action="store_true", help="skip the large randomized-SVD measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-problems measurement")
     args = ap.parse_args()
     if args.probe:
         return run_probe(args.probe)

@@ -169,6 +169,36 @@ int rmc_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t ld
 int rmc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X,
                   int64_t l, int64_t ldx, int prec, float *W, int64_t ldw);
 
+/* ------------------------------------------------------------------- batches of small, uneven problems */
+
+#define RMC_REQ_LSR   0   /* count-sketch sketch-and-solve least squares (Sec. 4.2 with Alg. 3.1)          */
+#define RMC_REQ_RSVD  1   /* randomized k-SVD with q power iterations (Alg. 5.2, power step of Sec. 5.1)   */
+
+/* One problem of a batch.  All pointers are device pointers owned by the caller.
+ *   LSR:  A (m x n, lda), b (m), sketch size s (n <= s <= 1024), output x (n, FP64).
+ *   RSVD: A (m x n, lda), k, p, q with l = k + p <= 32, outputs U (m x k, row stride k), sigma (k),
+ *         V (n x k, row stride k); the same algorithm and sign convention as rmc_rsvd.
+ * Limits for both: 1 <= m <= 2^24, 1 <= n <= 256, l <= min(m, n) for RSVD. */
+typedef struct rmc_request {
+  int kind;
+  int k, p, q;
+  int64_t m, n, lda, s;
+  uint64_t seed;
+  const float *A;
+  const float *b;
+  double *x;
+  float *U, *sigma, *V;
+} rmc_request;
+
+/* Run every request of the batch in ONE persistent kernel launch (the Ch. 4 and Ch. 5 problems, many at
+ * once): the host orders the requests largest first and lays out their workspace; each CTA then pulls whole
+ * problems from a device queue and runs all of a problem's passes itself, so uneven problems balance across
+ * the SMs without a launch per problem.  Results match rmc_lsr_sketch / rmc_rsvd on the same problem within
+ * the FP32 tolerances of those calls.  The descriptor array is read before the call returns.
+ * Errors: RMC_EINVAL (a request breaks the limits; nothing is enqueued), RMC_ENOMEM, RMC_ECUDA; RMC_ENUMERIC
+ * at rmc_sync when a problem's factorization broke down (its outputs are then NaN). */
+int rmc_batch_run(rmc_ctx *ctx, const rmc_request *reqs, int nreq);
+
 /* ------------------------------------------------------------------------------- measurement hooks */
 
 /* Kernel tags for rmc_profile_read. */
@@ -180,7 +210,8 @@ int rmc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t ld
 #define RMC_K_MATMUL_AT    5   /* W = X^T A                                                          */
 #define RMC_K_GRAM         6   /* FP64 Gram matrix of CholeskyQR2 / the least-squares solve          */
 #define RMC_K_SMALL        7   /* Cholesky, triangular inverse, Jacobi SVD (single-block kernels)    */
-#define RMC_K_NTAGS        8
+#define RMC_K_BATCH        8   /* persistent batch kernel of rmc_batch_run                           */
+#define RMC_K_NTAGS        9
 
 /* While profiling is on, the kernels above are bracketed by CUDA events recorded on the context's stream.
  * rmc_profile_begin clears the records; rmc_profile_read waits for the stream and returns, for one tag, the

@@ -54,7 +54,7 @@ _SIGS.update({
 })
 RMC_ESCRATCH = 8
 RMC_NOALLOC_SCRATCH_BYTES = 32 << 20
-K_COUNTSKETCH, K_SRHT, K_SRHT_REDUCE, K_GAUSSIAN, K_MATMUL_AN, K_MATMUL_AT, K_GRAM, K_SMALL = range(8)
+K_COUNTSKETCH, K_SRHT, K_SRHT_REDUCE, K_GAUSSIAN, K_MATMUL_AN, K_MATMUL_AT, K_GRAM, K_SMALL, K_BATCH = range(9)
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
     _f.argtypes = _args
@@ -314,3 +314,50 @@ def rmc_countsketch_noalloc(A, s, seed, out=None):
     _check(lib.rmc_countsketch_noalloc(_p(torch.cuda.current_stream().cuda_stream), _ptr(A), m, n, A.stride(0),
                                        s, seed, _ptr(C), C.stride(0)), "rmc_countsketch_noalloc")
     return C
+
+
+RMC_REQ_LSR, RMC_REQ_RSVD = 0, 1
+
+
+class rmc_request(ctypes.Structure):
+    """Mirror of the C struct rmc_request (include/rmc.h)."""
+    _fields_ = [("kind", _int), ("k", _int), ("p", _int), ("q", _int),
+                ("m", _i64), ("n", _i64), ("lda", _i64), ("s", _i64),
+                ("seed", _u64),
+                ("A", _p), ("b", _p), ("x", _p), ("U", _p), ("sigma", _p), ("V", _p)]
+
+
+lib.rmc_batch_run.argtypes = [_p, ctypes.POINTER(rmc_request), _int]
+lib.rmc_batch_run.restype = ctypes.c_int
+
+
+def lsr_request(A, b, s, seed):
+    """A batch request for count-sketch least squares; returns (request, x) with x the FP64 output tensor."""
+    import torch
+    _mat(A, "A")
+    m, n = A.shape
+    if not (b.is_cuda and b.dtype == torch.float32 and b.is_contiguous() and b.numel() == m):
+        raise ValueError("b must be a contiguous CUDA float32 vector of length m")
+    x = torch.empty(n, device=A.device, dtype=torch.float64)
+    r = rmc_request(kind=RMC_REQ_LSR, k=0, p=0, q=0, m=m, n=n, lda=A.stride(0), s=s, seed=seed,
+                    A=A.data_ptr(), b=b.data_ptr(), x=x.data_ptr())
+    return r, x
+
+
+def rsvd_request(A, k, p, q, seed):
+    """A batch request for the randomized k-SVD; returns (request, (U, sigma, V)) with the output tensors."""
+    import torch
+    _mat(A, "A")
+    m, n = A.shape
+    U = torch.empty(m, k, device=A.device, dtype=torch.float32)
+    sigma = torch.empty(k, device=A.device, dtype=torch.float32)
+    V = torch.empty(n, k, device=A.device, dtype=torch.float32)
+    r = rmc_request(kind=RMC_REQ_RSVD, k=k, p=p, q=q, m=m, n=n, lda=A.stride(0), s=0, seed=seed,
+                    A=A.data_ptr(), U=U.data_ptr(), sigma=sigma.data_ptr(), V=V.data_ptr())
+    return r, (U, sigma, V)
+
+
+def rmc_batch_run(requests):
+    """Run a list of rmc_request in one persistent launch on the current stream (outputs as given)."""
+    arr = (rmc_request * len(requests))(*requests)
+    _check(lib.rmc_batch_run(context().bind(), arr, len(requests)), "rmc_batch_run")

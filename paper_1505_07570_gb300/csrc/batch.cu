@@ -1,0 +1,1089 @@
+// Many small, uneven randomized least-squares and randomized-SVD problems in ONE persistent launch.
+//
+// Each CTA takes whole problems from a device queue (the host orders them largest first, so the long ones
+// start early and the short ones fill the tail) and runs every step of a problem itself:
+//   * count-sketch sketch-and-solve least squares (Sec. 4.2 with the count sketch of Algorithm 3.1):
+//     hash the rows, counting-sort them by bucket, gather [S^T A, S^T b], Gram matrix, Cholesky, then
+//     solves with two steps of iterative refinement against the sketched matrix;
+//   * the randomized k-SVD with q power iterations (Algorithm 5.2 with the power step of Sec. 5.1):
+//     Y = A Omega, one CholeskyQR pass for intermediate bases and CholeskyQR2 for the final one,
+//     B = Q^T A, B^T = Q2 R by CholeskyQR2, one-sided Jacobi on R, U = Q Ub, V = Q2 Vr.
+// A problem's A streams through shared memory in row tiles (cp.async, three stages).  Every product with
+// A is an FP32 register-tiled SIMT product out of those tiles: with l <= 32 columns in Omega there is too
+// little reuse per byte for tensor cores to matter, and the aggregate over the batch is bound by HBM.
+// Factorizations are FP32 in shared memory (FP64 Gram sums, FP64 fallback for the small Cholesky).
+
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "philox.cuh"
+#include "rmc_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
+constexpr int kStages = 3;
+constexpr int kStageFloats = 10880;  // one stage of the row-tile ring (42.5 KB)
+constexpr int kPartFloats = 12288;   // k-split partial products, the product tile, small-SVD matrices (48 KB)
+constexpr int kZFloats = 256 * 32;   // Omega / Z / B^T / Q2, n x l (32 KB)
+constexpr int kSmallFloats = 4096;   // T^-1 and R^-1 (FP32, 32 x 32) and the FP64 Gram matrix (32 x 32)
+constexpr int kSmemFloats = kStages * kStageFloats + kPartFloats + kZFloats + kSmallFloats;
+constexpr size_t kSmemBytes = sizeof(float) * kSmemFloats;
+constexpr int kMaxN = 256, kMaxL = 32, kMaxS = 1024;
+constexpr int64_t kMaxM = int64_t(1) << 24;
+
+struct BatchItem {
+  int kind, k, p, q;
+  int m, n, s, vec;   // vec: rows of A start on 16-byte boundaries (16-byte cp.async)
+  int64_t lda;
+  uint64_t seed;
+  const float *A, *b;
+  double *x;
+  float *U, *sigma, *V;
+  float *ws0;         // rsvd: Y, then Q1 (m x LP); lsr: [S^T A, S^T b] (s x n8)
+  uint32_t *ws1;      // lsr: bucket keys (m), then the row permutation (m)
+  float *ws2;         // lsr: Gram block partials
+};
+
+// ------------------------------------------------------------------------------------- small helpers
+
+__device__ __forceinline__ void cp16(float *dst, const float *src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp4(float *dst, const float *src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int C>
+__device__ __forceinline__ void ld_vec(const float *p, float (&v)[C]) {
+  if constexpr (C % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < C; i += 4) {
+      const float4 t = *reinterpret_cast<const float4 *>(p + i);
+      v[i] = t.x; v[i + 1] = t.y; v[i + 2] = t.z; v[i + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < C; i += 2) {
+      const float2 t = *reinterpret_cast<const float2 *>(p + i);
+      v[i] = t.x; v[i + 1] = t.y;
+    }
+  }
+}
+template <int C>
+__device__ __forceinline__ void st_vec(float *p, const float (&v)[C]) {
+  if constexpr (C % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < C; i += 4) *reinterpret_cast<float4 *>(p + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < C; i += 2) *reinterpret_cast<float2 *>(p + i) = make_float2(v[i], v[i + 1]);
+  }
+}
+
+__device__ __forceinline__ float f4(const float4 &a, int i) { return i == 0 ? a.x : i == 1 ? a.y : i == 2 ? a.z : a.w; }
+
+// Rows [r0, r0 + R) of a row-major matrix (leading dimension ld) into shared memory with row stride S:
+// columns [0, ncols), zeros in the padding up to the next multiple of 4 and in rows at or past `rows`.
+__device__ __forceinline__ void load_rows(float *dst, int S, const float *src, int64_t ld, int r0, int R, int rows,
+                                          int ncols, bool vec) {
+  const int nq = (ncols + 3) >> 2, total = R * nq;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    const int r = e / nq, c = (e - r * nq) << 2;
+    float *d = dst + r * S + c;
+    const bool ok = r0 + r < rows;
+    const float *s = ok ? src + (int64_t)(r0 + r) * ld + c : src;
+    const int cnt = ok ? min(4, ncols - c) : 0;
+    if (vec) {
+      cp16(d, s, cnt * 4);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) cp4(d + u, u < cnt ? s + u : src, u < cnt ? 4 : 0);
+    }
+  }
+}
+
+// Stream rows [0, rows) in tiles of R rows through the three-stage ring: load(stage, r0) issues one tile's
+// copies, use(stage, r0) consumes it (every thread takes part in both).  Loads run two tiles ahead.
+template <class Load, class Use>
+__device__ __forceinline__ void stream_tiles(float *ring, int rows, int R, Load load, Use use) {
+  const int T = (rows + R - 1) / R;
+#pragma unroll 1
+  for (int s = 0; s < 2; ++s) {
+    if (s < T) load(ring + s * kStageFloats, s * R);
+    cp_commit();
+  }
+#pragma unroll 1
+  for (int t = 0; t < T; ++t) {
+    cp_wait<1>();
+    __syncthreads();  // tile t is in; every thread is done with tile t - 1, whose stage is refilled next
+    if (t + 2 < T) load(ring + ((t + 2) % kStages) * kStageFloats, (t + 2) * R);
+    cp_commit();
+    use(ring + (t % kStages) * kStageFloats, t * R);
+  }
+  cp_wait<0>();
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------------- products out of row tiles
+
+// P[slice] (R x LP) = A_tile[:, slice's columns] Z[slice's rows, :].  Thread (slice, row quad, column group):
+// rows rq + i R/4 (i < 4), columns jg TN .. jg TN + TN - 1.
+template <int TN>
+__device__ __forceinline__ void tile_times_z(const float *At, int S, int R, int KS, int qper, int nq, const float *Z,
+                                             float *P) {
+  constexpr int LP = 4 * TN;
+  const int t = threadIdx.x;
+  if (t >= KS * R) return;
+  const int slice = t / R, u = t - slice * R;
+  const int R4 = R >> 2, rq = u >> 2, jg = u & 3;
+  const int q0 = slice * qper, q1 = min(nq, q0 + qper);
+  float acc[4][TN];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+  const float *a0 = At + rq * S;
+  const float *z0 = Z + jg * TN;
+#pragma unroll 1
+  for (int qd = q0; qd < q1; ++qd) {
+    float4 a[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4 *>(a0 + i * R4 * S + 4 * qd);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      float zv[TN];
+      ld_vec<TN>(z0 + (4 * qd + kk) * LP, zv);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float av = f4(a[i], kk);
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av, zv[j], acc[i][j]);
+      }
+    }
+  }
+  float *dst = P + slice * R * LP + jg * TN;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) st_vec<TN>(dst + (rq + i * R4) * LP, acc[i]);
+}
+
+// Sum the KS slices of P into slice 0, in slice order.
+__device__ __forceinline__ void reduce_slices(float *P, int count4, int KS) {
+  if (KS <= 1) return;
+  float4 *P4 = reinterpret_cast<float4 *>(P);
+  for (int e = threadIdx.x; e < count4; e += kThreads) {
+    float4 s = P4[e];
+    for (int sl = 1; sl < KS; ++sl) {
+      const float4 v = P4[sl * count4 + e];
+      s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+    }
+    P4[e] = s;
+  }
+}
+
+// acc += X_tile^T T_tile over the tile's rows.  Thread (jg, cq, g) owns rows jg TN .. of the result and
+// columns 4 cq .. 4 cq + 3, and takes tile rows g, g + G, ...
+template <int TN>
+__device__ __forceinline__ void xt_accum(const float *X, int LX, const float *T, int ST, int R, int nqT, int G,
+                                         float (&acc)[TN][4]) {
+  const int t = threadIdx.x, jg = t & 3, rest = t >> 2, cq = rest % nqT, g = rest / nqT;
+  if (g >= G) return;
+  const float *x = X + jg * TN, *tt = T + 4 * cq;
+#pragma unroll 2
+  for (int r = g; r < R; r += G) {
+    const float4 a = *reinterpret_cast<const float4 *>(tt + r * ST);
+    float xv[TN];
+    ld_vec<TN>(x + r * LX, xv);
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      acc[j][0] = fmaf(xv[j], a.x, acc[j][0]);
+      acc[j][1] = fmaf(xv[j], a.y, acc[j][1]);
+      acc[j][2] = fmaf(xv[j], a.z, acc[j][2]);
+      acc[j][3] = fmaf(xv[j], a.w, acc[j][3]);
+    }
+  }
+}
+
+// Write each group's accumulator to scr[g] (LP x 4 nqT, row-major).
+template <int TN>
+__device__ __forceinline__ void dump_acc(float *scr, int nqT, int G, const float (&acc)[TN][4]) {
+  constexpr int LP = 4 * TN;
+  const int t = threadIdx.x, jg = t & 3, rest = t >> 2, cq = rest % nqT, g = rest / nqT;
+  if (g >= G) return;
+  const int W4 = 4 * nqT;
+  float *d = scr + (size_t)g * LP * W4 + 4 * cq;
+#pragma unroll
+  for (int j = 0; j < TN; ++j)
+    *reinterpret_cast<float4 *>(d + (jg * TN + j) * W4) = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
+}
+
+template <int TN>
+__device__ __forceinline__ void zero_acc(float (&acc)[TN][4]) {
+#pragma unroll
+  for (int j = 0; j < TN; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+}
+template <int TN>
+__device__ __forceinline__ void add_acc(float (&tot)[TN][4], const float (&a)[TN][4]) {
+#pragma unroll
+  for (int j = 0; j < TN; ++j)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tot[j][c] += a[j][c];
+}
+
+// G64 (ld 32) = sum over the G groups of the l x l leading block of scr, in group order, in FP64.
+__device__ __forceinline__ void gram_reduce64(const float *scr, int LP, int G, int l, double *G64) {
+  for (int e = threadIdx.x; e < l * l; e += kThreads) {
+    const int i = e / l, j = e - i * l;
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) s += (double)scr[((size_t)g * LP + i) * LP + j];
+    G64[i * 32 + j] = s;
+  }
+}
+
+// ----------------------------------------------------------------------------- small factorizations
+
+// Upper Cholesky factor of the l x l matrix G64 (ld 32) and its inverse, both FP32 with ld 32 and zeros
+// outside the leading l x l block.  One warp.  FP32 first; if a pivot is not positive the factorization is
+// repeated in FP64 (in place in G64); if that fails too, R is NaN and the problem reports RMC_ENUMERIC.
+__device__ void factor_small(double *G64, int l, float *R, float *Ri, int *status) {
+  const int lane = threadIdx.x & 31;
+  for (int i = 0; i < 32; ++i) R[i * 32 + lane] = (i < l && lane < l && lane >= i) ? (float)G64[i * 32 + lane] : 0.f;
+  __syncwarp();
+  bool ok = true;
+  for (int k = 0; k < l; ++k) {
+    const float d = R[k * 32 + k];
+    if (!(d > 0.f) || !(d < INFINITY)) { ok = false; break; }
+    const float rd = sqrtf(d);
+    const float rkj = (lane > k && lane < l) ? R[k * 32 + lane] / rd : 0.f;
+    __syncwarp();
+    if (lane == k) R[k * 32 + k] = rd;
+    if (lane > k && lane < l) R[k * 32 + lane] = rkj;
+    __syncwarp();
+    if (lane > k && lane < l)
+      for (int i = k + 1; i <= lane; ++i) R[i * 32 + lane] -= R[k * 32 + i] * rkj;
+    __syncwarp();
+  }
+  if (!ok) {
+    // FP64 retry, in place in G64's upper triangle
+    ok = true;
+    for (int k = 0; k < l; ++k) {
+      const double d = G64[k * 32 + k];
+      if (!(d > 0.0) || !(d < INFINITY)) { ok = false; break; }
+      const double rd = sqrt(d);
+      const double rkj = (lane > k && lane < l) ? G64[k * 32 + lane] / rd : 0.0;
+      __syncwarp();
+      if (lane == k) G64[k * 32 + k] = rd;
+      if (lane > k && lane < l) G64[k * 32 + lane] = rkj;
+      __syncwarp();
+      if (lane > k && lane < l)
+        for (int i = k + 1; i <= lane; ++i) G64[i * 32 + lane] -= G64[k * 32 + i] * rkj;
+      __syncwarp();
+    }
+    for (int i = 0; i < 32; ++i)
+      R[i * 32 + lane] = (i < l && lane < l && lane >= i) ? (ok ? (float)G64[i * 32 + lane] : nanf("")) : 0.f;
+    __syncwarp();
+    if (!ok && lane == 0) rmc_report(status, RMC_ENUMERIC);
+  }
+  // inverse, column `lane`: R x = e_lane by back substitution
+  for (int i = 31; i >= 0; --i) {
+    float v = 0.f;
+    if (lane < l && i <= lane) {
+      float s = (i == lane) ? 1.f : 0.f;
+      for (int c = i + 1; c <= lane; ++c) s -= R[i * 32 + c] * Ri[c * 32 + lane];
+      v = s / R[i * 32 + i];
+    }
+    Ri[i * 32 + lane] = v;
+  }
+  __syncwarp();
+}
+
+// X[r, :] <- X[r, :] M for rows r < rows (LP columns, row stride LP).  M is 32 x 32 (ld 32) with zeros
+// outside its leading l x l block; `upper` skips its zero lower triangle.
+template <int TN, bool upper>
+__device__ __forceinline__ void rows_times(float *X, int rows, const float *M) {
+  constexpr int LP = 4 * TN;
+  const volatile float *Mv = M;  // volatile: keeps the compiler from hoisting all of M into registers
+  for (int r = threadIdx.x; r < rows; r += kThreads) {
+    float v[LP];
+    ld_vec<LP>(X + r * LP, v);
+#pragma unroll
+    for (int j = 0; j < LP; ++j) {
+      float s = 0.f;
+#pragma unroll
+      for (int i = 0; i < LP; ++i)
+        if (!upper || i <= j) s = fmaf(v[i], Mv[i * 32 + j], s);
+      X[r * LP + j] = s;  // the row's inputs are all in registers already
+    }
+  }
+}
+
+// One-sided Jacobi on W (l x l, column j at W + 32 j), rotations accumulated into V; round-robin pairing,
+// one warp per column pair.  Rotation of the one-sided (Hestenes) method with correctly rounded reciprocal
+// and square root so that c^2 + s^2 does not drift below 1.
+__device__ void jacobi_small(float *W, float *V, int l, int *flag, int *status) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < 1024; e += kThreads) V[e] = ((e >> 5) == (e & 31) && (e & 31) < l) ? 1.f : 0.f;
+  const int lp = (l + 1) & ~1;
+  const float tol = 4.f * 1.1920929e-7f * sqrtf((float)l);
+  int sweep = 0;
+  for (; sweep < 60; ++sweep) {
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    for (int round = 0; round < lp - 1; ++round) {
+      if (warp < lp / 2) {
+        const int a = warp, b = lp - 1 - warp;
+        int p = a == 0 ? 0 : 1 + (a - 1 + round) % (lp - 1);
+        int q = b == 0 ? 0 : 1 + (b - 1 + round) % (lp - 1);
+        if (p > q) { const int t = p; p = q; q = t; }
+        if (q < l) {
+          float *wp = W + 32 * p, *wq = W + 32 * q;
+          const float x = lane < l ? wp[lane] : 0.f, y = lane < l ? wq[lane] : 0.f;
+          float alpha = x * x, beta = y * y, gamma = x * y;
+#pragma unroll
+          for (int o = 16; o; o >>= 1) {
+            alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+            beta += __shfl_xor_sync(0xffffffffu, beta, o);
+            gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
+          }
+          if (gamma != 0.f && fabsf(gamma) > tol * sqrtf(alpha * beta)) {
+            const float zeta = (beta - alpha) * __frcp_rn(2.f * gamma);
+            const float tt = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + __fsqrt_rn(fmaf(zeta, zeta, 1.f)));
+            const float c = __frcp_rn(__fsqrt_rn(fmaf(tt, tt, 1.f))), s = c * tt;
+            if (lane < l) {
+              wp[lane] = c * x - s * y;
+              wq[lane] = s * x + c * y;
+              float *vp = V + 32 * p, *vq = V + 32 * q;
+              const float u = vp[lane], v = vq[lane];
+              vp[lane] = c * u - s * v;
+              vq[lane] = s * u + c * v;
+            }
+            if (lane == 0) *flag = 1;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    const int rotated = *flag;
+    __syncthreads();
+    if (!rotated) break;
+  }
+  if (sweep == 60 && threadIdx.x == 0) rmc_report(status, RMC_ENUMERIC);
+}
+
+// ------------------------------------------------------------------------------------- rsvd problem
+
+struct RsvdGeo {
+  int m, n, n4, nq, S, R, KS, qper, GY, GW, R2;
+};
+
+template <int TN>
+__device__ void rsvd_problem(const BatchItem &it, float *sm, int *flag, int *status) {
+  constexpr int LP = 4 * TN;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int l = it.k + it.p, k = it.k;
+  RsvdGeo g;
+  g.m = it.m;
+  g.n = it.n;
+  g.n4 = (g.n + 3) & ~3;
+  g.nq = g.n4 >> 2;
+  g.S = (g.n4 & 7) ? g.n4 : g.n4 + 4;  // row stride of A tiles: 4 mod 8, so 8 rows hit 8 different bank quads
+  g.R = min(256, kStageFloats / (g.S + LP)) & ~3;
+  g.KS = max(1, min(kThreads / g.R, kPartFloats / (g.R * LP)));
+  g.qper = (g.nq + g.KS - 1) / g.KS;
+  g.KS = (g.nq + g.qper - 1) / g.qper;
+  g.GY = kThreads / LP;          // row groups of the Gram accumulation (4 TN threads per group)
+  g.GW = kThreads / (4 * g.nq);  // row groups of the X^T A accumulation
+  g.R2 = min(256, kStageFloats / LP) & ~3;
+
+  float *ring = sm;
+  float *P = sm + kStages * kStageFloats;
+  float *Z = P + kPartFloats;
+  float *Tinv = Z + kZFloats;
+  float *Ri = Tinv + 1024;
+  double *G64 = reinterpret_cast<double *>(Ri + 1024);
+  float *Yg = it.ws0;
+  const float *A = it.A;
+  const int64_t lda = it.lda;
+  const bool vec = it.vec != 0;
+
+  // Omega (n x l): Gaussian block (r, c/4) of the same Philox stream as the single-problem path
+  for (int e = t; e < g.n4 * LP; e += kThreads) Z[e] = 0.f;
+  __syncthreads();
+  {
+    const int gl = (l + 3) >> 2;
+    for (int e = t; e < g.n * gl; e += kThreads) {
+      const int r = e / gl, cq = e - r * gl;
+      const float4 z = rmc::gaussian4(it.seed, 0, (uint64_t)e);
+      const float v[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (4 * cq + c < l) Z[r * LP + 4 * cq + c] = v[c];
+    }
+  }
+  __syncthreads();
+
+  // Gram matrix of the rows streamed by the last pass -> G64 -> R, R^-1 (warp 0)
+  auto finish_gram = [&](const float (&acc)[TN][4], float *Rout, float *Riout) {
+    dump_acc<TN>(ring, TN, g.GY, acc);
+    __syncthreads();
+    gram_reduce64(ring, LP, g.GY, l, G64);
+    __syncthreads();
+    if (warp == 0) factor_small(G64, l, Rout, Riout, status);
+    __syncthreads();
+  };
+
+  // Y = A Z (written to Yg) with the Gram matrix of Y accumulated on the way
+  auto y_pass = [&](float *Rout, float *Riout) {
+    float gtot[TN][4];
+    zero_acc<TN>(gtot);
+    stream_tiles(
+        ring, g.m, g.R,
+        [&](float *st, int r0) { load_rows(st, g.S, A, lda, r0, g.R, g.m, g.n, vec); },
+        [&](float *st, int r0) {
+          tile_times_z<TN>(st, g.S, g.R, g.KS, g.qper, g.nq, Z, P);
+          __syncthreads();
+          reduce_slices(P, g.R * LP / 4, g.KS);
+          __syncthreads();
+          const int rv = min(g.R, g.m - r0);
+          float4 *dst = reinterpret_cast<float4 *>(Yg + (size_t)r0 * LP);
+          const float4 *src = reinterpret_cast<const float4 *>(P);
+          for (int e = t; e < rv * LP / 4; e += kThreads) dst[e] = src[e];
+          float gt[TN][4];
+          zero_acc<TN>(gt);
+          xt_accum<TN>(P, LP, P, LP, g.R, TN, g.GY, gt);
+          add_acc<TN>(gtot, gt);
+        });
+    finish_gram(gtot, Rout, Riout);
+  };
+
+  // Second CholeskyQR pass over Yg: Q1 = Y R1^-1 written back in place, Gram matrix of Q1 accumulated
+  auto q_pass = [&](const float *R1i, float *Rout, float *Riout) {
+    float gtot[TN][4];
+    zero_acc<TN>(gtot);
+    stream_tiles(
+        ring, g.m, g.R2,
+        [&](float *st, int r0) { load_rows(st, LP, Yg, LP, r0, g.R2, g.m, LP, true); },
+        [&](float *st, int r0) {
+          const int rv = min(g.R2, g.m - r0);
+          rows_times<TN, true>(st, rv, R1i);
+          __syncthreads();
+          float4 *dst = reinterpret_cast<float4 *>(Yg + (size_t)r0 * LP);
+          const float4 *src = reinterpret_cast<const float4 *>(st);
+          for (int e = t; e < rv * LP / 4; e += kThreads) dst[e] = src[e];
+          float gt[TN][4];
+          zero_acc<TN>(gt);
+          xt_accum<TN>(st, LP, st, LP, g.R2, TN, g.GY, gt);
+          add_acc<TN>(gtot, gt);
+        });
+    finish_gram(gtot, Rout, Riout);
+  };
+
+  // Z = (Yg Tinv)^T A transposed, i.e. Z[c][i] = sum_j Tinv[j][i] (Yg^T A)[j][c]  (n x l)
+  auto w_pass = [&]() {
+    float wtot[TN][4];
+    zero_acc<TN>(wtot);
+    stream_tiles(
+        ring, g.m, g.R,
+        [&](float *st, int r0) {
+          load_rows(st, g.S, A, lda, r0, g.R, g.m, g.n, vec);
+          load_rows(st + g.R * g.S, LP, Yg, LP, r0, g.R, g.m, LP, true);
+        },
+        [&](float *st, int r0) {
+          float wt[TN][4];
+          zero_acc<TN>(wt);
+          xt_accum<TN>(st + g.R * g.S, LP, st, g.S, g.R, g.nq, g.GW, wt);
+          add_acc<TN>(wtot, wt);
+        });
+    dump_acc<TN>(ring, g.nq, g.GW, wtot);
+    __syncthreads();
+    // W (LP x n4) = sum over groups, into P
+    for (int e = t; e < LP * g.n4; e += kThreads) {
+      float s = 0.f;
+      for (int gg = 0; gg < g.GW; ++gg) s += ring[(size_t)gg * LP * g.n4 + e];
+      P[e] = s;
+    }
+    __syncthreads();
+    for (int e = t; e < g.n4 * LP; e += kThreads) {
+      const int c = e / LP, i = e - c * LP;
+      float s = 0.f;
+      for (int j = 0; j <= i && j < l; ++j) s = fmaf(Tinv[j * 32 + i], P[j * g.n4 + c], s);
+      Z[c * LP + i] = s;
+    }
+    __syncthreads();
+  };
+
+  // one CholeskyQR pass on Z (n4 x LP, in shared memory): Z <- Z R^-1, R kept in Rout
+  auto z_cholqr = [&](float *Rout) {
+    float acc[TN][4];
+    zero_acc<TN>(acc);
+    xt_accum<TN>(Z, LP, Z, LP, g.n4, TN, g.GY, acc);
+    finish_gram(acc, Rout, Ri);
+    rows_times<TN, true>(Z, g.n4, Ri);
+    __syncthreads();
+  };
+
+  float *Rscr = P;  // R factors of the CholeskyQR passes that are not kept
+  // ---- range finder
+  y_pass(Rscr, Ri);  // Y = A Omega; R1^-1 in Ri
+  if (it.q == 0) {
+    for (int e = t; e < 1024; e += kThreads) Tinv[e] = Ri[e];
+    __syncthreads();
+    q_pass(Tinv, Rscr, Ri);  // Q1 = Y R1^-1; R2^-1 in Ri
+    for (int e = t; e < 1024; e += kThreads) Tinv[e] = Ri[e];
+    __syncthreads();
+  } else {
+    for (int e = t; e < 1024; e += kThreads) Tinv[e] = Ri[e];
+    __syncthreads();
+  }
+  for (int itn = 0; itn < it.q; ++itn) {
+    w_pass();          // Z = (Q^T A)^T
+    z_cholqr(Rscr);    // Z = orth(A^T Q)
+    y_pass(Rscr, Ri);  // Y = A Z
+    for (int e = t; e < 1024; e += kThreads) Tinv[e] = Ri[e];
+    __syncthreads();
+    if (itn == it.q - 1) {
+      q_pass(Tinv, Rscr, Ri);
+      for (int e = t; e < 1024; e += kThreads) Tinv[e] = Ri[e];
+      __syncthreads();
+    }
+  }
+  w_pass();  // Z = B^T = (Q^T A)^T, n x l
+
+  // ---- small SVD: B^T = Q2 R by CholeskyQR2, R = W V^T by one-sided Jacobi
+  float *Ra = P, *Rb = P + 1024, *W = P + 2048, *V = P + 3072, *Ub = P + 4096, *M = P + 5120;
+  float *Ms = P + 6144;
+  double *sg = reinterpret_cast<double *>(P + 7168);
+  float *sgs = P + 7232;
+  z_cholqr(Ra);
+  z_cholqr(Rb);
+  // W = R = Rb Ra, column j at W + 32 j
+  for (int e = t; e < 1024; e += kThreads) {
+    const int j = e >> 5, i = e & 31;
+    float s = 0.f;
+    if (i < l && j < l)
+      for (int c = i; c <= j; ++c) s = fmaf(Rb[i * 32 + c], Ra[c * 32 + j], s);
+    W[j * 32 + i] = s;
+  }
+  __syncthreads();
+  jacobi_small(W, V, l, flag, status);
+  for (int j = t; j < 32; j += kThreads) {
+    double s = 0.0;
+    for (int r = 0; r < l; ++r) s += (double)W[j * 32 + r] * (double)W[j * 32 + r];
+    sg[j] = j < l ? sqrt(s) : 0.0;
+  }
+  for (int e = t; e < 1024; e += kThreads) Ub[e] = M[e] = 0.f;
+  __syncthreads();
+  // Ub[:, rank j] = V[:, j], M[:, rank j] = w_j / sigma_j, sigma descending (ties by index)
+  for (int j = t; j < l; j += kThreads) {
+    int rank = 0;
+    for (int u = 0; u < l; ++u) rank += (sg[u] > sg[j]) || (sg[u] == sg[j] && u < j);
+    sgs[rank] = (float)sg[j];
+    const double inv = sg[j] > 0 ? 1.0 / sg[j] : 0.0;
+    for (int r = 0; r < l; ++r) {
+      Ub[r * 32 + rank] = V[j * 32 + r];
+      M[r * 32 + rank] = (float)((double)W[j * 32 + r] * inv);
+    }
+  }
+  __syncthreads();
+  rows_times<TN, false>(Z, g.n4, M);  // Vb = Q2 M
+  __syncthreads();
+  // signs: the entry of largest magnitude of Vb[:, i] (first on ties) is made positive
+  for (int e = t; e < 1024; e += kThreads) Ms[e] = 0.f;
+  __syncthreads();
+  for (int i = warp; i < k; i += kWarps) {
+    float best = -1.f;
+    int where = 0;
+    for (int r = lane; r < g.n; r += 32) {
+      const float v = fabsf(Z[r * LP + i]);
+      if (v > best) { best = v; where = r; }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const float b2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int w2 = __shfl_xor_sync(0xffffffffu, where, o);
+      if (b2 > best || (b2 == best && w2 < where)) { best = b2; where = w2; }
+    }
+    const float sgn = Z[where * LP + i] < 0.f ? -1.f : 1.f;
+    for (int r = lane; r < g.n; r += 32) it.V[(int64_t)r * k + i] = sgn * Z[r * LP + i];
+    if (lane < l) Ms[lane * 32 + i] = sgn * Ub[lane * 32 + i];
+    if (lane == 0) it.sigma[i] = sgs[i];
+  }
+  __syncthreads();
+  // U = Q1 Tinv Ms: fold Tinv Ms (l x k) into Ri, then one pass over Q1
+  for (int e = t; e < 1024; e += kThreads) {
+    const int r = e >> 5, c = e & 31;
+    float s = 0.f;
+    if (r < l && c < k)
+      for (int i = r; i < l; ++i) s = fmaf(Tinv[r * 32 + i], Ms[i * 32 + c], s);
+    Ri[e] = s;
+  }
+  __syncthreads();
+  stream_tiles(
+      ring, g.m, g.R2, [&](float *st, int r0) { load_rows(st, LP, Yg, LP, r0, g.R2, g.m, LP, true); },
+      [&](float *st, int r0) {
+        const int rv = min(g.R2, g.m - r0);
+        for (int e = t; e < rv * k; e += kThreads) {
+          const int r = e / k, c = e - r * k;
+          float s = 0.f;
+#pragma unroll
+          for (int i = 0; i < LP; ++i) s = fmaf(st[r * LP + i], Ri[i * 32 + c], s);
+          it.U[(int64_t)(r0 + r) * k + c] = s;
+        }
+      });
+}
+
+// -------------------------------------------------------------------------------------- lsr problem
+
+// Packed upper triangle of an nn x nn matrix: row i holds columns i .. nn-1.
+__device__ __forceinline__ int poff(int i, int nn) { return i * nn - (i * (i - 1)) / 2; }
+
+// Block exclusive scan of one int per thread; returns the prefix, total in *total.
+__device__ __forceinline__ int block_scan(int v, int *wsum, int *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < kWarps ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kWarps) wsum[lane] = w;
+  }
+  __syncthreads();
+  const int before = (warp ? wsum[warp - 1] : 0) + x - v;
+  if (total) *total = wsum[kWarps - 1];
+  __syncthreads();
+  return before;
+}
+
+// Triangular solves with the packed factor (row stride nn = n + 1) by one warp; index c lives in lane c % 32,
+// slot c / 32.  forward: R^T y = rhs; backward: R x = rhs.  Result to out (shared memory).
+template <bool forward>
+__device__ void packed_solve(const float *Pk, int n, int nn, const float *rhs, float *out) {
+  const int lane = threadIdx.x & 31;
+  float rr[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int c = lane + 32 * u;
+    rr[u] = c < n ? rhs[c] : 0.f;
+  }
+  if (forward) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (32 * u >= n) break;
+      for (int ii = 0; ii < 32; ++ii) {
+        const int i = 32 * u + ii;
+        if (i >= n) break;
+        const int oi = poff(i, nn);
+        const float yi = __shfl_sync(0xffffffffu, rr[u], ii) / Pk[oi];
+        if (lane == ii) out[i] = yi;
+#pragma unroll
+        for (int u2 = u; u2 < 8; ++u2) {
+          const int c = lane + 32 * u2;
+          if (c > i && c < n) rr[u2] = fmaf(-Pk[oi + c - i], yi, rr[u2]);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int u = 7; u >= 0; --u) {
+      if (32 * u >= n) continue;
+      for (int ii = 31; ii >= 0; --ii) {
+        const int i = 32 * u + ii;
+        if (i >= n) continue;
+        const float xi = __shfl_sync(0xffffffffu, rr[u], ii) / Pk[poff(i, nn)];
+        if (lane == ii) out[i] = xi;
+#pragma unroll
+        for (int u2 = 0; u2 <= u; ++u2) {
+          const int c = lane + 32 * u2;
+          if (c < i) rr[u2] = fmaf(-Pk[poff(c, nn) + i - c], xi, rr[u2]);
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
+__device__ void lsr_problem(const BatchItem &it, float *sm, int *wsum, int *status) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int m = it.m, n = it.n, s = it.s, n1 = n + 1, n8 = (n1 + 7) & ~7;
+  const float *A = it.A, *bv = it.b;
+  const int64_t lda = it.lda;
+  float *SAb = it.ws0;
+  uint32_t *keys = it.ws1, *perm = it.ws1 + m;
+
+  // ---- 1. hash every row; per-warp bucket histograms (warp w takes rows [w chunk, (w+1) chunk))
+  int *hs = reinterpret_cast<int *>(sm);  // hs[b * 16 + w]
+  int *bstart = hs + kWarps * kMaxS;
+  for (int e = t; e < kWarps * s; e += kThreads) hs[e] = 0;
+  __syncthreads();
+  const int chunk = (m + kWarps - 1) / kWarps;
+  const int lo = min(m, warp * chunk), hi = min(m, lo + chunk);
+  for (int i = lo + lane; i < hi; i += 32) {
+    uint32_t b;
+    float sg;
+    rmc::cs_hash(it.seed, 0, (uint64_t)i, (uint32_t)s, &b, &sg);
+    keys[i] = b | (sg < 0.f ? 0x80000000u : 0u);
+    atomicAdd(&hs[b * kWarps + warp], 1);
+  }
+  __syncthreads();
+  // ---- 2. exclusive scan in (bucket, warp) order: the start of each warp's run inside each bucket
+  {
+    const int tot = kWarps * s, per = (tot + kThreads - 1) / kThreads;
+    const int a = min(tot, t * per), z = min(tot, a + per);
+    int sum = 0;
+    for (int e = a; e < z; ++e) sum += hs[e];
+    int run = block_scan(sum, wsum, nullptr);
+    for (int e = a; e < z; ++e) {
+      const int v = hs[e];
+      hs[e] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  for (int b = t; b < s; b += kThreads) bstart[b] = hs[b * kWarps];
+  if (t == 0) bstart[s] = m;
+  __syncthreads();
+  // ---- 3. stable placement: rows of a bucket in increasing order
+  for (int base = lo; base < hi; base += 32) {
+    const int i = base + lane;
+    const bool v = i < hi;
+    const uint32_t key = v ? keys[i] : 0xFFFFFFFFu;
+    const uint32_t b = key & 0x7FFFFFFFu;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (v) perm[hs[b * kWarps + warp] + rank] = (uint32_t)i | (key & 0x80000000u);
+    __syncwarp();
+    if (v && rank == 0) hs[b * kWarps + warp] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // ---- 4. gather: row b of [S^T A, S^T b] = signed sum of the rows hashed to bucket b (one warp per bucket)
+  for (int b = warp; b < s; b += kWarps) {
+    const int p0 = bstart[b], p1 = bstart[b + 1];
+    float acc[9];
+#pragma unroll
+    for (int u = 0; u < 9; ++u) acc[u] = 0.f;
+    for (int p = p0; p < p1; p += 4) {
+      float va[4][9];
+      float sgn[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool ok = p + j < p1;
+        const uint32_t e = ok ? perm[p + j] : 0u;
+        const int row = (int)(e & 0x7FFFFFFFu);
+        sgn[j] = ok ? ((e >> 31) ? -1.f : 1.f) : 0.f;
+        const float *ar = A + (int64_t)row * lda;
+#pragma unroll
+        for (int u = 0; u < 9; ++u) {
+          const int c = lane + 32 * u;
+          va[j][u] = !ok ? 0.f : c < n ? __ldg(ar + c) : c == n ? __ldg(bv + row) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int u = 0; u < 9; ++u) acc[u] = fmaf(sgn[j], va[j][u], acc[u]);
+    }
+    float *d = SAb + (size_t)b * n8;
+#pragma unroll
+    for (int u = 0; u < 9; ++u) {
+      const int c = lane + 32 * u;
+      if (c < n8) d[c] = c < n1 ? acc[u] : 0.f;
+    }
+  }
+  __syncthreads();
+  // ---- 5. augmented Gram matrix [SA, Sb]^T [SA, Sb] in 8 x 8 blocks (FP32), block partials to ws2
+  const int nbk = n8 >> 3, blocks = nbk * (nbk + 1) / 2;
+  const int splits = max(1, kThreads / blocks), items = blocks * splits;
+  const int CR = min(s, kStageFloats / n8);
+  for (int round = 0; round * kThreads < items; ++round) {
+    const int item = round * kThreads + t;
+    const bool active = item < items;
+    const int sp = active ? item / blocks : 0, blk = active ? item - (item / blocks) * blocks : 0;
+    int bi = 0, rem = blk;
+    while (rem >= nbk - bi) { rem -= nbk - bi; ++bi; }
+    const int bj = bi + rem;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    stream_tiles(
+        sm, s, CR, [&](float *st, int r0) { load_rows(st, n8, SAb, n8, r0, CR, s, n8, true); },
+        [&](float *st, int r0) {
+          if (!active) return;
+          const int rv = min(CR, s - r0);
+          for (int r = (sp - r0 % splits + splits) % splits; r < rv; r += splits) {
+            const float *row = st + r * n8;
+            const float4 x0 = *reinterpret_cast<const float4 *>(row + 8 * bi);
+            const float4 x1 = *reinterpret_cast<const float4 *>(row + 8 * bi + 4);
+            const float4 y0 = *reinterpret_cast<const float4 *>(row + 8 * bj);
+            const float4 y1 = *reinterpret_cast<const float4 *>(row + 8 * bj + 4);
+            const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            const float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+              for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(xv[i], yv[j], acc[i][j]);
+          }
+        });
+    if (active) {
+      float4 *d = reinterpret_cast<float4 *>(it.ws2 + (size_t)item * 64);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        d[2 * i] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        d[2 * i + 1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+      }
+    }
+  }
+  __syncthreads();
+  float *Pk = sm;  // packed upper triangle of the (n+1) x (n+1) augmented Gram matrix
+  for (int i = warp; i < n1; i += kWarps) {
+    const int bi = i >> 3, o = poff(i, n1);
+    for (int j = i + lane; j < n1; j += 32) {
+      const int bj = j >> 3;
+      const int blk = bi * nbk - (bi * (bi - 1)) / 2 + (bj - bi);
+      float v = 0.f;
+      for (int sp = 0; sp < splits; ++sp) v += it.ws2[((size_t)sp * blocks + blk) * 64 + (i & 7) * 8 + (j & 7)];
+      Pk[o + j - i] = v;
+    }
+  }
+  __syncthreads();
+  // ---- 6. right-looking Cholesky of the leading n x n block; the augmented column becomes R^-T S^T A^T S b
+  float *vecs = sm + ((poff(n1, n1) + 63) & ~31);
+  float *y = vecs, *xf = vecs + 288, *rres = vecs + 576, *gp = rres + kMaxS;
+  double *x64 = reinterpret_cast<double *>(gp + 2 * 288);
+  bool ok = true;
+  float dprev = 0.f;
+  for (int kk = 0; kk < n; ++kk) {
+    const float d = Pk[poff(kk, n1)];
+    if (!(d > 0.f) || !(d < INFINITY)) { ok = false; break; }
+    if (kk > 0) {
+      const int o = poff(kk - 1, n1);
+      const float rd = sqrtf(dprev), inv = 1.f / rd;
+      for (int c = kk - 1 + t; c <= n; c += kThreads) Pk[o + c - (kk - 1)] = (c == kk - 1) ? rd : Pk[o + c - (kk - 1)] * inv;
+    }
+    const float invd = 1.f / d;
+    const int ok_ = poff(kk, n1);
+    for (int i = kk + 1 + warp; i < n; i += kWarps) {
+      const float f = Pk[ok_ + i - kk] * invd;
+      const int oi = poff(i, n1);
+      for (int c = i + lane; c <= n; c += 32) Pk[oi + c - i] = fmaf(-f, Pk[ok_ + c - kk], Pk[oi + c - i]);
+    }
+    dprev = d;
+    __syncthreads();
+  }
+  if (ok) {
+    const int o = poff(n - 1, n1);
+    const float rd = sqrtf(dprev), inv = 1.f / rd;
+    for (int c = n - 1 + t; c <= n; c += kThreads) Pk[o + c - (n - 1)] = (c == n - 1) ? rd : Pk[o + c - (n - 1)] * inv;
+  }
+  __syncthreads();
+  if (!ok) {
+    for (int c = t; c < n; c += kThreads) it.x[c] = nan("");
+    if (t == 0) rmc_report(status, RMC_ENUMERIC);
+    return;
+  }
+  // ---- 7. x0 = R^-1 (augmented column), then two refinement steps against [SA, Sb]:
+  //         r = Sb - SA x, dx = (R^T R)^-1 SA^T r
+  for (int i = t; i < n; i += kThreads) y[i] = Pk[poff(i, n1) + n - i];
+  __syncthreads();
+  if (warp == 0) packed_solve<false>(Pk, n, n1, y, xf);
+  __syncthreads();
+  for (int i = t; i < n; i += kThreads) x64[i] = xf[i];
+  __syncthreads();
+  for (int iter = 0; iter < 2; ++iter) {
+    for (int i = warp; i < s; i += kWarps) {
+      const float *row = SAb + (size_t)i * n8;
+      float acc = 0.f;
+      for (int c = lane; c < n; c += 32) acc = fmaf(row[c], xf[c], acc);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) rres[i] = row[n] - acc;
+    }
+    __syncthreads();
+    {
+      const int c = t & 255, h = t >> 8;
+      if (c < n) {
+        float acc = 0.f;
+        for (int i = h; i < s; i += 2) acc = fmaf(SAb[(size_t)i * n8 + c], rres[i], acc);
+        gp[h * 288 + c] = acc;
+      }
+    }
+    __syncthreads();
+    for (int c = t; c < n; c += kThreads) rres[c] = gp[c] + gp[288 + c];  // reuse: SA^T r
+    __syncthreads();
+    if (warp == 0) {
+      packed_solve<true>(Pk, n, n1, rres, y);
+      packed_solve<false>(Pk, n, n1, y, gp);
+    }
+    __syncthreads();
+    for (int c = t; c < n; c += kThreads) {
+      x64[c] += (double)gp[c];
+      xf[c] = (float)x64[c];
+    }
+    __syncthreads();
+  }
+  for (int c = t; c < n; c += kThreads) it.x[c] = x64[c];
+}
+
+// ------------------------------------------------------------------------------------------- kernel
+
+__global__ void __launch_bounds__(kThreads, 1)
+    batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ order, int nitems, int *next,
+                 int *status) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ int s_item, s_flag;
+  __shared__ int s_wsum[kWarps];
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int w = s_item;
+    __syncthreads();
+    if (w >= nitems) break;
+    const BatchItem it = items[order[w]];
+    if (it.kind == RMC_REQ_LSR) {
+      lsr_problem(it, sm, s_wsum, status);
+    } else {
+      const int l = it.k + it.p;
+      if (l <= 8) rsvd_problem<2>(it, sm, &s_flag, status);
+      else if (l <= 16) rsvd_problem<4>(it, sm, &s_flag, status);
+      else if (l <= 24) rsvd_problem<6>(it, sm, &s_flag, status);
+      else rsvd_problem<8>(it, sm, &s_flag, status);
+    }
+    __syncthreads();
+  }
+}
+
+static int lp_of(int l) { return (l + 7) & ~7; }
+
+// Rough per-problem cost in microseconds of one SM: streamed bytes at ~40 GB/s or FP32 FMAs at ~60% of one
+// SM's rate, plus the fixed tail (small factorizations).  Only the ORDER matters (largest first).
+static double cost_us(const rmc_request &r) {
+  const double m = (double)r.m, n = (double)r.n;
+  if (r.kind == RMC_REQ_LSR) {
+    const double bytes = m * (n + 1) * 4 + 16 * m;
+    const double fma = (double)r.s * (n + 8) * (n + 8) / 2 + 4 * (double)r.s * n + n * n * n / 6;
+    return std::max(bytes / 4.0e4, fma / 1.5e5) + 0.2 * n;
+  }
+  const int lp = lp_of(r.k + r.p);
+  const double passes = 2.0 + 2.0 * r.q;
+  const double bytes = passes * m * n * 4 + (3.0 + r.q) * m * lp * 8;
+  const double fma = passes * m * n * lp + (2.0 + r.q) * m * lp * lp;
+  return std::max(bytes / 4.0e4, fma / 1.5e5) + 40.0;
+}
+
+static bool bad_request(const rmc_request &r) {
+  if (!r.A || r.m < 1 || r.m > kMaxM || r.n < 1 || r.n > kMaxN || r.lda < r.n) return true;
+  if (r.kind == RMC_REQ_LSR) return !r.b || !r.x || r.s < r.n || r.s > kMaxS;
+  if (r.kind == RMC_REQ_RSVD) {
+    const int64_t l = int64_t(r.k) + r.p;
+    return !r.U || !r.sigma || !r.V || r.k < 1 || r.p < 0 || r.q < 0 || r.q > 64 || l > kMaxL || l > r.n || l > r.m;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" int rmc_batch_run(rmc_ctx *ctx, const rmc_request *reqs, int nreq) {
+  if (!ctx || nreq < 0 || (nreq > 0 && !reqs)) return RMC_EINVAL;
+  if (nreq == 0) return RMC_OK;
+  for (int i = 0; i < nreq; ++i)
+    if (bad_request(reqs[i])) return RMC_EINVAL;
+
+  std::vector<int> order(nreq);
+  std::vector<double> cost(nreq);
+  for (int i = 0; i < nreq; ++i) {
+    order[i] = i;
+    cost[i] = cost_us(reqs[i]);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+
+  // workspace: descriptors, order, queue counter, then each problem's buffers
+  std::vector<BatchItem> host(nreq);
+  BatchItem *d_items = nullptr;
+  int *d_order = nullptr, *d_next = nullptr;
+  auto carve = [&](WsCarve &w) {
+    d_items = w.take<BatchItem>(nreq);
+    d_order = w.take<int>(nreq);
+    d_next = w.take<int>(1);
+    for (int i = 0; i < nreq; ++i) {
+      const rmc_request &r = reqs[i];
+      BatchItem &b = host[i];
+      b.ws0 = nullptr;
+      b.ws1 = nullptr;
+      b.ws2 = nullptr;
+      if (r.kind == RMC_REQ_RSVD) {
+        b.ws0 = w.take<float>(size_t(r.m) * lp_of(r.k + r.p));
+      } else {
+        const int n8 = (int(r.n) + 8) & ~7;
+        const int nbk = n8 / 8, blocks = nbk * (nbk + 1) / 2;
+        const int items = blocks * std::max(1, kThreads / blocks);
+        b.ws0 = w.take<float>(size_t(r.s) * n8);
+        b.ws1 = w.take<uint32_t>(2 * size_t(r.m));
+        b.ws2 = w.take<float>(size_t(items) * 64);
+      }
+    }
+  };
+  WsCarve plan;
+  carve(plan);
+  RMC_TRY(rmc_ws_reserve(ctx, plan.off));
+  WsCarve w;
+  w.base = static_cast<char *>(ctx->ws);
+  carve(w);
+  for (int i = 0; i < nreq; ++i) {
+    const rmc_request &r = reqs[i];
+    BatchItem &b = host[i];
+    b.kind = r.kind;
+    b.k = r.k;
+    b.p = r.p;
+    b.q = r.q;
+    b.m = (int)r.m;
+    b.n = (int)r.n;
+    b.s = (int)r.s;
+    b.vec = ((reinterpret_cast<uintptr_t>(r.A) & 15) == 0 && (r.lda & 3) == 0) ? 1 : 0;
+    b.lda = r.lda;
+    b.seed = r.seed;
+    b.A = r.A;
+    b.b = r.b;
+    b.x = r.x;
+    b.U = r.U;
+    b.sigma = r.sigma;
+    b.V = r.V;
+  }
+  cudaStream_t st = ctx->stream;
+  RMC_TRY_CUDA(cudaMemcpyAsync(d_items, host.data(), sizeof(BatchItem) * nreq, cudaMemcpyHostToDevice, st));
+  RMC_TRY_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * nreq, cudaMemcpyHostToDevice, st));
+  RMC_TRY_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), st));
+  RMC_TRY_CUDA(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+  const int grid = std::min(nreq, ctx->num_sms);
+  {
+    RmcProf prof(ctx, RMC_K_BATCH);
+    batch_kernel<<<grid, kThreads, kSmemBytes, st>>>(d_items, d_order, nreq, d_next, ctx->d_status);
+  }
+  rmc_note_launch();
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}

@@ -120,3 +120,63 @@ def batch_sizes(count=4096, seed=0, m_range=(512, 32768), n_range=(16, 256)):
     m = np.exp(gen.uniform(lo, hi, count)).astype(np.int64)
     n = gen.integers(n_range[0], n_range[1] + 1, count)
     return m, n
+
+
+def batch_specs(count=4096, seed=0, m_range=(512, 32768), n_range=(16, 256), k=16, p=8, q=1, s_factor=4):
+    """The batched workload: ``count`` problems with m log-uniform and n uniform (``batch_sizes``); even
+    positions are randomized k-SVD problems (k, p, q; oversampling cut to p = n - k where n < k + p, since
+    l = k + p may not exceed n), odd positions count-sketch least squares with s = s_factor * n.  Each
+    problem has its own seed.  Returns a list of dicts."""
+    m, n = batch_sizes(count, seed, m_range, n_range)
+    specs = []
+    for i in range(count):
+        mi, ni = int(m[i]), int(n[i])
+        pseed = seed * 1000003 + i
+        if i % 2 == 0:
+            ki = min(k, ni)
+            specs.append(dict(kind="rsvd", m=mi, n=ni, k=ki, p=max(0, min(p, ni - ki)), q=q, seed=pseed))
+        else:
+            specs.append(dict(kind="lsr", m=mi, n=ni, s=s_factor * ni, seed=pseed))
+    return specs
+
+
+def batch_problem_numpy(spec, exponent=1.5, noise_std=math.sqrt(1e-3)):
+    """Inputs of one batched problem on the CPU (FP32).  rsvd: A = U diag(i^-exponent) V^T with Haar U
+    (m x r), V (n x r), r = min(m, n).  lsr: A iid N(0, 1), b = A x* + N(0, noise_std^2) with x* ~ N(0, 1).
+    Returns (A, b) with b None for rsvd."""
+    gen = rng(spec["seed"])
+    m, n = spec["m"], spec["n"]
+    if spec["kind"] == "rsvd":
+        r = min(m, n)
+        U = haar(m, r, gen)
+        V = haar(n, r, gen)
+        sigma = np.arange(1, r + 1, dtype=np.float64) ** (-exponent)
+        return ((U * sigma) @ V.T).astype(np.float32), None
+    A = gen.standard_normal((m, n)).astype(np.float32)
+    x = gen.standard_normal(n)
+    b = (A.astype(np.float64) @ x + noise_std * gen.standard_normal(m)).astype(np.float32)
+    return A, b
+
+
+def batch_problem_torch(spec, exponent=1.5, noise_std=math.sqrt(1e-3), device="cuda"):
+    """The same recipe drawn on ``device`` with a seeded torch generator (for the full-size batch).  Haar
+    factors come from the Q of a Cholesky QR of a Gaussian matrix, in FP64."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(spec["seed"])
+    m, n = spec["m"], spec["n"]
+    if spec["kind"] == "rsvd":
+        r = min(m, n)
+
+        def orth(rows):
+            G = torch.randn(rows, r, generator=g, device=device, dtype=torch.float64)
+            R = torch.linalg.cholesky(G.T @ G, upper=True)
+            return torch.linalg.solve_triangular(R, G, upper=True, left=False)
+
+        U, V = orth(m), orth(n)
+        sigma = torch.arange(1, r + 1, device=device, dtype=torch.float64).pow(-exponent)
+        return ((U * sigma) @ V.T).float().contiguous(), None
+    A = torch.randn(m, n, generator=g, device=device, dtype=torch.float32)
+    x = torch.randn(n, generator=g, device=device, dtype=torch.float64)
+    b = (A.double() @ x + noise_std * torch.randn(m, generator=g, device=device, dtype=torch.float64)).float()
+    return A, b
