@@ -22,6 +22,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -324,6 +326,9 @@ def run_ours(args, world, rank, local):
     batch_info = None
     if world == 1 and not args.no_batch:
         batch_info = batch_measure(torch, rmc)
+    serve_info = None
+    if world == 1 and not args.no_serve:
+        serve_info = serve_measure(torch, rmc)
 
     cpu = None
     if world == 1:
@@ -340,7 +345,7 @@ def run_ours(args, world, rank, local):
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernels, "kernels_isolated": isolated,
-        "rsvd": rsvd_info, "batch": batch_info,
+        "rsvd": rsvd_info, "batch": batch_info, "serve": serve_info,
     }
     print(json.dumps(line))
     if world > 1:
@@ -457,6 +462,67 @@ def batch_measure(torch, rmc, count=4096, m_range=(512, 32768), reps=3):
     return out
 
 
+def serve_measure(torch, rmc, rates=(1000, 5000), window_s=1.0, pool=48, budget=64 << 30, nstreams=4):
+    """The served stream: Poisson arrivals at each rate for window_s seconds over a pool of resident problems
+    (m log-uniform [1e3, 2e5], n log-uniform [32, 1024]; 60% count-sketch least squares with s = 4n, 40%
+    randomized k-SVD with k in {8, 32, 64}, p = 8, q = 1), admitted under a 64 GB budget on 4 streams.  The
+    stream is replayed in real time, once with FP32 products and once with TF32 products for the k-SVDs that
+    run on the single-problem path.  Reports completed requests/s and p50/p99 latency (submit to
+    completion)."""
+    import time
+    import workloads
+    ms_, ns_ = workloads.serve_pool(pool, seed=SEED)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(SEED)
+    mats = []
+    for m, n in zip(ms_, ns_):
+        A = torch.randn(m, n, generator=g, device="cuda", dtype=torch.float32)
+        b = torch.randn(m, generator=g, device="cuda", dtype=torch.float32)
+        mats.append((A, b))
+    torch.cuda.synchronize()
+    out = {"workload": "poisson stream, pool of %d resident problems m~logU[1e3,2e5] n~logU[32,1024]; 60%% lsr "
+                       "(countsketch s=4n) / 40%% rsvd (k in {8,32,64}, p=8, q=1); budget 64 GB, %d streams"
+                       % (pool, nstreams), "window_s": window_s, "runs": {}}
+    for prec in ("fp32", "tf32"):
+        for rate in rates:
+            arr = workloads.serve_arrivals(rate, window_s, pool, seed=SEED + rate)
+            srv = rmc.Server(budget, nstreams=nstreams, max_batch=256)
+            live, lat = {}, []
+            i, t0 = 0, time.perf_counter()
+            while True:
+                now = time.perf_counter() - t0
+                while i < len(arr) and arr[i]["t"] <= now:
+                    a = arr[i]
+                    A, b = mats[a["pool"]]
+                    n = A.shape[1]
+                    if a["kind"] == "lsr":
+                        r, o = rmc.lsr_request(A, b, a["s_factor"] * n, a["seed"])
+                        tk = srv.submit(r, sketch="countsketch", prec="fp32")
+                    else:
+                        k = max(1, min(a["k"], n - a["p"]))
+                        r, o = rmc.rsvd_request(A, k, a["p"], a["q"], a["seed"])
+                        tk = srv.submit(r, prec=prec)
+                    live[tk] = o
+                    i += 1
+                srv.progress()
+                for tk, st, l in srv.poll():
+                    assert st == rmc.RMC_OK, st
+                    lat.append(l)
+                    del live[tk]
+                if i == len(arr) and not live:
+                    break
+            t_end = time.perf_counter() - t0
+            srv.close()
+            lat_ms = np.sort(np.array(lat)) * 1e3
+            out["runs"]["%s_rate%d" % (prec, rate)] = {
+                "offered_per_s": len(arr) / window_s, "completed": len(lat), "completed_per_s": len(lat) / t_end,
+                "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                "mean_ms": float(lat_ms.mean()), "drain_s": t_end}
+    del mats
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -467,6 +533,7 @@ def main():
                     help="run one small case of one kernel family (for profiler captures) and exit")
     ap.add_argument("--no-rsvd", action="store_true", help="skip the large randomized-SVD measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-problems measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-stream measurement")
     args = ap.parse_args()
     if args.probe:
         return run_probe(args.probe)

@@ -199,6 +199,42 @@ typedef struct rmc_request {
  * at rmc_sync when a problem's factorization broke down (its outputs are then NaN). */
 int rmc_batch_run(rmc_ctx *ctx, const rmc_request *reqs, int nreq);
 
+/* ------------------------------------------------------------------ continuous-batching request server */
+
+/* A served request: one problem of Ch. 4 (sketch-and-solve least squares) or Ch. 5 (randomized k-SVD) plus how to
+ * run it.  `req` is as for rmc_batch_run, except that here LSR allows n <= 1024 with any sketch kind and RSVD
+ * allows l = k + p <= 256; its inputs and outputs are device memory that the caller keeps resident and
+ * untouched until the request completes. */
+typedef struct rmc_serve_request {
+  rmc_request req;
+  int sketch;   /* LSR: RMC_GAUSSIAN, RMC_SRHT or RMC_COUNTSKETCH (RSVD: ignored)                        */
+  int prec;     /* RMC_FP32, RMC_TF32 or RMC_BF16: operand precision of the products with A                 */
+} rmc_serve_request;
+
+typedef struct rmc_server rmc_server;
+
+/* A server on the current device with `nstreams` streams (1..16), each with its own workspace of at most
+ * hbm_budget / nstreams bytes: the device memory the server holds never exceeds hbm_budget.  Small requests
+ * (count-sketch LSR with n <= 256, s <= 1024; FP32 RSVD with l <= 32, n <= 256) are batched, up to
+ * max_batch per launch, into rmc_batch_run launches; the others run one per launch through rmc_lsr_sketch /
+ * rmc_rsvd.  Launches on different streams overlap on the device.  Single-threaded: one host thread drives
+ * a server.  The paper has no counterpart (it treats one problem at a time). */
+int rmc_server_create(rmc_server **out, size_t hbm_budget, int nstreams, int max_batch);
+/* Waits for every launch in flight, then frees the server. */
+int rmc_server_destroy(rmc_server *srv);
+/* Queue a request; *ticket identifies it in rmc_server_poll.  Never blocks.  RMC_EINVAL for a malformed
+ * request, RMC_ENOMEM when its workspace alone exceeds one stream's share of the budget. */
+int rmc_server_submit(rmc_server *srv, const rmc_serve_request *req, uint64_t *ticket);
+/* Retire finished launches, then admit queued requests onto free streams (continuous batching: a request
+ * that arrives while others run is admitted as soon as a stream and its memory free up).  Never blocks.
+ * Returns the number of requests in flight and still queued (either pointer may be NULL). */
+int rmc_server_progress(rmc_server *srv, int *inflight, int *queued);
+/* Completed requests since the last poll, in completion order: ticket, status (RMC_OK or the error its
+ * launch reported) and latency in seconds from submit to the progress call that saw it finish. */
+int rmc_server_poll(rmc_server *srv, uint64_t *tickets, int *status, double *latency_s, int max, int *count);
+/* Progress until nothing is queued or in flight (blocks, yielding the CPU between checks). */
+int rmc_server_drain(rmc_server *srv);
+
 /* ------------------------------------------------------------------------------- measurement hooks */
 
 /* Kernel tags for rmc_profile_read. */

@@ -361,3 +361,70 @@ def rmc_batch_run(requests):
     """Run a list of rmc_request in one persistent launch on the current stream (outputs as given)."""
     arr = (rmc_request * len(requests))(*requests)
     _check(lib.rmc_batch_run(context().bind(), arr, len(requests)), "rmc_batch_run")
+
+
+class rmc_serve_request(ctypes.Structure):
+    """Mirror of the C struct rmc_serve_request."""
+    _fields_ = [("req", rmc_request), ("sketch", _int), ("prec", _int)]
+
+
+lib.rmc_server_create.argtypes = [ctypes.POINTER(_p), _sz, _int, _int]
+lib.rmc_server_destroy.argtypes = [_p]
+lib.rmc_server_submit.argtypes = [_p, ctypes.POINTER(rmc_serve_request), ctypes.POINTER(_u64)]
+lib.rmc_server_progress.argtypes = [_p, ctypes.POINTER(_int), ctypes.POINTER(_int)]
+lib.rmc_server_poll.argtypes = [_p, ctypes.POINTER(_u64), ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_double),
+                                _int, ctypes.POINTER(_int)]
+lib.rmc_server_drain.argtypes = [_p]
+for _f in ("rmc_server_create", "rmc_server_destroy", "rmc_server_submit", "rmc_server_progress",
+           "rmc_server_poll", "rmc_server_drain"):
+    getattr(lib, _f).restype = ctypes.c_int
+
+
+class Server:
+    """Continuous-batching server (rmc_server_*) on the current device.  Requests are (rmc_request, sketch,
+    prec); their tensors must stay alive until the request is polled as done."""
+
+    def __init__(self, hbm_budget, nstreams=4, max_batch=256):
+        self.handle = _p()
+        _check(lib.rmc_server_create(ctypes.byref(self.handle), _sz(hbm_budget), nstreams, max_batch),
+               "rmc_server_create")
+        self._buf = 256
+        self._t = (_u64 * self._buf)()
+        self._s = (_int * self._buf)()
+        self._l = (ctypes.c_double * self._buf)()
+
+    def submit(self, request, sketch="countsketch", prec="fp32"):
+        r = rmc_serve_request(req=request, sketch=_kind(sketch), prec=_prec(prec))
+        t = _u64()
+        _check(lib.rmc_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)), "rmc_server_submit")
+        return t.value
+
+    def progress(self):
+        a, b = _int(), _int()
+        _check(lib.rmc_server_progress(self.handle, ctypes.byref(a), ctypes.byref(b)), "rmc_server_progress")
+        return a.value, b.value
+
+    def poll(self):
+        """[(ticket, status, latency_s)] of the requests completed since the last poll."""
+        out = []
+        while True:
+            c = _int()
+            _check(lib.rmc_server_poll(self.handle, self._t, self._s, self._l, self._buf, ctypes.byref(c)),
+                   "rmc_server_poll")
+            out.extend((self._t[i], self._s[i], self._l[i]) for i in range(c.value))
+            if c.value < self._buf:
+                return out
+
+    def drain(self):
+        _check(lib.rmc_server_drain(self.handle), "rmc_server_drain")
+
+    def close(self):
+        if self.handle:
+            lib.rmc_server_destroy(self.handle)
+            self.handle = _p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

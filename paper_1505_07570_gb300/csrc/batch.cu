@@ -16,6 +16,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <string.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -1005,7 +1007,43 @@ static bool bad_request(const rmc_request &r) {
   return true;
 }
 
+// Workspace of a batch: descriptors, order, queue counter, then each problem's buffers.
+static void batch_carve(WsCarve &w, const rmc_request *reqs, int nreq, BatchItem *host, BatchItem **d_items,
+                        int **d_order, int **d_next) {
+  *d_items = w.take<BatchItem>(nreq);
+  *d_order = w.take<int>(nreq);
+  *d_next = w.take<int>(1);
+  for (int i = 0; i < nreq; ++i) {
+    const rmc_request &r = reqs[i];
+    BatchItem &b = host[i];
+    b.ws0 = nullptr;
+    b.ws1 = nullptr;
+    b.ws2 = nullptr;
+    if (r.kind == RMC_REQ_RSVD) {
+      b.ws0 = w.take<float>(size_t(r.m) * lp_of(r.k + r.p));
+    } else {
+      const int n8 = (int(r.n) + 8) & ~7;
+      const int nbk = n8 / 8, blocks = nbk * (nbk + 1) / 2;
+      const int items = blocks * std::max(1, kThreads / blocks);
+      b.ws0 = w.take<float>(size_t(r.s) * n8);
+      b.ws1 = w.take<uint32_t>(2 * size_t(r.m));
+      b.ws2 = w.take<float>(size_t(items) * 64);
+    }
+  }
+}
+
 }  // namespace
+
+bool rmc_batch_request_ok(const rmc_request &r) { return !bad_request(r); }
+
+size_t rmc_batch_plan_bytes(const rmc_request *reqs, int nreq) {
+  std::vector<BatchItem> host(nreq);
+  BatchItem *d_items;
+  int *d_order, *d_next;
+  WsCarve plan;
+  batch_carve(plan, reqs, nreq, host.data(), &d_items, &d_order, &d_next);
+  return plan.off;
+}
 
 extern "C" int rmc_batch_run(rmc_ctx *ctx, const rmc_request *reqs, int nreq) {
   if (!ctx || nreq < 0 || (nreq > 0 && !reqs)) return RMC_EINVAL;
@@ -1021,32 +1059,10 @@ extern "C" int rmc_batch_run(rmc_ctx *ctx, const rmc_request *reqs, int nreq) {
   }
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
 
-  // workspace: descriptors, order, queue counter, then each problem's buffers
   std::vector<BatchItem> host(nreq);
   BatchItem *d_items = nullptr;
   int *d_order = nullptr, *d_next = nullptr;
-  auto carve = [&](WsCarve &w) {
-    d_items = w.take<BatchItem>(nreq);
-    d_order = w.take<int>(nreq);
-    d_next = w.take<int>(1);
-    for (int i = 0; i < nreq; ++i) {
-      const rmc_request &r = reqs[i];
-      BatchItem &b = host[i];
-      b.ws0 = nullptr;
-      b.ws1 = nullptr;
-      b.ws2 = nullptr;
-      if (r.kind == RMC_REQ_RSVD) {
-        b.ws0 = w.take<float>(size_t(r.m) * lp_of(r.k + r.p));
-      } else {
-        const int n8 = (int(r.n) + 8) & ~7;
-        const int nbk = n8 / 8, blocks = nbk * (nbk + 1) / 2;
-        const int items = blocks * std::max(1, kThreads / blocks);
-        b.ws0 = w.take<float>(size_t(r.s) * n8);
-        b.ws1 = w.take<uint32_t>(2 * size_t(r.m));
-        b.ws2 = w.take<float>(size_t(items) * 64);
-      }
-    }
-  };
+  auto carve = [&](WsCarve &w) { batch_carve(w, reqs, nreq, host.data(), &d_items, &d_order, &d_next); };
   WsCarve plan;
   carve(plan);
   RMC_TRY(rmc_ws_reserve(ctx, plan.off));
@@ -1074,8 +1090,24 @@ extern "C" int rmc_batch_run(rmc_ctx *ctx, const rmc_request *reqs, int nreq) {
     b.V = r.V;
   }
   cudaStream_t st = ctx->stream;
-  RMC_TRY_CUDA(cudaMemcpyAsync(d_items, host.data(), sizeof(BatchItem) * nreq, cudaMemcpyHostToDevice, st));
-  RMC_TRY_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * nreq, cudaMemcpyHostToDevice, st));
+  // descriptors go through the context's pinned staging buffer (an asynchronous copy that never waits on the
+  // device, unlike one from pageable memory); the buffer is reused once the previous copy out of it is done
+  const size_t items_bytes = sizeof(BatchItem) * nreq, stage_bytes = items_bytes + sizeof(int) * nreq;
+  if (!ctx->stage_ev) RMC_TRY_CUDA(cudaEventCreateWithFlags(&ctx->stage_ev, cudaEventDisableTiming));
+  else RMC_TRY_CUDA(cudaEventSynchronize(ctx->stage_ev));
+  if (ctx->h_stage_bytes < stage_bytes) {
+    if (ctx->h_stage) RMC_TRY_CUDA(cudaFreeHost(ctx->h_stage));
+    ctx->h_stage = nullptr;
+    ctx->h_stage_bytes = 0;
+    RMC_TRY_CUDA(cudaMallocHost(&ctx->h_stage, stage_bytes + stage_bytes / 2));
+    ctx->h_stage_bytes = stage_bytes + stage_bytes / 2;
+  }
+  char *stage = static_cast<char *>(ctx->h_stage);
+  memcpy(stage, host.data(), items_bytes);
+  memcpy(stage + items_bytes, order.data(), sizeof(int) * nreq);
+  RMC_TRY_CUDA(cudaMemcpyAsync(d_items, stage, items_bytes, cudaMemcpyHostToDevice, st));
+  RMC_TRY_CUDA(cudaMemcpyAsync(d_order, stage + items_bytes, sizeof(int) * nreq, cudaMemcpyHostToDevice, st));
+  RMC_TRY_CUDA(cudaEventRecord(ctx->stage_ev, st));
   RMC_TRY_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), st));
   RMC_TRY_CUDA(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
   const int grid = std::min(nreq, ctx->num_sms);

@@ -67,6 +67,8 @@ int rmc_destroy(rmc_ctx *ctx) {
   if (!ctx) return RMC_OK;
   int rc = RMC_OK;
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = RMC_ECUDA;
+  if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->prof_recs) {
     for (int r = 0; r < ctx->prof_cap; ++r) {
       cudaEventDestroy(ctx->prof_recs[r].start);
@@ -164,33 +166,83 @@ int rmc_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, 
   return run_sketch(ctx, A, m, n, lda, nullptr, s, kind, seed, prec, C, ldc, nullptr, ctx->ws);
 }
 
+// Workspace plan of rmc_lsr_sketch: [S^T A, S^T b] (s x (n+1)), S^T b, then the larger of the sketch's and
+// the solve's scratch.
+static size_t lsr_rest_bytes(rmc_ctx *ctx, int64_t m, int64_t n, int64_t s, int kind, int prec) {
+  size_t rest = sketch_ws(ctx, m, n + 1, s, kind, prec);
+  const size_t solve = rmc_lsr_solve_ws(s, n, ctx->num_sms);
+  return solve > rest ? solve : rest;
+}
+
+static void lsr_carve(WsCarve &w, int64_t n, int64_t s, size_t rest_bytes, float **SAb, float **Sb, void **rest) {
+  *SAb = w.take<float>(size_t(s) * (n + 1));
+  *Sb = w.take<float>(size_t(s));
+  *rest = w.take<char>(rest_bytes);
+}
+
+size_t rmc_lsr_plan_bytes(rmc_ctx *ctx, int64_t m, int64_t n, int64_t s, int kind, int prec) {
+  float *SAb, *Sb;
+  void *rest;
+  WsCarve plan;
+  lsr_carve(plan, n, s, lsr_rest_bytes(ctx, m, n, s, kind, prec), &SAb, &Sb, &rest);
+  return plan.off;
+}
+
 int rmc_lsr_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b, int64_t s,
                    int kind, uint64_t seed, int prec, double *x) {
   if (!ctx || !b || !x) return RMC_EINVAL;
   RMC_TRY(check_sketch_args(A, m, n, lda, s, kind, prec));
   if (s < n || n > 1024) return RMC_EINVAL;
-  // [S^T A, S^T b] is kept as one s x (n+1) matrix; S^T b is sketched into its own vector first.
-  size_t rest_bytes = sketch_ws(ctx, m, n + 1, s, kind, prec);
-  const size_t solve = rmc_lsr_solve_ws(s, n, ctx->num_sms);
-  if (solve > rest_bytes) rest_bytes = solve;
-  auto carve = [&](WsCarve &w, float **SAb, float **Sb, void **rest) {
-    *SAb = w.take<float>(size_t(s) * (n + 1));
-    *Sb = w.take<float>(size_t(s));
-    *rest = w.take<char>(rest_bytes);
-  };
+  const size_t rest_bytes = lsr_rest_bytes(ctx, m, n, s, kind, prec);
   float *SAb, *Sb;
   void *rest;
   WsCarve plan;
-  carve(plan, &SAb, &Sb, &rest);
+  lsr_carve(plan, n, s, rest_bytes, &SAb, &Sb, &rest);
   RMC_TRY(rmc_ws_reserve(ctx, plan.off));
   WsCarve w;
   w.base = static_cast<char *>(ctx->ws);
-  carve(w, &SAb, &Sb, &rest);
+  lsr_carve(w, n, s, rest_bytes, &SAb, &Sb, &rest);
+  // [S^T A, S^T b] is kept as one s x (n+1) matrix; S^T b is sketched into its own vector first.
   RMC_TRY(run_sketch(ctx, A, m, n, lda, b, s, kind, seed, prec, SAb, n + 1, Sb, rest));
   return rmc_launch_lsr_solve(ctx, SAb, s, n, n + 1, Sb, x, rest);
 }
 
 // -------------------------------------------------------------------------------------------------- rsvd
+
+// Workspace plan of rmc_rsvd: Omega (n x l), Y/Q (m x l), Z (n x l), B (l x n), Ub (l x l), sigma (l),
+// Vb (n x l), then the largest scratch of its steps.
+static size_t rsvd_scratch_bytes(rmc_ctx *ctx, int64_t m, int64_t n, int64_t l, int gp) {
+  size_t scratch = rmc_cholqr2_ws(m > n ? m : n, l, ctx->num_sms);
+  size_t t = rmc_matmul_ws(m, n, l, 0, gp, ctx->num_sms);
+  if (t > scratch) scratch = t;
+  t = rmc_matmul_ws(m, n, l, 1, gp, ctx->num_sms);
+  if (t > scratch) scratch = t;
+  t = rmc_svd_wide_ws(l, n, ctx->num_sms);
+  return t > scratch ? t : scratch;
+}
+
+static void rsvd_carve(WsCarve &w, int64_t m, int64_t n, int64_t l, size_t scratch, float **Om, float **Y, float **Z,
+                       float **B, float **Ub, float **sg, float **Vb, void **scr) {
+  *Om = w.take<float>(size_t(n) * l);
+  *Y = w.take<float>(size_t(m) * l);
+  *Z = w.take<float>(size_t(n) * l);
+  *B = w.take<float>(size_t(l) * n);
+  *Ub = w.take<float>(size_t(l) * l);
+  *sg = w.take<float>(size_t(l));
+  *Vb = w.take<float>(size_t(n) * l);
+  *scr = w.take<char>(scratch);
+}
+
+static int rsvd_gemm_prec(int prec) { return prec == RMC_BF16 ? RMC_TF32 : prec; }  // products read FP32 A
+
+size_t rmc_rsvd_plan_bytes(rmc_ctx *ctx, int64_t m, int64_t n, int64_t l, int prec) {
+  float *Om, *Y, *Z, *B, *Ub, *sg, *Vb;
+  void *scr;
+  WsCarve plan;
+  rsvd_carve(plan, m, n, l, rsvd_scratch_bytes(ctx, m, n, l, rsvd_gemm_prec(prec)), &Om, &Y, &Z, &B, &Ub, &sg, &Vb,
+             &scr);
+  return plan.off;
+}
 
 int rmc_rsvd(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, int k, int p, int q, uint64_t seed,
              int prec, float *U, int64_t ldu, float *sigma, float *V, int64_t ldv) {
@@ -199,34 +251,17 @@ int rmc_rsvd(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, in
   if (k < 1 || p < 0 || q < 0 || m < 1 || n < 1 || bad_ld(lda, n) || l > m || l > n || l > 256) return RMC_EINVAL;
   if (bad_ld(ldu, k) || bad_ld(ldv, k)) return RMC_EINVAL;
   if (prec != RMC_FP32 && prec != RMC_TF32 && prec != RMC_BF16) return RMC_EINVAL;
-  const int gp = (prec == RMC_BF16) ? RMC_TF32 : prec;  // the products with A read FP32 A directly
+  const int gp = rsvd_gemm_prec(prec);
 
-  // workspace: Omega (n x l), Y/Q (m x l), Z (n x l), B (l x n), Ub (l x l), sigma (l), Vb (n x l) + scratch
-  size_t scratch = rmc_cholqr2_ws(m > n ? m : n, l, ctx->num_sms);
-  size_t t = rmc_matmul_ws(m, n, l, 0, gp, ctx->num_sms);
-  if (t > scratch) scratch = t;
-  t = rmc_matmul_ws(m, n, l, 1, gp, ctx->num_sms);
-  if (t > scratch) scratch = t;
-  t = rmc_svd_wide_ws(l, n, ctx->num_sms);
-  if (t > scratch) scratch = t;
   float *Om, *Y, *Z, *B, *Ub, *sg, *Vb;
   void *scr;
-  auto carve = [&](WsCarve &w) {
-    Om = w.take<float>(size_t(n) * l);
-    Y = w.take<float>(size_t(m) * l);
-    Z = w.take<float>(size_t(n) * l);
-    B = w.take<float>(size_t(l) * n);
-    Ub = w.take<float>(size_t(l) * l);
-    sg = w.take<float>(size_t(l));
-    Vb = w.take<float>(size_t(n) * l);
-    scr = w.take<char>(scratch);
-  };
+  const size_t scratch = rsvd_scratch_bytes(ctx, m, n, l, gp);
   WsCarve plan;
-  carve(plan);
+  rsvd_carve(plan, m, n, l, scratch, &Om, &Y, &Z, &B, &Ub, &sg, &Vb, &scr);
   RMC_TRY(rmc_ws_reserve(ctx, plan.off));
   WsCarve w;
   w.base = static_cast<char *>(ctx->ws);
-  carve(w);
+  rsvd_carve(w, m, n, l, scratch, &Om, &Y, &Z, &B, &Ub, &sg, &Vb, &scr);
 
   cudaStream_t st = ctx->stream;
   RMC_TRY(rmc_launch_gaussian(st, seed, 0, n, l, Om, l, 1.0f));                  // Omega, n x l

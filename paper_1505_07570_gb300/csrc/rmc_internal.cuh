@@ -28,6 +28,10 @@ struct rmc_ctx {
   RmcProfRec *prof_recs;
   int64_t prof_launches[RMC_K_NTAGS];
   double prof_ms[RMC_K_NTAGS];
+  // pinned staging for host-built descriptors (batched launches); reused once stage_ev has completed
+  void *h_stage;
+  size_t h_stage_bytes;
+  cudaEvent_t stage_ev;
 };
 
 // Count kernel launches (process-wide).
@@ -134,6 +138,13 @@ int rmc_launch_transpose(cudaStream_t st, const float *in, int64_t rows, int64_t
 int rmc_launch_rsvd_finish(rmc_ctx *ctx, const float *Q, int64_t m, int64_t l, const float *Ub, const float *sg,
                            const float *Vb, int64_t n, int k, float *U, int64_t ldu, float *sigma, float *V,
                            int64_t ldv, void *ws);
+
+// capi.cu / batch.cu: device workspace of one call (what rmc_ws_reserve will be asked for)
+extern "C" size_t rmc_lsr_plan_bytes(rmc_ctx *ctx, int64_t m, int64_t n, int64_t s, int kind, int prec);
+extern "C" size_t rmc_rsvd_plan_bytes(rmc_ctx *ctx, int64_t m, int64_t n, int64_t l, int prec);
+size_t rmc_batch_plan_bytes(const rmc_request *reqs, int nreq);
+// batch.cu: the limits of one batched problem (false when the problem must go to the single-problem path)
+bool rmc_batch_request_ok(const rmc_request &r);
 
 // tc_gemm.cu (tcgen05 tensor-core kernels)
 int rmc_tc_available(void);

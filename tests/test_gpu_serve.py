@@ -1,0 +1,135 @@
+"""The continuous-batching server (rmc_server_*): every request's result is the same whether it runs alone or
+in a mix of concurrently admitted requests (bit-identical: each request takes a route fixed by its own size
+and precision, and neither route's arithmetic depends on other requests), admission respects the memory
+budget, and every ticket completes exactly once."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def R():
+    import paper_1505_07570_gb300 as rmc
+    return rmc
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+# (kind, m, n, k or s, p, q, sketch, prec): both routes, several sketch kinds and precisions
+SPECS = [
+    ("lsr", 3000, 64, 256, 0, 0, "countsketch", "fp32"),   # batched
+    ("lsr", 5000, 300, 1200, 0, 0, "gaussian", "fp32"),    # n > 256: single-problem path
+    ("lsr", 4000, 48, 192, 0, 0, "srht", "fp32"),          # not a count sketch: single-problem path
+    ("lsr", 2000, 200, 800, 0, 0, "countsketch", "fp32"),  # batched
+    ("rsvd", 3000, 100, 16, 8, 1, None, "fp32"),           # batched
+    ("rsvd", 6000, 180, 32, 8, 1, None, "fp32"),           # l = 40: single-problem path
+    ("rsvd", 4000, 120, 16, 8, 1, None, "tf32"),           # TF32 products: single-problem path
+    ("rsvd", 800, 40, 8, 0, 0, None, "fp32"),              # batched, q = 0
+]
+
+
+def make(i, spec):
+    kind, m, n, ks, p, q, sketch, prec = spec
+    sp = dict(kind=kind, m=m, n=n, seed=500 + i)
+    if kind == "rsvd":
+        sp.update(k=ks, p=p, q=q)
+    else:
+        sp.update(s=ks)
+    A, b = workloads.batch_problem_numpy(sp)
+    return sp, dev(A), (dev(b) if b is not None else None), sketch or "countsketch", prec
+
+
+def new_request(R, sp, A, b):
+    if sp["kind"] == "rsvd":
+        return R.rsvd_request(A, sp["k"], sp["p"], sp["q"], sp["seed"])
+    return R.lsr_request(A, b, sp["s"], sp["seed"])
+
+
+def direct(R, sp, A, b, sketch, prec):
+    """The request through the entry point its route uses, alone."""
+    if sp["kind"] == "lsr":
+        if sketch == "countsketch" and sp["n"] <= 256 and sp["s"] <= 1024:
+            r, x = R.lsr_request(A, b, sp["s"], sp["seed"])
+            R.rmc_batch_run([r])
+            return (x,)
+        return (R.rmc_lsr_sketch(A, b, sp["s"], sketch, sp["seed"], prec=prec),)
+    if prec == "fp32" and sp["k"] + sp["p"] <= 32 and sp["n"] <= 256:
+        r, out = R.rsvd_request(A, sp["k"], sp["p"], sp["q"], sp["seed"])
+        R.rmc_batch_run([r])
+        return out
+    return R.rmc_rsvd(A, sp["k"], sp["p"], sp["q"], sp["seed"], prec=prec)
+
+
+@pytest.fixture(scope="module")
+def problems(R):
+    probs = [make(i, s) for i, s in enumerate(SPECS)]
+    refs = [direct(R, *p) for p in probs]
+    R.rmc_sync()
+    return probs, refs
+
+
+def outputs(o):
+    return o if isinstance(o, tuple) else (o,)
+
+
+def run_server(R, probs, waves, nstreams=4, budget=8 << 30):
+    """Submit the problems in `waves` (lists of indices) with progress calls in between; returns outputs."""
+    srv = R.Server(budget, nstreams=nstreams, max_batch=64)
+    outs, tickets = {}, {}
+    for wave in waves:
+        for i in wave:
+            sp, A, b, sketch, prec = probs[i]
+            r, o = new_request(R, sp, A, b)
+            outs[i] = outputs(o)
+            tickets[srv.submit(r, sketch=sketch, prec=prec)] = i
+        srv.progress()
+    srv.drain()
+    done = srv.poll()
+    srv.close()
+    assert sorted(t for t, _, _ in done) == sorted(tickets)
+    assert all(st == R.RMC_OK for _, st, _ in done)
+    assert all(lat >= 0 for _, _, lat in done)
+    return outs
+
+
+def test_serve_all_at_once_equals_alone(R, problems):
+    probs, refs = problems
+    outs = run_server(R, probs, [list(range(len(probs)))])
+    for i, ref in enumerate(refs):
+        for g, e in zip(outs[i], outputs(ref)):
+            assert torch.equal(g, e), SPECS[i]
+
+
+def test_serve_interleaved_equals_alone(R, problems):
+    """Requests arriving while others are in flight (several waves, one stream and two streams)."""
+    probs, refs = problems
+    waves = [[0, 4], [1, 5, 7], [2], [3, 6]]
+    for nstreams in (1, 2):
+        outs = run_server(R, probs, waves, nstreams=nstreams)
+        for i, ref in enumerate(refs):
+            for g, e in zip(outs[i], outputs(ref)):
+                assert torch.equal(g, e), (nstreams, SPECS[i])
+
+
+def test_serve_budget_and_invalid(R, problems):
+    probs, _ = problems
+    srv = R.Server(1 << 20, nstreams=1, max_batch=8)   # 1 MB: too small for the n = 300 least squares
+    sp, A, b, sketch, prec = probs[1]
+    r, x = new_request(R, sp, A, b)
+    with pytest.raises(R.RmcError) as e:
+        srv.submit(r, sketch=sketch, prec=prec)
+    assert e.value.status == R.RMC_ENOMEM
+    sp, A, b, sketch, prec = probs[0]
+    r, x = new_request(R, sp, A, b)
+    r.s = 10  # s < n
+    with pytest.raises(R.RmcError) as e:
+        srv.submit(r, sketch=sketch, prec=prec)
+    assert e.value.status == R.RMC_EINVAL
+    srv.close()

@@ -180,3 +180,29 @@ def batch_problem_torch(spec, exponent=1.5, noise_std=math.sqrt(1e-3), device="c
     x = torch.randn(n, generator=g, device=device, dtype=torch.float64)
     b = (A.double() @ x + noise_std * torch.randn(m, generator=g, device=device, dtype=torch.float64)).float()
     return A, b
+
+
+def serve_pool(count=48, seed=0, m_range=(1000, 200000), n_range=(32, 1024)):
+    """Resident problems of the served stream: m and n log-uniform on their ranges.  Returns (m, n) lists."""
+    gen = rng(seed)
+    m = np.exp(gen.uniform(math.log(m_range[0]), math.log(m_range[1]), count)).astype(np.int64)
+    n = np.exp(gen.uniform(math.log(n_range[0]), math.log(n_range[1]), count)).astype(np.int64)
+    return [int(v) for v in m], [int(v) for v in n]
+
+
+def serve_arrivals(rate, window_s, pool_size, seed=0, lsr_share=0.6, ks=(8, 32, 64), p=8, q=1, s_factor=4):
+    """A Poisson request stream over ``window_s`` seconds at ``rate`` requests/s: each request picks a resident
+    problem uniformly, is least squares with probability lsr_share (count sketch, s = s_factor n) and a
+    randomized k-SVD otherwise (k uniform on ks, oversampling p, q power iterations; k is cut so that k + p
+    <= n).  Returns a list of dicts with the arrival time 't'."""
+    gen = rng(seed)
+    out, t = [], 0.0
+    while True:
+        t += gen.exponential(1.0 / rate)
+        if t >= window_s:
+            return out
+        j = int(gen.integers(pool_size))
+        if gen.uniform() < lsr_share:
+            out.append(dict(t=t, pool=j, kind="lsr", s_factor=s_factor, seed=len(out)))
+        else:
+            out.append(dict(t=t, pool=j, kind="rsvd", k=int(gen.choice(ks)), p=p, q=q, seed=len(out)))
