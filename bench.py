@@ -33,6 +33,13 @@ STEP = [("countsketch", 1024), ("countsketch", 4096), ("srht", 1024), ("srht", 4
 SEED = 20150527
 ORACLE_SAMPLE_ROWS = 4096          # rows of A the CPU oracle sketches per call
 GAUSS_PREC = os.environ.get("RMC_BENCH_GAUSS_PREC", "tf32")
+# DRAM bytes per row of A per launch from ncu captures of `python bench.py --probe <kind>` (A 262,144 x 256 + b):
+# dram__bytes_read.sum + dram__bytes_write.sum divided by 262,144.  Re-capture when a kernel changes.
+PROFILED_DRAM_BYTES_PER_ROW = {
+    "gaussian_sketch": (270.348032e6 + 5.421056e6) / 262144,
+    "srht_stage1": (268.521216e6 + 9.106176e6) / 262144,
+    "countsketch_gather": (271.633408e6 + 4.247552e6) / 262144,
+}
 
 
 def peaks():
@@ -295,6 +302,10 @@ def run_ours(args, world, rank, local):
         r["frac"] = r["achieved"] / r["peak"]
         r["kernel"] = name
         r["ms_avg"] = avg_s * 1e3
+        # dram__bytes_read.sum + dram__bytes_write.sum of one launch, captured on the 262,144-row probe and
+        # scaled by rows to this workload (each kernel reads every row once, so traffic grows in proportion)
+        per_row = PROFILED_DRAM_BYTES_PER_ROW.get(name)
+        r["traffic"] = per_row * M if per_row else None
         return r
 
     sketch_kernels = {k: v for k, v in kernels.items() if k in ("countsketch_gather", "srht_stage1", "gaussian_sketch")}
@@ -302,7 +313,6 @@ def run_ours(args, world, rank, local):
     if sketch_kernels:
         name, rec = max(sketch_kernels.items(), key=lambda kv: kv[1]["ms_total"])
         roof = roofline_of(name, rec)
-        roof["traffic"] = None
     for name, rec in kernels.items():
         rec["ms_avg"] = rec["ms_total"] / rec["launches"]
     # the same kernels once more, one call at a time on one stream (no overlap), for per-kernel rooflines
@@ -360,6 +370,8 @@ def run_probe(kind):
     import torch
     import paper_1505_07570_gb300 as rmc
     import workloads
+    if kind == "peaks":
+        return matmul_peaks(torch)
     if kind == "batch":
         info = batch_measure(torch, rmc, count=512, m_range=(512, 8192), reps=2)
         print(json.dumps({"probe": kind, "ms_per_call": info["ms"], "info": info}))
@@ -415,6 +427,35 @@ def rsvd_measure(torch, rmc):
     del A
     torch.cuda.empty_cache()
     return out
+
+
+def matmul_peaks(torch):
+    """Context figures: cuBLAS GEMM rates through torch.matmul (best of 5, CUDA events) in FP64, FP32 (no TF32),
+    TF32 and BF16.  Library GEMMs, not part of the path; they show what each precision costs on this GPU."""
+    out = {}
+    for name, dtype, tf32, size in [("dgemm", torch.float64, False, 4096), ("sgemm", torch.float32, False, 8192),
+                                    ("tf32_gemm", torch.float32, True, 8192), ("bf16_gemm", torch.bfloat16, False, 8192)]:
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        try:
+            a = torch.randn(size, size, device="cuda", dtype=torch.float32).to(dtype)
+            b = torch.randn(size, size, device="cuda", dtype=torch.float32).to(dtype)
+            torch.matmul(a, b)
+            best = None
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            out[name] = {"n": size, "ms": best, "tflops": 2.0 * size ** 3 / best / 1e9}
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = prev
+        del a, b
+    print(json.dumps({"probe": "peaks", "matmul": out}))
+    return 0
 
 
 def batch_measure(torch, rmc, count=4096, m_range=(512, 32768), reps=3):
@@ -529,7 +570,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--probe", choices=["countsketch", "srht", "gaussian", "lsr", "rsvd", "batch"], default=None,
+    ap.add_argument("--probe", choices=["countsketch", "srht", "gaussian", "lsr", "rsvd", "batch", "peaks"], default=None,
                     help="run one small case of one kernel family (for profiler captures) and exit")
     ap.add_argument("--no-rsvd", action="store_true", help="skip the large randomized-SVD measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-problems measurement")
