@@ -3,6 +3,7 @@
 //  - CholeskyQR2 (Gram matrix accumulated in FP64 from exact FP32 products, FP64 Cholesky, triangular apply),
 //  - the small SVD by one-sided Jacobi on the l x l triangular factor,
 //  - the FP64 solve of the sketched least-squares problem.
+#include <algorithm>
 #include <cmath>
 
 #include "rmc_internal.cuh"
@@ -118,7 +119,9 @@ constexpr int GRAM_T = 32;
 // Partial Gram of one chunk of rows for one 32 x 32 tile pair (ti <= tj): products of FP32 values are exact in
 // FP64, and the sums are FP64.
 __global__ void __launch_bounds__(256) gram_f64_kernel(const float *__restrict__ Y, int64_t m, int l, int64_t ldy,
-                                                       int64_t rows_per_chunk, double *__restrict__ part) {
+                                                       int64_t rows_per_chunk, double *__restrict__ part,
+                                                       const int *gate) {
+  if (gate && !*gate) return;  // a fallback that is not needed
   __shared__ double As[GRAM_T][GRAM_T + 1];
   __shared__ double Bs[GRAM_T][GRAM_T + 1];
   // decode the tile pair
@@ -203,7 +206,9 @@ __global__ void __launch_bounds__(256) gram_f32_kernel(const float *__restrict__
   if (i1 < l && j1 < l) o[i1 * l + j1] = acc11;
 }
 
-__global__ void gram_reduce_kernel(const double *__restrict__ part, int chunks, int l, double *__restrict__ G) {
+__global__ void gram_reduce_kernel(const double *__restrict__ part, int chunks, int l, double *__restrict__ G,
+                                   const int *gate) {
+  if (gate && !*gate) return;
   const int total = l * l;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const int i = e / l, j = e % l;
@@ -273,58 +278,6 @@ __device__ bool chol32_smem(float *P, const int *base, float *dinv, int l) {
   return true;
 }
 
-// Solve U^T U d = w in place (w in shared memory, length l), blocked by 32: the diagonal block on warp 0,
-// the off-diagonal updates block-wide.
-__device__ void chol32_solve(const float *P, const int *base, const float *dinv, int l, float *w) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // forward: U^T y = w
-  for (int k0 = 0; k0 < l; k0 += 32) {
-    const int nb = min(32, l - k0);
-    if (warp == 0) {
-      float v = (lane < nb) ? w[k0 + lane] : 0.f;
-#pragma unroll
-      for (int p = 0; p < 32; ++p) {
-        if (p < nb) {
-          const float yp = __shfl_sync(0xffffffffu, v, p) * dinv[k0 + p];
-          if (lane == p) v = yp;
-          if (lane > p && lane < nb) v = fmaf(-P[base[k0 + p] + k0 + lane], yp, v);
-        }
-      }
-      if (lane < nb) w[k0 + lane] = v;
-    }
-    __syncthreads();
-    for (int k = k0 + nb + tid; k < l; k += blockDim.x) {
-      float v = w[k];
-      for (int t = 0; t < nb; ++t) v = fmaf(-P[base[k0 + t] + k], w[k0 + t], v);
-      w[k] = v;
-    }
-    __syncthreads();
-  }
-  // backward: U d = y
-  for (int k1 = l; k1 > 0; k1 -= 32) {
-    const int k0 = max(0, k1 - 32), nb = k1 - k0;
-    if (warp == 0) {
-      float v = (lane < nb) ? w[k0 + lane] : 0.f;
-#pragma unroll
-      for (int p = 31; p >= 0; --p) {
-        if (p < nb) {
-          const float dp = __shfl_sync(0xffffffffu, v, p) * dinv[k0 + p];
-          if (lane == p) v = dp;
-          if (lane < p) v = fmaf(-P[base[k0 + lane] + k0 + p], dp, v);
-        }
-      }
-      if (lane < nb) w[k0 + lane] = v;
-    }
-    __syncthreads();
-    for (int k = tid; k < k0; k += blockDim.x) {
-      float v = w[k];
-      const int bk = base[k];
-      for (int t = 0; t < nb; ++t) v = fmaf(-P[bk + k0 + t], w[k0 + t], v);
-      w[k] = v;
-    }
-    __syncthreads();
-  }
-}
 
 __device__ void load_packed(const double *G, int l, int ldg, float *P, int *base) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -375,49 +328,6 @@ __global__ void __launch_bounds__(512) chol32_inv_kernel(double *G, int l, float
 // Least squares on the augmented FP64 Gram matrix G ((n+1) x (n+1), last column g = [S^T A]^T S^T b):
 // U = chol32(G11), then x0 = U^-1 U^-T g and x += U^-1 U^-T (g - G11 x) with FP64 residuals (iters times).
 // fail[0] = 1 when the FP32 factorization broke down (the FP64 kernels below then take over).
-__global__ void __launch_bounds__(512) lsr_chol32_refine_kernel(const double *G, int n, double *x, int iters,
-                                                                  int *fail) {
-  extern __shared__ float smem32[];
-  int *base = reinterpret_cast<int *>(smem32);
-  float *dinv = smem32 + n;
-  double *r = reinterpret_cast<double *>(smem32 + 2 * n);   // 2n floats = 8n bytes: 8-byte aligned
-  double *xs = r + n;
-  float *w = reinterpret_cast<float *>(xs + n);
-  float *P = w + n;
-  const int ld = n + 1, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  load_packed(G, n, ld, P, base);
-  const bool ok = chol32_smem(P, base, dinv, n);
-  if (tid == 0) fail[0] = ok ? 0 : 1;
-  if (!ok) return;
-  for (int i = tid; i < n; i += blockDim.x) {
-    r[i] = G[(int64_t)i * ld + n];
-    xs[i] = 0.0;
-  }
-  __syncthreads();
-  for (int it = 0; it <= iters; ++it) {
-    for (int i = tid; i < n; i += blockDim.x) w[i] = (float)r[i];
-    __syncthreads();
-    chol32_solve(P, base, dinv, n, w);
-    for (int i = tid; i < n; i += blockDim.x) xs[i] += (double)w[i];
-    __syncthreads();
-    if (it == iters) break;
-    for (int i = warp; i < n; i += nwarps) {         // r = g - G11 x, one warp per row
-      const double *row = G + (int64_t)i * ld;
-      double acc = 0.0;
-      for (int k = lane; k < n; k += 32) acc = fma(row[k], xs[k], acc);
-      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) r[i] = row[n] - acc;
-    }
-    __syncthreads();
-  }
-  for (int i = tid; i < n; i += blockDim.x) x[i] = xs[i];
-}
-
-size_t lsr32_smem_bytes(int n) {
-  return sizeof(float) * (2 * (size_t)n + 1) + sizeof(double) * 2 * n + sizeof(float) * n +
-         sizeof(float) * ((size_t)n * (n + 1) / 2) + 16;
-}
-
 size_t chol32_smem_bytes(int l) { return sizeof(float) * (2 * (size_t)l + (size_t)l * (l + 1) / 2); }
 
 // The FP64 path runs only when the FP32 one failed.  Matrices whose packed triangle does not fit in shared
@@ -767,6 +677,255 @@ __global__ void copy_column_kernel(const float *v, int64_t s, float *W, int64_t 
     W[i * ldw + col] = v[i];
 }
 
+// ------------------------------------------------------------- least-squares solve: FP32 factor, refinement
+// The normal-equation matrix SA^T SA is factored in FP32 (Gram with FP32 products summed in FP64 across
+// 32-row slices; blocked right-looking Cholesky over 32-wide panels, many CTAs per step), and x is then refined
+// against SA itself: r = Sb - SA x and g = SA^T r in FP64 (FP32 x FP32 products are exact in FP64), dx from
+// R^T R dx = g.  The fixed point is the least-squares solution of the FP32 [SA, Sb] whatever the rounding of
+// the factor; each step shrinks the error by about cond(SA)^2 x 2^-24.  A pivot that is not positive, or a last
+// step that has not converged, hands the problem to the FP64 path.
+
+constexpr int kPanel = 32;
+
+// Rf (n x n, row-major, upper triangle used) = the leading n x n block of G (FP64, ld = ldg).
+__global__ void lsr_rf_init_kernel(const double *G, int ldg, int n, float *Rf, int *flags) {
+  if (blockIdx.x == 0 && threadIdx.x < 4) flags[threadIdx.x] = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e - (int64_t)i * n);
+    Rf[e] = i <= j ? (float)G[(int64_t)i * ldg + j] : 0.f;
+  }
+}
+
+// Panel j0: every CTA factors the 32 x 32 diagonal block (FP32, in shared memory), CTA 0 stores it, and each
+// CTA forms its 256 columns of the panel rows R[j0 : j0+32, c] = R_jj^-T Rf[j0 : j0+32, c] (thread per column).
+__global__ void __launch_bounds__(256) lsr_chol_panel_kernel(float *Rf, int n, int j0, int *fail) {
+  __shared__ float D[kPanel][kPanel + 1];
+  __shared__ int bad;
+  if (*fail) return;
+  const int t = threadIdx.x;
+  const int b = min(kPanel, n - j0);
+  for (int e = t; e < kPanel * kPanel; e += blockDim.x) {
+    const int i = e / kPanel, j = e % kPanel;
+    D[i][j] = (i < b && j < b && i <= j) ? Rf[(int64_t)(j0 + i) * n + j0 + j] : (i == j ? 1.f : 0.f);
+  }
+  if (t == 0) bad = 0;
+  __syncthreads();
+  // right-looking over the 32 x 32 block, all threads on each trailing update
+  for (int k = 0; k < b; ++k) {
+    const float d = D[k][k];
+    if (!(d > 0.f) || !(d < INFINITY)) {
+      if (t == 0) bad = 1;
+      break;
+    }
+    const float rd = sqrtf(d);
+    __syncthreads();  // every thread has read the pivot
+    if (t < b) D[k][t] = t == k ? rd : (t > k ? D[k][t] / rd : D[k][t]);
+    __syncthreads();
+    for (int e = t; e < kPanel * kPanel; e += blockDim.x) {
+      const int i = e / kPanel, j = e % kPanel;
+      if (i > k && i <= j && j < b) D[i][j] = fmaf(-D[k][i], D[k][j], D[i][j]);
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (bad) {
+    if (t == 0 && blockIdx.x == 0) *fail = 1;
+    return;
+  }
+  if (blockIdx.x == 0)
+    for (int e = t; e < b * b; e += blockDim.x) {
+      const int i = e / b, j = e % b;
+      if (i <= j) Rf[(int64_t)(j0 + i) * n + j0 + j] = D[i][j];
+    }
+  const int c = j0 + b + blockIdx.x * blockDim.x + t;
+  if (c >= n) return;
+  float x[kPanel];
+#pragma unroll
+  for (int k = 0; k < kPanel; ++k) x[k] = k < b ? Rf[(int64_t)(j0 + k) * n + c] : 0.f;
+#pragma unroll
+  for (int k = 0; k < kPanel; ++k) {
+    float v = x[k];
+#pragma unroll
+    for (int p = 0; p < k; ++p) v = fmaf(-D[p][k], x[p], v);
+    x[k] = v / D[k][k];
+  }
+#pragma unroll
+  for (int k = 0; k < kPanel; ++k)
+    if (k < b) Rf[(int64_t)(j0 + k) * n + c] = x[k];
+}
+
+// Trailing update after panel j0: Rf[i, c] -= sum_k R[j0+k, i] R[j0+k, c] for j0+32 <= i <= c < n, in 64 x 64
+// tiles of the upper triangle (thread: 4 x 4 outputs).
+__global__ void __launch_bounds__(256) lsr_chol_update_kernel(float *Rf, int n, int j0, const int *fail) {
+  __shared__ float Pi[kPanel][64], Pc[kPanel][64];
+  if (*fail) return;
+  const int j1 = j0 + kPanel;
+  int p = blockIdx.x, ti = 0;
+  const int T = (n - j1 + 63) / 64;
+  while (p >= T - ti) { p -= T - ti; ++ti; }
+  const int tj = ti + p;
+  const int i0 = j1 + 64 * ti, c0 = j1 + 64 * tj;
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  for (int e = t; e < kPanel * 64; e += blockDim.x) {
+    const int k = e / 64, q = e % 64;
+    Pi[k][q] = i0 + q < n ? Rf[(int64_t)(j0 + k) * n + i0 + q] : 0.f;
+    Pc[k][q] = c0 + q < n ? Rf[(int64_t)(j0 + k) * n + c0 + q] : 0.f;
+  }
+  __syncthreads();
+  float acc[4][4] = {};
+#pragma unroll 8
+  for (int k = 0; k < kPanel; ++k) {
+    float a[4], bb[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a[u] = Pi[k][ty + 16 * u];
+      bb[u] = Pc[k][tx + 16 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], bb[v], acc[u][v]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = i0 + ty + 16 * u, c = c0 + tx + 16 * v;
+      if (i < n && c < n && i <= c) Rf[(int64_t)i * n + c] -= acc[u][v];
+    }
+}
+
+// r = Sb - SA x (FP64), one warp per row of [SA, Sb] (s x (n+1), Sb in column n).
+__global__ void lsr_resid_kernel(const float *SA, int64_t s, int n, int64_t ld, const double *x, double *r,
+                                 const int *flags) {
+  if (flags[0] || flags[2]) return;  // failed, or already converged
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < s;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const float *row = SA + i * ld;
+    double acc = 0.0;
+    for (int c = lane; c < n; c += 32) acc = fma((double)row[c], x[c], acc);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) r[i] = (double)row[n] - acc;
+  }
+}
+
+// part[chunk][c] = sum over the chunk's rows of SA[i, c] r_i (FP64), thread per column.
+__global__ void lsr_atr_kernel(const float *SA, int64_t s, int n, int64_t ld, const double *r, int64_t rows_per,
+                               double *part, const int *flags) {
+  if (flags[0] || flags[2]) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int64_t r0 = blockIdx.y * rows_per, r1 = min(s, r0 + rows_per);
+  double acc = 0.0;
+  for (int64_t i = r0; i < r1; ++i) acc = fma((double)SA[i * ld + c], r[i], acc);
+  part[(int64_t)blockIdx.y * n + c] = acc;
+}
+
+// One CTA: g = sum of the chunk partials; R^T y = g and R dx = y in 32-row blocks (one warp solves a diagonal
+// block, all threads update the rest); x += dx.  A correction below 1e-9 ||x|| ends the iteration early
+// (flags[2]); on the last step a correction larger than 1e-5 ||x|| (or not finite) sets flags[0] so that the
+// FP64 path takes over.  x is written out when the iteration ends.
+__global__ void __launch_bounds__(1024) lsr_refine_solve_kernel(const float *Rf, int n, const double *part,
+                                                                int chunks, double *xs, bool last, double *xout,
+                                                                int *flags) {
+  extern __shared__ float ysm[];  // n floats
+  __shared__ float red_dx[32], red_x[32];
+  __shared__ float Dsm[32][33];
+  if (flags[0] || flags[2]) return;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nb = (n + 31) / 32;
+  for (int c = t; c < n; c += blockDim.x) {
+    double g = 0.0;
+    for (int k = 0; k < chunks; ++k) g += part[(int64_t)k * n + c];
+    ysm[c] = (float)g;
+  }
+  __syncthreads();
+  // forward: R^T y = g
+  for (int B = 0; B < nb; ++B) {
+    const int base = 32 * B, bw = min(32, n - base);
+    {  // the diagonal block into shared memory (one element per thread), then one warp solves it
+      const int i = t >> 5, j = t & 31;
+      Dsm[i][j] = (i < bw && j < bw && i <= j) ? Rf[(int64_t)(base + i) * n + base + j] : (i == j ? 1.f : 0.f);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float v = lane < bw ? ysm[base + lane] : 0.f;
+      for (int k = 0; k < bw; ++k) {
+        const float yk = __shfl_sync(0xffffffffu, v, k) / Dsm[k][k];
+        if (lane == k) v = yk;
+        if (lane > k) v = fmaf(-Dsm[k][lane], yk, v);
+      }
+      if (lane < bw) ysm[base + lane] = v;
+    }
+    __syncthreads();
+    for (int c = base + bw + t; c < n; c += blockDim.x) {
+      float v = ysm[c];
+      for (int k = 0; k < bw; ++k) v = fmaf(-Rf[(int64_t)(base + k) * n + c], ysm[base + k], v);
+      ysm[c] = v;
+    }
+    __syncthreads();
+  }
+  // backward: R dx = y
+  for (int B = nb - 1; B >= 0; --B) {
+    const int base = 32 * B, bw = min(32, n - base);
+    {
+      const int i = t >> 5, j = t & 31;
+      Dsm[i][j] = (i < bw && j < bw && i <= j) ? Rf[(int64_t)(base + i) * n + base + j] : (i == j ? 1.f : 0.f);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float v = lane < bw ? ysm[base + lane] : 0.f;
+      for (int k = bw - 1; k >= 0; --k) {
+        const float dk = __shfl_sync(0xffffffffu, v, k) / Dsm[k][k];
+        if (lane == k) v = dk;
+        if (lane < k) v = fmaf(-Dsm[lane][k], dk, v);
+      }
+      if (lane < bw) ysm[base + lane] = v;
+    }
+    __syncthreads();
+    for (int i = t; i < base; i += blockDim.x) {
+      float v = ysm[i];
+      const float *row = Rf + (int64_t)i * n + base;
+      for (int k = 0; k < bw; ++k) v = fmaf(-row[k], ysm[base + k], v);
+      ysm[i] = v;
+    }
+    __syncthreads();
+  }
+  float mdx = 0.f, mx = 0.f;
+  for (int c = t; c < n; c += blockDim.x) {
+    const double nx = xs[c] + (double)ysm[c];
+    xs[c] = nx;
+    mdx = fmaxf(mdx, isfinite(ysm[c]) ? fabsf(ysm[c]) : INFINITY);
+    mx = fmaxf(mx, fabsf((float)nx));
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    mdx = fmaxf(mdx, __shfl_xor_sync(0xffffffffu, mdx, o));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (lane == 0) {
+    red_dx[warp] = mdx;
+    red_x[warp] = mx;
+  }
+  __syncthreads();
+  __shared__ int verdict;  // 0: continue, 1: converged, 2: failed
+  if (t == 0) {
+    float a = 0.f, b = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a = fmaxf(a, red_dx[w]);
+      b = fmaxf(b, red_x[w]);
+    }
+    verdict = (a <= 1e-9f * b) ? 1 : !last ? 0 : (a <= 1e-5f * b) ? 1 : 2;
+    if (verdict == 1) flags[2] = 1;
+    if (verdict == 2) flags[0] = 1;
+  }
+  __syncthreads();
+  if (verdict != 1) return;
+  for (int c = t; c < n; c += blockDim.x) xout[c] = xs[c];
+}
+
 // ----------------------------------------------------------------------------------------- host helpers
 
 int gram_chunks(int64_t m, int l, int num_sms) {
@@ -785,8 +944,9 @@ size_t gram_ws(int64_t m, int l, int num_sms) {
 
 // G (l x l FP64) = Y^T Y; fp64_products selects FP64 products (least squares) or FP32 products with FP64
 // sums across 32-row slices (CholeskyQR2).
+// With `gate`, the kernels run only if *gate is nonzero (decided on the device).
 int launch_gram(rmc_ctx *ctx, const float *Y, int64_t m, int l, int64_t ldy, double *G, double *part,
-                bool fp64_products = true) {
+                bool fp64_products = true, const int *gate = nullptr) {
   const int T = (l + GRAM_T - 1) / GRAM_T;
   const int pairs = T * (T + 1) / 2;
   const int chunks = gram_chunks(m, l, ctx->num_sms);
@@ -794,11 +954,11 @@ int launch_gram(rmc_ctx *ctx, const float *Y, int64_t m, int l, int64_t ldy, dou
   rows = (rows + GRAM_T - 1) / GRAM_T * GRAM_T;
   {
     RmcProf prof(ctx, RMC_K_GRAM);
-    if (fp64_products) gram_f64_kernel<<<dim3(pairs, chunks), 256, 0, ctx->stream>>>(Y, m, l, ldy, rows, part);
+    if (fp64_products) gram_f64_kernel<<<dim3(pairs, chunks), 256, 0, ctx->stream>>>(Y, m, l, ldy, rows, part, gate);
     else gram_f32_kernel<<<dim3(pairs, chunks), 256, 0, ctx->stream>>>(Y, m, l, ldy, rows, part);
   }
   rmc_note_launch(2);
-  gram_reduce_kernel<<<rmc_blocks((int64_t)l * l, 256, 1024), 256, 0, ctx->stream>>>(part, chunks, l, G);
+  gram_reduce_kernel<<<rmc_blocks((int64_t)l * l, 256, 1024), 256, 0, ctx->stream>>>(part, chunks, l, G, gate);
   RMC_LAUNCH_CHECK();
   return RMC_OK;
 }
@@ -1027,45 +1187,81 @@ int rmc_launch_rsvd_finish(rmc_ctx *ctx, const float *Q, int64_t m, int64_t l, c
 
 // ------------------------------------------------------------------------------------ least-squares solve
 
+constexpr int kRefineSteps = 4;
+
+static int atr_chunks(int64_t s) { return (int)std::min<int64_t>(64, std::max<int64_t>(1, s / 64)); }
+
+struct LsrBufs {
+  double *G, *xs, *r, *part, *gpart;
+  float *Rf;
+  int *flags;  // [0] FP32 path failed (FP64 takes over), [1] FP64 path failed, [2] refinement converged
+};
+
+static LsrBufs lsr_carve(WsCarve &w, int64_t s, int64_t n, int num_sms) {
+  LsrBufs b;
+  const int l = (int)n + 1;
+  b.G = w.take<double>((size_t)l * l);
+  b.flags = w.take<int>(4);
+  b.xs = w.take<double>(n);
+  b.r = w.take<double>(s);
+  b.part = w.take<double>((size_t)atr_chunks(s) * n);
+  b.Rf = w.take<float>((size_t)n * n);
+  b.gpart = reinterpret_cast<double *>(w.take<char>(gram_ws(s, l, num_sms)));
+  return b;
+}
+
 size_t rmc_lsr_solve_ws(int64_t s, int64_t n, int num_sms) {
   WsCarve w;
-  w.take<double>((n + 1) * (n + 1));
-  w.take<int>(4);
-  w.take<char>(gram_ws(s, (int)n + 1, num_sms));
+  lsr_carve(w, s, n, num_sms);
   return w.off;
 }
 
-int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n, int64_t ldsa, const float *Sb,
+int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n_, int64_t ldsa, const float *Sb,
                          double *x, void *ws) {
   // SA is s x (n+1) with ldsa >= n+1; column n receives Sb first.
   cudaStream_t st = ctx->stream;
-  const int l = (int)n + 1;
+  const int n = (int)n_, l = n + 1;
   WsCarve w;
   w.base = static_cast<char *>(ws);
-  double *G = w.take<double>((size_t)l * l);
-  int *fail = w.take<int>(4);
-  double *part = reinterpret_cast<double *>(w.take<char>(gram_ws(s, l, ctx->num_sms)));
+  const LsrBufs b = lsr_carve(w, s, n, ctx->num_sms);
   copy_column_kernel<<<rmc_blocks(s, 256, 1024), 256, 0, st>>>(Sb, s, const_cast<float *>(SA), ldsa, n);
   rmc_note_launch();
-  RMC_TRY(launch_gram(ctx, SA, s, l, ldsa, G, part));     // FP64 augmented Gram [S^T A, S^T b]^T [...]
-  // FP32 Cholesky of the leading n x n block in shared memory, then x refined against the FP64 Gram matrix
-  const size_t smem = lsr32_smem_bytes((int)n);
+  // FP32 products summed in FP64 across 32-row slices: the factor only preconditions the refinement
+  RMC_TRY(launch_gram(ctx, SA, s, l, ldsa, b.G, b.gpart, false));
   {
     RmcProf prof(ctx, RMC_K_SMALL);
-    if (smem > kMaxPackedBytes) {
-      force_fp64_kernel<<<1, 1, 0, st>>>(&fail[0]);
-    } else {
-      if (smem > 48 * 1024)
-        RMC_TRY_CUDA(cudaFuncSetAttribute(lsr_chol32_refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-      lsr_chol32_refine_kernel<<<1, 512, smem, st>>>(G, (int)n, x, 1, fail);
+    lsr_rf_init_kernel<<<rmc_blocks((int64_t)n * n, 256, 1024), 256, 0, st>>>(b.G, l, n, b.Rf, b.flags);
+    rmc_note_launch();
+    for (int j0 = 0; j0 < n; j0 += kPanel) {
+      const int bw = std::min(kPanel, n - j0), rest = n - j0 - bw;
+      lsr_chol_panel_kernel<<<std::max(1, (rest + 255) / 256), 256, 0, st>>>(b.Rf, n, j0, &b.flags[0]);
+      rmc_note_launch();
+      if (rest > 0) {
+        const int T = (rest + 63) / 64;
+        lsr_chol_update_kernel<<<T * (T + 1) / 2, 256, 0, st>>>(b.Rf, n, j0, &b.flags[0]);
+        rmc_note_launch();
+      }
     }
-    // FP64 fallback on the augmented matrix (returns at once unless the FP32 factorization failed)
-    RMC_TRY_CUDA(cudaMemsetAsync(&fail[1], 0, sizeof(int), st));
-    chol64_fallback_kernel<<<1, 1024, 0, st>>>(G, l, &fail[0], ctx->d_status, &fail[1]);
-    lsr_backsub_kernel<<<1, 32, sizeof(double) * n, st>>>(G, (int)n, x, &fail[0], &fail[1]);
+    RMC_TRY_CUDA(cudaMemsetAsync(b.xs, 0, sizeof(double) * n, st));
+    const int chunks = atr_chunks(s);
+    const int64_t rows_per = (s + chunks - 1) / chunks;
+    for (int it = 0; it < kRefineSteps; ++it) {
+      lsr_resid_kernel<<<rmc_blocks(s * 32, 256, 4096), 256, 0, st>>>(SA, s, n, ldsa, b.xs, b.r, b.flags);
+      lsr_atr_kernel<<<dim3((n + 255) / 256, chunks), 256, 0, st>>>(SA, s, n, ldsa, b.r, rows_per, b.part, b.flags);
+      lsr_refine_solve_kernel<<<1, 1024, sizeof(float) * n, st>>>(b.Rf, n, b.part, chunks, b.xs,
+                                                                  it == kRefineSteps - 1, x, b.flags);
+      rmc_note_launch(3);
+    }
   }
-  rmc_note_launch(3);
+  // FP64 path (every kernel returns at once unless flags[0] is set): FP64 Gram, FP64 Cholesky of the augmented
+  // matrix, back substitution
+  RMC_TRY(launch_gram(ctx, SA, s, l, ldsa, b.G, b.gpart, true, &b.flags[0]));
+  {
+    RmcProf prof(ctx, RMC_K_SMALL);
+    chol64_fallback_kernel<<<1, 1024, 0, st>>>(b.G, l, &b.flags[0], ctx->d_status, &b.flags[1]);
+    lsr_backsub_kernel<<<1, 32, sizeof(double) * n, st>>>(b.G, n, x, &b.flags[0], &b.flags[1]);
+  }
+  rmc_note_launch(2);
   RMC_LAUNCH_CHECK();
   return RMC_OK;
 }

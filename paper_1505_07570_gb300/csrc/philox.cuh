@@ -30,9 +30,11 @@ __device__ __forceinline__ uint4 philox_block(uint64_t seed, uint32_t stream, ui
                   (uint32_t)(seed >> 32));
 }
 
-// ((w >> 9) + 1/2) * 2^-23: exact in FP32, strictly inside (0, 1).
+// ((w >> 9) + 1/2) * 2^-23: exact in FP32, strictly inside (0, 1).  Built from the bit pattern of
+// 1 + (w >> 9) 2^-23 in [1, 2) minus (1 - 2^-24): the difference (2 (w >> 9) + 1) 2^-24 has at most 24
+// significant bits, so the subtraction is exact and no integer-to-float conversion is needed.
 __device__ __forceinline__ float unit_f32(uint32_t w) {
-  return __fmaf_rn((float)(w >> 9), 1.1920928955078125e-7f, 5.9604644775390625e-8f);
+  return __fsub_rn(__uint_as_float(0x3F800000u | (w >> 9)), 0.999999940395355224609375f);
 }
 
 // Box-Muller pair from two words: r = sqrt(-2 ln u_a), (r cos 2 pi u_b, r sin 2 pi u_b).

@@ -5,13 +5,16 @@
 //     C[r] = (1/sqrt(s)) sum_{i1} (H_N1)[r1, i1] T[i1, r2],   T[i1, r2] = sum_{i2} (H_N2)[r2, i2] g_i A[i],
 // and only the r2 that occur among the s sampled rows are needed.
 //
-// Stage 1 (one thread-block cluster per block of N2 = 4096 * C consecutive rows and per 4-column slab):
-//   each CTA loads 4096 rows x 4 columns straight into registers with the sign flip applied, transforms its
-//   12 low index bits in three register phases of four bits separated by two shared-memory transposes, and
-//   the cluster then combines the C CTAs (the top index bits of i2) for the needed r2 only, reading the
-//   peers' shared memory over DSMEM.  The result T[i1, slot(r2), slab] goes to a small buffer.
-// Stage 2: C[r] = (1/sqrt(s)) sum over the N1 blocks of +-T[i1, slot(r2)], one thread per (row, 4 columns).
-// A is read once; the intermediate holds N1 * |R2| rows, a small fraction of A when N2 >> s.
+// Stage 1 (persistent CTAs, in clusters of C CTAs per block of N2 = 4096 C rows; C = 1 is used): each CTA takes
+//   (4-column slab, block) items in turn, streams the next item's 4096 x 4 tile into shared memory with cp.async
+//   while it transforms the current one (sign flip, then its 12 index bits in three register phases of four
+//   bits separated by shared-memory transposes), and writes the transformed rows whose index r2 occurs in the
+//   sample to T[i1, slot(r2), slab].  (With C > 1 the cluster would first combine its CTAs over DSMEM.)
+// Stage 2: C[r] = (1/sqrt(s)) sum over the N1 = N / N2 blocks of +-T[i1, slot(r2)], one thread per (row,
+//   4 columns), eight loads in flight.
+// A is read once; T holds N1 * |R2| rows (|R2| <= min(s, N2)), written once and read about s / |R2| times.
+#include <algorithm>
+
 #include <cooperative_groups.h>
 
 #include "rmc_internal.cuh"
@@ -24,7 +27,6 @@ namespace {
 
 constexpr int kRowsCta = 4096;   // rows transformed by one CTA (12 index bits)
 constexpr int kThreads = 256;    // 16 rows x 4 columns per thread
-constexpr int kMaxCluster = 8;
 
 // shared-memory slot of local row r: XOR the low 3 bits with bits 4..6 (conflict-free float4 phases)
 __device__ __forceinline__ int swz(int r) { return r ^ ((r >> 4) & 7); }
@@ -71,75 +73,114 @@ __global__ void srht_signs_kernel(uint64_t seed, uint32_t instance, int64_t m, u
   }
 }
 
-// grid: x = slab * C + rank (cluster of C along x), y = i1.  T out: [N1][umax][slabs] float4, rows u < *U valid.
-__global__ void __launch_bounds__(kThreads) srht_stage1_kernel(const float *__restrict__ A, int64_t m, int64_t n,
-                                                                int64_t lda, const float *__restrict__ b,
-                                                                const uint32_t *__restrict__ sign_bits, int csize,
-                                                                const uint32_t *__restrict__ r2_list,
-                                                                const int *__restrict__ U_ptr, int64_t umax,
-                                                                int64_t slabs, float4 *__restrict__ T, bool vec) {
-  extern __shared__ float4 sm[];   // kRowsCta float4, swizzled
+__device__ __forceinline__ void cp_async16(float4 *dst, const void *src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(bytes)
+               : "memory");
+}
+
+// Persistent stage 1.  Cluster k of the grid (C CTAs) takes items k, k + #clusters, ... where an item is one
+// (slab, i1) pair; CTA `rank` of the cluster transforms rows [i1 N2 + rank 4096, + 4096) of the slab.  Each CTA
+// double-buffers its 4096 x 4 tile in shared memory: the rows of the next item stream in with cp.async while
+// the current one is transformed and combined.  T out: [N1][umax][slabs] float4, rows u < *U valid.
+__global__ void __launch_bounds__(kThreads, 1) srht_stage1_kernel(const float *__restrict__ A, int64_t m, int64_t n,
+                                                                   int64_t lda, const float *__restrict__ b,
+                                                                   const uint32_t *__restrict__ sign_bits, int csize,
+                                                                   const uint32_t *__restrict__ r2_list,
+                                                                   const int *__restrict__ U_ptr, int64_t umax,
+                                                                   int64_t slabs, int64_t N1, float4 *__restrict__ T,
+                                                                   bool vec) {
+  extern __shared__ float4 sm[];   // two buffers of kRowsCta float4, swizzled
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
-  const int64_t slab = blockIdx.x / csize;
-  const int64_t i1 = blockIdx.y;
+  const int64_t nclusters = gridDim.x / csize, cid = blockIdx.x / csize;
+  const int64_t items = slabs * N1;
   const int64_t N2 = (int64_t)kRowsCta * csize;
-  const int64_t row_base = i1 * N2 + (int64_t)rank * kRowsCta;
   const int t = threadIdx.x;
-  const int64_t c0 = slab * 4;
-
-  // phase 1: rows t*16 + j, transform bits 0..3
-  float4 v[16];
-  const int64_t row16 = row_base + t * 16;
-  const uint32_t gw = row16 < m ? __ldg(sign_bits + row16 / 32) >> (row16 & 31) : 0u;
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int64_t row = row16 + j;
-    float4 x = load_slab(A, m, n, lda, b, row, c0, vec);
-    if ((gw >> j) & 1u) x = make_float4(-x.x, -x.y, -x.z, -x.w);
-    v[j] = x;
-  }
-  fwht16(v);
-#pragma unroll
-  for (int j = 0; j < 16; ++j) sm[swz(t * 16 + j)] = v[j];
-  __syncthreads();
-  // phase 2: bits 4..7 in registers; thread owns bits 0..3 and 8..11
-  {
-    const int lo = t & 15, hi = t >> 4;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = sm[swz(lo | (j << 4) | (hi << 8))];
-    fwht16(v);
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < 16; ++j) sm[swz(lo | (j << 4) | (hi << 8))] = v[j];
-  }
-  __syncthreads();
-  // phase 3: bits 8..11 in registers; thread owns bits 0..7
-  {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = sm[swz(t | (j << 8))];
-    fwht16(v);
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < 16; ++j) sm[swz(t | (j << 8))] = v[j];
-  }
-  // every CTA of the cluster has its 4096-point transform in shared memory
-  cluster.sync();
-  // combine over the cluster (index bits 12.. of i2) for the needed r2, split across the cluster's CTAs
-  float4 *Tout = T + i1 * umax * slabs;
   const int U = *U_ptr;
-  for (int u = rank + csize * t; u < U; u += csize * kThreads) {
-    const uint32_t r2 = r2_list[u];
-    const int lo = (int)(r2 & (kRowsCta - 1));
-    const int hi = (int)(r2 >> 12);
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int c = 0; c < csize; ++c) {
-      const float4 *peer = cluster.map_shared_rank(sm, c);
-      const float4 x = peer[swz(lo)];
-      const float sg = (__popc(hi & c) & 1) ? -1.f : 1.f;
-      acc = make_float4(fmaf(sg, x.x, acc.x), fmaf(sg, x.y, acc.y), fmaf(sg, x.z, acc.z), fmaf(sg, x.w, acc.w));
+
+  auto issue = [&](int64_t item, float4 *buf) {
+    const int64_t slab = item % slabs, i1 = item / slabs;
+    const int64_t row16 = i1 * N2 + (int64_t)rank * kRowsCta + t * 16;
+    const int64_t c0 = slab * 4;
+    if (vec && c0 + 3 < n) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int64_t row = row16 + j;
+        cp_async16(buf + swz(t * 16 + j), row < m ? (const void *)(A + row * lda + c0) : (const void *)A,
+                   row < m ? 16 : 0);
+      }
+    } else {  // the slab holding b, or unaligned rows: plain loads
+#pragma unroll
+      for (int j = 0; j < 16; ++j) buf[swz(t * 16 + j)] = load_slab(A, m, n, lda, b, row16 + j, c0, vec);
     }
-    Tout[(int64_t)u * slabs + slab] = acc;
+  };
+
+  int64_t item = cid;
+  int cur = 0;
+  if (item < items) issue(item, sm);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (; item < items; item += nclusters, cur ^= 1) {
+    float4 *S = sm + cur * kRowsCta;
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    // every CTA of the cluster is done reading the other buffer (the previous combine) before it is refilled
+    cluster.sync();
+    if (item + nclusters < items) issue(item + nclusters, sm + (cur ^ 1) * kRowsCta);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+
+    const int64_t slab = item % slabs, i1 = item / slabs;
+    float4 v[16];
+    // phase 1: rows t*16 + j, sign flip, bits 0..3
+    {
+      const int64_t row16 = i1 * N2 + (int64_t)rank * kRowsCta + t * 16;
+      const uint32_t gw = row16 < m ? __ldg(sign_bits + row16 / 32) >> (row16 & 31) : 0u;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        float4 x = S[swz(t * 16 + j)];
+        if ((gw >> j) & 1u) x = make_float4(-x.x, -x.y, -x.z, -x.w);
+        v[j] = x;
+      }
+      fwht16(v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) S[swz(t * 16 + j)] = v[j];
+    }
+    __syncthreads();
+    // phase 2: bits 4..7 (each thread rewrites exactly the slots it read)
+    {
+      const int lo = t & 15, hi = t >> 4;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = S[swz(lo | (j << 4) | (hi << 8))];
+      fwht16(v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) S[swz(lo | (j << 4) | (hi << 8))] = v[j];
+    }
+    __syncthreads();
+    // phase 3: bits 8..11
+    {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = S[swz(t | (j << 8))];
+      fwht16(v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) S[swz(t | (j << 8))] = v[j];
+    }
+    // every CTA of the cluster has its 4096-point transform of this item in shared memory
+    cluster.sync();
+    // combine over the cluster (index bits 12.. of i2) for the needed r2, split across the cluster's CTAs
+    float4 *Tout = T + i1 * umax * slabs;
+    for (int u = rank + csize * t; u < U; u += csize * kThreads) {
+      const uint32_t r2 = r2_list[u];
+      const int lo = (int)(r2 & (kRowsCta - 1));
+      const int hi = (int)(r2 >> 12);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int c = 0; c < csize; ++c) {
+        const float4 *peer = cluster.map_shared_rank(S, c);
+        const float4 x = peer[swz(lo)];
+        const float sg = (__popc(hi & c) & 1) ? -1.f : 1.f;
+        acc = make_float4(fmaf(sg, x.x, acc.x), fmaf(sg, x.y, acc.y), fmaf(sg, x.z, acc.z), fmaf(sg, x.w, acc.w));
+      }
+      Tout[(int64_t)u * slabs + slab] = acc;
+    }
   }
   // keep this CTA's shared memory alive until every peer has read it
   cluster.sync();
@@ -157,8 +198,9 @@ __global__ void srht_stage2_kernel(const float4 *__restrict__ T, int64_t N1, int
     const int64_t r1 = r / N2;
     const uint32_t u = slot[r % N2];
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int64_t i1 = 0; i1 < N1; ++i1) {
-      const float4 x = T[(i1 * umax + u) * slabs + sl];
+#pragma unroll 8
+    for (int64_t i1 = 0; i1 < N1; ++i1) {  // unrolled: eight independent loads in flight per thread
+      const float4 x = __ldg(&T[(i1 * umax + u) * slabs + sl]);
       const float sg = (__popcll(r1 & i1) & 1) ? -1.f : 1.f;
       acc = make_float4(fmaf(sg, x.x, acc.x), fmaf(sg, x.y, acc.y), fmaf(sg, x.z, acc.z), fmaf(sg, x.w, acc.w));
     }
@@ -215,11 +257,11 @@ SrhtPlan srht_plan(int64_t m, int64_t ntot) {
   SrhtPlan p;
   p.N = 1;
   while (p.N < m) p.N <<= 1;
-  int64_t c = p.N / kRowsCta;
-  if (c < 1) c = 1;
-  if (c > kMaxCluster) c = kMaxCluster;
-  p.csize = (int)c;
-  p.N2 = (int64_t)kRowsCta * c;
+  // One CTA per 4096-row block: a cluster that combines several blocks over DSMEM moves about as many bytes
+  // between shared memories as it reads from HBM and waits on two cluster barriers per tile, which measured
+  // slower than writing the needed rows of each block and combining N / 4096 blocks in stage 2.
+  p.csize = 1;
+  p.N2 = (int64_t)kRowsCta * p.csize;
   p.N1 = p.N > p.N2 ? p.N / p.N2 : 1;
   p.slabs = (ntot + 3) / 4;
   return p;
@@ -275,10 +317,9 @@ int rmc_launch_srht(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t 
   const int64_t umax = s < p.N2 ? s : p.N2;
 
   const bool vec = (lda % 4 == 0) && (reinterpret_cast<uintptr_t>(A) % 16 == 0);
-  const size_t smem = sizeof(float4) * kRowsCta;
+  const size_t smem = 2 * sizeof(float4) * kRowsCta;
   RMC_TRY_CUDA(cudaFuncSetAttribute(srht_stage1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(p.slabs * p.csize), (unsigned)p.N1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
@@ -289,12 +330,22 @@ int rmc_launch_srht(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  // as many clusters as are co-resident (one CTA per SM), each looping over (slab, i1) items
+  const int64_t items = p.slabs * p.N1;
+  cfg.gridDim = dim3((unsigned)p.csize, 1, 1);
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, srht_stage1_kernel, &cfg) != cudaSuccess || nclusters < 1) {
+    (void)cudaGetLastError();
+    nclusters = std::max(1, ctx->num_sms / (2 * p.csize));
+  }
+  if (nclusters > items) nclusters = (int)items;
+  cfg.gridDim = dim3((unsigned)(nclusters * p.csize), 1, 1);
   rmc_note_launch(2);
   {
     RmcProf prof(ctx, RMC_K_SRHT);
     RMC_TRY_CUDA(cudaLaunchKernelEx(&cfg, srht_stage1_kernel, A, m, n, lda, b, (const uint32_t *)bf.sign_bits,
-                                    p.csize, (const uint32_t *)bf.list, (const int *)bf.U, umax, p.slabs, bf.T,
-                                    vec));
+                                    p.csize, (const uint32_t *)bf.list, (const int *)bf.U, umax, p.slabs, p.N1,
+                                    bf.T, vec));
   }
   const float scale = 1.0f / sqrtf((float)s);
   RmcProf prof(ctx, RMC_K_SRHT_REDUCE);
