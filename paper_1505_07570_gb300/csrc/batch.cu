@@ -23,14 +23,17 @@
 
 #include "philox.cuh"
 #include "rmc_internal.cuh"
+#include "tc_common.cuh"
 
 namespace {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kStages = 3;
-constexpr int kStageFloats = 10880;  // one stage of the row-tile ring (42.5 KB)
-constexpr int kPartFloats = 12288;   // k-split partial products, the product tile, small-SVD matrices (48 KB)
+// Two large stages: the cost of a tile is dominated by its barriers and short dependent phases, not by load
+// latency (one tile of ~73 KB in flight already streams at this SM's share of HBM), so fewer, larger tiles win.
+constexpr int kStages = 2;
+constexpr int kStageFloats = 18752;  // one stage of the row-tile ring (73.25 KB)
+constexpr int kPartFloats = 8192;    // k-split partial products, the product tile, small-SVD matrices (32 KB)
 constexpr int kZFloats = 256 * 32;   // Omega / Z / B^T / Q2, n x l (32 KB)
 constexpr int kSmallFloats = 4096;   // T^-1 and R^-1 (FP32, 32 x 32) and the FP64 Gram matrix (32 x 32)
 constexpr int kSmemFloats = kStages * kStageFloats + kPartFloats + kZFloats + kSmallFloats;
@@ -99,42 +102,102 @@ __device__ __forceinline__ void st_vec(float *p, const float (&v)[C]) {
 __device__ __forceinline__ float f4(const float4 &a, int i) { return i == 0 ? a.x : i == 1 ? a.y : i == 2 ? a.z : a.w; }
 
 // Rows [r0, r0 + R) of a row-major matrix (leading dimension ld) into shared memory with row stride S:
-// columns [0, ncols), zeros in the padding up to the next multiple of 4 and in rows at or past `rows`.
+// columns [0, ncols), zeros in columns [ncols, npad) (npad a multiple of 4) and in rows at or past `rows`.
 __device__ __forceinline__ void load_rows(float *dst, int S, const float *src, int64_t ld, int r0, int R, int rows,
-                                          int ncols, bool vec) {
-  const int nq = (ncols + 3) >> 2, total = R * nq;
+                                          int ncols, int npad, bool vec) {
+  const int nq = npad >> 2, total = R * nq;
+  // element e = threadIdx.x + k kThreads is (row r, quad q) with e = r nq + q, stepped without a division per
+  // element (a runtime division costs tens of instructions, more than the copy itself)
+  const int dr = kThreads / nq, dq = kThreads - dr * nq;
+  int r = threadIdx.x / nq, q = threadIdx.x - r * nq;
   for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int r = e / nq, c = (e - r * nq) << 2;
+    const int c = q << 2;
     float *d = dst + r * S + c;
     const bool ok = r0 + r < rows;
     const float *s = ok ? src + (int64_t)(r0 + r) * ld + c : src;
-    const int cnt = ok ? min(4, ncols - c) : 0;
+    const int cnt = ok ? max(0, min(4, ncols - c)) : 0;
     if (vec) {
-      cp16(d, s, cnt * 4);
+      cp16(d, cnt ? s : src, cnt * 4);
     } else {
 #pragma unroll
       for (int u = 0; u < 4; ++u) cp4(d + u, u < cnt ? s + u : src, u < cnt ? 4 : 0);
     }
+    r += dr;
+    q += dq;
+    if (q >= nq) {
+      q -= nq;
+      ++r;
+    }
   }
 }
 
-// Stream rows [0, rows) in tiles of R rows through the three-stage ring: load(stage, r0) issues one tile's
-// copies, use(stage, r0) consumes it (every thread takes part in both).  Loads run two tiles ahead.
+// One bulk (TMA) copy global -> shared, completing on an mbarrier (both addresses 16-byte aligned, bytes a
+// multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   tc::smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+               : "memory");
+}
+
+// Rows [r0, r0 + R) of a matrix whose rows are contiguous (leading dimension == ncols) and whose tile start is
+// 16-byte aligned (R ncols a multiple of 4): one span of R ncols floats into a dense tile (row stride ncols).
+// Thread 0 issues the 16-byte-multiple prefix as one bulk copy; all threads fill the rest of the tile and a
+// 16-float tail (the < 4 leftover floats from global memory, zeros past the valid rows).  Returns the bytes
+// the bulk copy will deliver (the caller arms the mbarrier with them).
+struct Span {
+  float *dst;
+  const float *src;
+  uint32_t bytes;
+};
+__device__ __forceinline__ Span span_tile(float *dst, const float *src, int r0, int R, int rows, int ncols) {
+  const int64_t base = (int64_t)r0 * ncols;
+  const int span = max(0, min(R, rows - r0)) * ncols, pre = span & ~3;
+  for (int f = pre + threadIdx.x; f < R * ncols + 16; f += kThreads) dst[f] = f < span ? src[base + f] : 0.f;
+  return Span{dst, src + base, (uint32_t)pre * 4u};
+}
+
+// Thread 0: arm the stage's mbarrier with the spans' bytes and issue their bulk copies (spans of 0 bytes skip).
+__device__ __forceinline__ void issue_spans(uint64_t *bar, Span a, Span b = Span{nullptr, nullptr, 0u}) {
+  if (threadIdx.x != 0) return;
+  tc::fence_proxy_async_smem();  // this stage's earlier generic accesses come before the async writes
+  tc::mbar_arrive_expect_tx(bar, a.bytes + b.bytes);
+  if (a.bytes) bulk_g2s(a.dst, a.src, a.bytes, bar);
+  if (b.bytes) bulk_g2s(b.dst, b.src, b.bytes, bar);
+}
+
+// The row-tile ring: kStages stages in shared memory with one mbarrier each.  Every load arms its stage's
+// mbarrier exactly once (with 0 bytes when it used cp.async only), so the barrier phases stay in step.
+struct Ring {
+  float *buf;
+  uint64_t *full;
+  uint32_t phase;  // bit s: parity of the next completion of stage s
+};
+
+// Stream rows [0, rows) in tiles of R rows: load(stage, r0, bar) issues one tile (cp.async by all threads and/or
+// spans via issue_spans), use(stage, r0) consumes it.  Loads run kStages - 1 tiles ahead.  Thread 0 waits on the
+// mbarrier (bounded: RMC_ETIMEOUT to *status) and a CTA barrier passes the tile on.
 template <class Load, class Use>
-__device__ __forceinline__ void stream_tiles(float *ring, int rows, int R, Load load, Use use) {
+__device__ __forceinline__ void stream_tiles(Ring &rg, int rows, int R, int *status, Load load, Use use) {
   const int T = (rows + R - 1) / R;
 #pragma unroll 1
-  for (int s = 0; s < 2; ++s) {
-    if (s < T) load(ring + s * kStageFloats, s * R);
+  for (int s = 0; s < kStages - 1; ++s) {
+    if (s < T) load(rg.buf + s * kStageFloats, s * R, &rg.full[s]);
     cp_commit();
   }
 #pragma unroll 1
   for (int t = 0; t < T; ++t) {
-    cp_wait<1>();
+    const int st = t % kStages;
+    cp_wait<kStages - 2>();
+    if (threadIdx.x == 0 && !tc::mbar_wait(&rg.full[st], (rg.phase >> st) & 1u)) rmc_report(status, RMC_ETIMEOUT);
+    rg.phase ^= 1u << st;
     __syncthreads();  // tile t is in; every thread is done with tile t - 1, whose stage is refilled next
-    if (t + 2 < T) load(ring + ((t + 2) % kStages) * kStageFloats, (t + 2) * R);
+    if (t + kStages - 1 < T) {
+      const int sn = (t + kStages - 1) % kStages;
+      load(rg.buf + sn * kStageFloats, (t + kStages - 1) * R, &rg.full[sn]);
+    }
     cp_commit();
-    use(ring + (t % kStages) * kStageFloats, t * R);
+    use(rg.buf + st * kStageFloats, t * R);
   }
   cp_wait<0>();
   __syncthreads();
@@ -142,44 +205,91 @@ __device__ __forceinline__ void stream_tiles(float *ring, int rows, int R, Load 
 
 // ------------------------------------------------------------------------- products out of row tiles
 
-// P[slice] (R x LP) = A_tile[:, slice's columns] Z[slice's rows, :].  Thread (slice, row quad, column group):
-// rows rq + i R/4 (i < 4), columns jg TN .. jg TN + TN - 1.
+// Warp-level tensor-core products in FP32 accuracy: mma.sync m16n8k8 on TF32 operands, each operand split into a
+// TF32 high part and a TF32 remainder, D += A_lo B_hi + A_hi B_lo + A_hi B_hi (the A_lo B_lo term, below 2^-22 of
+// the product, is dropped).  Fragment layout of m16n8k8 (g = lane / 4, t = lane % 4): A a0 (g, t), a1 (g + 8, t),
+// a2 (g, t + 4), a3 (g + 8, t + 4); B b0 (k = t, n = g), b1 (k = t + 4, n = g); C c0 (g, 2t), c1 (g, 2t + 1),
+// c2 (g + 8, 2t), c3 (g + 8, 2t + 1).
+// TF32 rounding to nearest, ties away from zero (the rounding of cvt.rna.tf32.f32), on the bit pattern with integer
+// operations, which issue at a much higher rate than the conversion instruction.  Finite inputs only.
+__device__ __forceinline__ uint32_t tf32_rna(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4], float b0,
+                                     float b1) {
+  uint32_t bh0, bl0, bh1, bl1;
+  split_tf32(b0, bh0, bl0);
+  split_tf32(b1, bh1, bl1);
+  mma_tf32(d, al, bh0, bh1);  // small terms first
+  mma_tf32(d, ah, bl0, bl1);
+  mma_tf32(d, ah, bh0, bh1);
+}
+
+// P[ks] (R x LP) = A_tile[:, k-steps of slice ks] Z[those rows, :]: warp unit (16-row block mb, k slice ks),
+// all LP / 8 column blocks, k-steps of 8 columns of A.
 template <int TN>
-__device__ __forceinline__ void tile_times_z(const float *At, int S, int R, int KS, int qper, int nq, const float *Z,
-                                             float *P) {
-  constexpr int LP = 4 * TN;
-  const int t = threadIdx.x;
-  if (t >= KS * R) return;
-  const int slice = t / R, u = t - slice * R;
-  const int R4 = R >> 2, rq = u >> 2, jg = u & 3;
-  const int q0 = slice * qper, q1 = min(nq, q0 + qper);
-  float acc[4][TN];
+__device__ __forceinline__ void tile_times_z(const float *At, int S, int R, int ksplit, int kb_per, int KB,
+                                             const float *Z, float *P) {
+  constexpr int LP = 4 * TN, NB = LP / 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int MB = R >> 4;
+  for (int u = warp; u < MB * ksplit; u += kWarps) {
+    const int mb = u % MB, ks = u / MB;
+    const int k0 = ks * kb_per, k1 = min(KB, k0 + kb_per);
+    float acc[NB][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int nb = 0; nb < NB; ++nb) acc[nb][0] = acc[nb][1] = acc[nb][2] = acc[nb][3] = 0.f;
+    const float *ap = At + (mb * 16 + g) * S + t;
+    const float *zp = Z + t * LP + g;
+#pragma unroll 2
+    for (int kb = k0; kb < k1; ++kb) {
+      const float *a = ap + kb * 8;
+      uint32_t ah[4], al[4];
+      split_tf32(a[0], ah[0], al[0]);
+      split_tf32(a[8 * S], ah[1], al[1]);
+      split_tf32(a[4], ah[2], al[2]);
+      split_tf32(a[8 * S + 4], ah[3], al[3]);
+      const float *z = zp + kb * 8 * LP;
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
-  const float *a0 = At + rq * S;
-  const float *z0 = Z + jg * TN;
-#pragma unroll 1
-  for (int qd = q0; qd < q1; ++qd) {
-    float4 a[4];
+      for (int nb = 0; nb < NB; ++nb) mma3(acc[nb], ah, al, z[nb * 8], z[4 * LP + nb * 8]);
+    }
+    float *pp = P + (size_t)ks * R * LP + (mb * 16 + g) * LP + 2 * t;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4 *>(a0 + i * R4 * S + 4 * qd);
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      float zv[TN];
-      ld_vec<TN>(z0 + (4 * qd + kk) * LP, zv);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float av = f4(a[i], kk);
-#pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av, zv[j], acc[i][j]);
-      }
+    for (int nb = 0; nb < NB; ++nb) {
+      *reinterpret_cast<float2 *>(pp + nb * 8) = make_float2(acc[nb][0], acc[nb][1]);
+      *reinterpret_cast<float2 *>(pp + 8 * LP + nb * 8) = make_float2(acc[nb][2], acc[nb][3]);
     }
   }
-  float *dst = P + slice * R * LP + jg * TN;
+}
+
+// acc (warp unit: 16 columns of A in block mb, k-steps kb = rs, rs + RS, ...) += A_tile^T Y_tile: the m16 x n8
+// blocks of W^T (columns of A x LP).
+template <int TN>
+__device__ __forceinline__ void at_times_y(const float *At, int S, const float *Yt, int R, int mb, int rs, int RS,
+                                           float (&acc)[TN / 2][4]) {
+  constexpr int LP = 4 * TN, NB = LP / 8;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const float *ap = At + t * S + mb * 16 + g;
+  const float *yp = Yt + t * LP + g;
+#pragma unroll 2
+  for (int kb = rs; kb < (R >> 3); kb += RS) {
+    const float *a = ap + kb * 8 * S;
+    uint32_t ah[4], al[4];
+    split_tf32(a[0], ah[0], al[0]);
+    split_tf32(a[8], ah[1], al[1]);
+    split_tf32(a[4 * S], ah[2], al[2]);
+    split_tf32(a[4 * S + 8], ah[3], al[3]);
+    const float *y = yp + kb * 8 * LP;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) st_vec<TN>(dst + (rq + i * R4) * LP, acc[i]);
+    for (int nb = 0; nb < NB; ++nb) mma3(acc[nb], ah, al, y[nb * 8], y[4 * LP + nb * 8]);
+  }
 }
 
 // Sum the KS slices of P into slice 0, in slice order.
@@ -388,27 +498,36 @@ __device__ void jacobi_small(float *W, float *V, int l, int *flag, int *status) 
 // ------------------------------------------------------------------------------------- rsvd problem
 
 struct RsvdGeo {
-  int m, n, n4, nq, S, R, KS, qper, GY, GW, R2;
+  int m, n, nz, S, R, MB, KB, ksplit, kb_per, GY, MBW, RS, R2, yoff;
+  bool dense;
 };
 
 template <int TN>
-__device__ void rsvd_problem(const BatchItem &it, float *sm, int *flag, int *status) {
+__device__ void rsvd_problem(const BatchItem &it, float *sm, Ring &rg, int *flag, int *status) {
   constexpr int LP = 4 * TN;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int l = it.k + it.p, k = it.k;
   RsvdGeo g;
   g.m = it.m;
   g.n = it.n;
-  g.n4 = (g.n + 3) & ~3;
-  g.nq = g.n4 >> 2;
-  g.S = (g.n4 & 7) ? g.n4 : g.n4 + 4;  // row stride of A tiles: 4 mod 8, so 8 rows hit 8 different bank quads
-  g.R = min(256, kStageFloats / (g.S + LP)) & ~3;
-  g.KS = max(1, min(kThreads / g.R, kPartFloats / (g.R * LP)));
-  g.qper = (g.nq + g.KS - 1) / g.KS;
-  g.KS = (g.nq + g.qper - 1) / g.qper;
-  g.GY = kThreads / LP;          // row groups of the Gram accumulation (4 TN threads per group)
-  g.GW = kThreads / (4 * g.nq);  // row groups of the X^T A accumulation
-  g.R2 = min(256, kStageFloats / LP) & ~3;
+  g.nz = (g.n + 15) & ~15;  // Z rows and A tile columns, zero-padded to whole 16-column MMA blocks
+  // Contiguous A: each tile is one 16-byte aligned span copied into a dense tile (row stride n); the columns
+  // n..nz-1 the MMAs read then hold the next row's (finite) values, which meet zero rows of Z in A Z, and the
+  // rows c >= n of A^T Y are dropped.  Otherwise rows go one by one into a zero-padded tile (stride nz + 4,
+  // which puts the 8 rows of an A fragment in 8 different bank quads).
+  g.dense = it.lda == it.n && (reinterpret_cast<uintptr_t>(it.A) & 15) == 0;
+  g.S = g.dense ? g.n : g.nz + 4;
+  g.R = min(256, (kStageFloats - 32) / (g.S + LP)) & ~15;  // A span + Y span, each with a 16-float tail
+  g.yoff = g.R * g.S + (g.dense ? 16 : 0);  // where the W pass puts the Y tile in a stage
+  g.MB = g.R >> 4;
+  g.KB = g.nz >> 3;
+  g.ksplit = max(1, min(kWarps / g.MB, g.KB));
+  g.kb_per = (g.KB + g.ksplit - 1) / g.ksplit;
+  g.ksplit = (g.KB + g.kb_per - 1) / g.kb_per;
+  g.GY = kThreads / LP;           // row groups of the Gram accumulation (4 TN threads per group)
+  g.MBW = g.nz >> 4;              // 16-column blocks of A in the W^T = A^T Y product
+  g.RS = max(1, kWarps / g.MBW);  // k-step groups per column block
+  g.R2 = min(256, (kStageFloats - 16) / LP) & ~3;
 
   float *ring = sm;
   float *P = sm + kStages * kStageFloats;
@@ -422,7 +541,7 @@ __device__ void rsvd_problem(const BatchItem &it, float *sm, int *flag, int *sta
   const bool vec = it.vec != 0;
 
   // Omega (n x l): Gaussian block (r, c/4) of the same Philox stream as the single-problem path
-  for (int e = t; e < g.n4 * LP; e += kThreads) Z[e] = 0.f;
+  for (int e = t; e < g.nz * LP; e += kThreads) Z[e] = 0.f;
   __syncthreads();
   {
     const int gl = (l + 3) >> 2;
@@ -452,12 +571,19 @@ __device__ void rsvd_problem(const BatchItem &it, float *sm, int *flag, int *sta
     float gtot[TN][4];
     zero_acc<TN>(gtot);
     stream_tiles(
-        ring, g.m, g.R,
-        [&](float *st, int r0) { load_rows(st, g.S, A, lda, r0, g.R, g.m, g.n, vec); },
+        rg, g.m, g.R, status,
+        [&](float *st, int r0, uint64_t *bar) {
+          if (g.dense) {
+            issue_spans(bar, span_tile(st, A, r0, g.R, g.m, g.n));
+          } else {
+            load_rows(st, g.S, A, lda, r0, g.R, g.m, g.n, g.nz, vec);
+            issue_spans(bar, Span{nullptr, nullptr, 0u});
+          }
+        },
         [&](float *st, int r0) {
-          tile_times_z<TN>(st, g.S, g.R, g.KS, g.qper, g.nq, Z, P);
+          tile_times_z<TN>(st, g.S, g.R, g.ksplit, g.kb_per, g.KB, Z, P);
           __syncthreads();
-          reduce_slices(P, g.R * LP / 4, g.KS);
+          reduce_slices(P, g.R * LP / 4, g.ksplit);
           __syncthreads();
           const int rv = min(g.R, g.m - r0);
           float4 *dst = reinterpret_cast<float4 *>(Yg + (size_t)r0 * LP);
@@ -476,8 +602,8 @@ __device__ void rsvd_problem(const BatchItem &it, float *sm, int *flag, int *sta
     float gtot[TN][4];
     zero_acc<TN>(gtot);
     stream_tiles(
-        ring, g.m, g.R2,
-        [&](float *st, int r0) { load_rows(st, LP, Yg, LP, r0, g.R2, g.m, LP, true); },
+        rg, g.m, g.R2, status,
+        [&](float *st, int r0, uint64_t *bar) { issue_spans(bar, span_tile(st, Yg, r0, g.R2, g.m, LP)); },
         [&](float *st, int r0) {
           const int rv = min(g.R2, g.m - r0);
           rows_times<TN, true>(st, rv, R1i);
@@ -493,47 +619,60 @@ __device__ void rsvd_problem(const BatchItem &it, float *sm, int *flag, int *sta
     finish_gram(gtot, Rout, Riout);
   };
 
-  // Z = (Yg Tinv)^T A transposed, i.e. Z[c][i] = sum_j Tinv[j][i] (Yg^T A)[j][c]  (n x l)
+  // Z = (Yg Tinv)^T A transposed, i.e. Z[c][i] = sum_j Tinv[j][i] (A^T Yg)[c][j]  (n x l)
   auto w_pass = [&]() {
-    float wtot[TN][4];
-    zero_acc<TN>(wtot);
+    float acc[TN / 2][4];
+#pragma unroll
+    for (int nb = 0; nb < TN / 2; ++nb) acc[nb][0] = acc[nb][1] = acc[nb][2] = acc[nb][3] = 0.f;
+    const int mb = warp % g.MBW, rs = warp / g.MBW;
+    const bool active = warp < g.MBW * g.RS;
     stream_tiles(
-        ring, g.m, g.R,
-        [&](float *st, int r0) {
-          load_rows(st, g.S, A, lda, r0, g.R, g.m, g.n, vec);
-          load_rows(st + g.R * g.S, LP, Yg, LP, r0, g.R, g.m, LP, true);
+        rg, g.m, g.R, status,
+        [&](float *st, int r0, uint64_t *bar) {
+          const Span y = span_tile(st + g.yoff, Yg, r0, g.R, g.m, LP);
+          if (g.dense) {
+            issue_spans(bar, span_tile(st, A, r0, g.R, g.m, g.n), y);
+          } else {
+            load_rows(st, g.S, A, lda, r0, g.R, g.m, g.n, g.nz, vec);
+            issue_spans(bar, y);
+          }
         },
         [&](float *st, int r0) {
-          float wt[TN][4];
-          zero_acc<TN>(wt);
-          xt_accum<TN>(st + g.R * g.S, LP, st, g.S, g.R, g.nq, g.GW, wt);
-          add_acc<TN>(wtot, wt);
+          if (active) at_times_y<TN>(st, g.S, st + g.yoff, g.R, mb, rs, g.RS, acc);
         });
-    dump_acc<TN>(ring, g.nq, g.GW, wtot);
+    // W^T partials of each k-step group: scr[rs][c][j] (nz x LP), then summed in group order into P
+    if (active) {
+      const int gq = lane >> 2, tq = lane & 3;
+      float *d = ring + (size_t)rs * g.nz * LP + (mb * 16 + gq) * LP + 2 * tq;
+#pragma unroll
+      for (int nb = 0; nb < TN / 2; ++nb) {
+        *reinterpret_cast<float2 *>(d + nb * 8) = make_float2(acc[nb][0], acc[nb][1]);
+        *reinterpret_cast<float2 *>(d + 8 * LP + nb * 8) = make_float2(acc[nb][2], acc[nb][3]);
+      }
+    }
     __syncthreads();
-    // W (LP x n4) = sum over groups, into P
-    for (int e = t; e < LP * g.n4; e += kThreads) {
+    for (int e = t; e < g.nz * LP; e += kThreads) {
       float s = 0.f;
-      for (int gg = 0; gg < g.GW; ++gg) s += ring[(size_t)gg * LP * g.n4 + e];
+      for (int r = 0; r < g.RS; ++r) s += ring[(size_t)r * g.nz * LP + e];
       P[e] = s;
     }
     __syncthreads();
-    for (int e = t; e < g.n4 * LP; e += kThreads) {
+    for (int e = t; e < g.nz * LP; e += kThreads) {
       const int c = e / LP, i = e - c * LP;
       float s = 0.f;
-      for (int j = 0; j <= i && j < l; ++j) s = fmaf(Tinv[j * 32 + i], P[j * g.n4 + c], s);
-      Z[c * LP + i] = s;
+      for (int j = 0; j <= i && j < l; ++j) s = fmaf(Tinv[j * 32 + i], P[c * LP + j], s);
+      Z[e] = c < g.n ? s : 0.f;
     }
     __syncthreads();
   };
 
-  // one CholeskyQR pass on Z (n4 x LP, in shared memory): Z <- Z R^-1, R kept in Rout
+  // one CholeskyQR pass on Z (nz x LP, in shared memory): Z <- Z R^-1, R kept in Rout
   auto z_cholqr = [&](float *Rout) {
     float acc[TN][4];
     zero_acc<TN>(acc);
-    xt_accum<TN>(Z, LP, Z, LP, g.n4, TN, g.GY, acc);
+    xt_accum<TN>(Z, LP, Z, LP, g.nz, TN, g.GY, acc);
     finish_gram(acc, Rout, Ri);
-    rows_times<TN, true>(Z, g.n4, Ri);
+    rows_times<TN, true>(Z, g.nz, Ri);
     __syncthreads();
   };
 
@@ -600,7 +739,7 @@ __device__ void rsvd_problem(const BatchItem &it, float *sm, int *flag, int *sta
     }
   }
   __syncthreads();
-  rows_times<TN, false>(Z, g.n4, M);  // Vb = Q2 M
+  rows_times<TN, false>(Z, g.nz, M);  // Vb = Q2 M
   __syncthreads();
   // signs: the entry of largest magnitude of Vb[:, i] (first on ties) is made positive
   for (int e = t; e < 1024; e += kThreads) Ms[e] = 0.f;
@@ -634,7 +773,8 @@ __device__ void rsvd_problem(const BatchItem &it, float *sm, int *flag, int *sta
   }
   __syncthreads();
   stream_tiles(
-      ring, g.m, g.R2, [&](float *st, int r0) { load_rows(st, LP, Yg, LP, r0, g.R2, g.m, LP, true); },
+      rg, g.m, g.R2, status,
+      [&](float *st, int r0, uint64_t *bar) { issue_spans(bar, span_tile(st, Yg, r0, g.R2, g.m, LP)); },
       [&](float *st, int r0) {
         const int rv = min(g.R2, g.m - r0);
         for (int e = t; e < rv * k; e += kThreads) {
@@ -727,7 +867,7 @@ __device__ void packed_solve(const float *Pk, int n, int nn, const float *rhs, f
   __syncwarp();
 }
 
-__device__ void lsr_problem(const BatchItem &it, float *sm, int *wsum, int *status) {
+__device__ void lsr_problem(const BatchItem &it, float *sm, Ring &rg, int *wsum, int *status) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int m = it.m, n = it.n, s = it.s, n1 = n + 1, n8 = (n1 + 7) & ~7;
   const float *A = it.A, *bv = it.b;
@@ -787,11 +927,11 @@ __device__ void lsr_problem(const BatchItem &it, float *sm, int *wsum, int *stat
     float acc[9];
 #pragma unroll
     for (int u = 0; u < 9; ++u) acc[u] = 0.f;
-    for (int p = p0; p < p1; p += 4) {
-      float va[4][9];
-      float sgn[4];
+    for (int p = p0; p < p1; p += 8) {  // eight rows in flight per warp
+      float va[8][9];
+      float sgn[8];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < 8; ++j) {
         const bool ok = p + j < p1;
         const uint32_t e = ok ? perm[p + j] : 0u;
         const int row = (int)(e & 0x7FFFFFFFu);
@@ -804,7 +944,7 @@ __device__ void lsr_problem(const BatchItem &it, float *sm, int *wsum, int *stat
         }
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < 8; ++j)
 #pragma unroll
         for (int u = 0; u < 9; ++u) acc[u] = fmaf(sgn[j], va[j][u], acc[u]);
     }
@@ -819,7 +959,7 @@ __device__ void lsr_problem(const BatchItem &it, float *sm, int *wsum, int *stat
   // ---- 5. augmented Gram matrix [SA, Sb]^T [SA, Sb] in 8 x 8 blocks (FP32), block partials to ws2
   const int nbk = n8 >> 3, blocks = nbk * (nbk + 1) / 2;
   const int splits = max(1, kThreads / blocks), items = blocks * splits;
-  const int CR = min(s, kStageFloats / n8);
+  const int CR = min((kStageFloats - 16) / n8, (s + 3) & ~3) & ~3;  // rows per staged tile, >= 4
   for (int round = 0; round * kThreads < items; ++round) {
     const int item = round * kThreads + t;
     const bool active = item < items;
@@ -833,7 +973,8 @@ __device__ void lsr_problem(const BatchItem &it, float *sm, int *wsum, int *stat
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
     stream_tiles(
-        sm, s, CR, [&](float *st, int r0) { load_rows(st, n8, SAb, n8, r0, CR, s, n8, true); },
+        rg, s, CR, status,
+        [&](float *st, int r0, uint64_t *bar) { issue_spans(bar, span_tile(st, SAb, r0, CR, s, n8)); },
         [&](float *st, int r0) {
           if (!active) return;
           const int rv = min(CR, s - r0);
@@ -959,6 +1100,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_item, s_flag;
   __shared__ int s_wsum[kWarps];
+  __shared__ __align__(8) uint64_t s_full[kStages];
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kStages; ++st) tc::mbar_init(&s_full[st], 1);
+    tc::fence_barrier_init();
+  }
+  __syncthreads();
+  Ring rg{sm, s_full, 0u};  // the ring's stages start at the front of shared memory, for every problem
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
     __syncthreads();
@@ -967,13 +1115,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (w >= nitems) break;
     const BatchItem it = items[order[w]];
     if (it.kind == RMC_REQ_LSR) {
-      lsr_problem(it, sm, s_wsum, status);
+      lsr_problem(it, sm, rg, s_wsum, status);
     } else {
       const int l = it.k + it.p;
-      if (l <= 8) rsvd_problem<2>(it, sm, &s_flag, status);
-      else if (l <= 16) rsvd_problem<4>(it, sm, &s_flag, status);
-      else if (l <= 24) rsvd_problem<6>(it, sm, &s_flag, status);
-      else rsvd_problem<8>(it, sm, &s_flag, status);
+      if (l <= 8) rsvd_problem<2>(it, sm, rg, &s_flag, status);
+      else if (l <= 16) rsvd_problem<4>(it, sm, rg, &s_flag, status);
+      else if (l <= 24) rsvd_problem<6>(it, sm, rg, &s_flag, status);
+      else rsvd_problem<8>(it, sm, rg, &s_flag, status);
     }
     __syncthreads();
   }

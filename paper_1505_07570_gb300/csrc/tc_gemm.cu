@@ -48,10 +48,11 @@ __device__ __forceinline__ float2 box_muller_fast(uint32_t wa, uint32_t wb) {
   return make_float2(-r * cs, -r * sn);
 }
 
+// Round to TF32 (10-bit mantissa), to nearest with ties away from zero, as cvt.rna.tf32.f32 does, with integer
+// operations on the bit pattern (add half of the dropped range, clear the 13 dropped bits): the conversion
+// instruction runs at a fraction of the integer rate and this kernel converts every draw.  Finite inputs only.
 __device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // Byte offset of (row r, 16-byte chunk q) in a tile with 128-byte rows and 128-byte swizzle.
