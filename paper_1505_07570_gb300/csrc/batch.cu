@@ -99,7 +99,6 @@ __device__ __forceinline__ void st_vec(float *p, const float (&v)[C]) {
   }
 }
 
-__device__ __forceinline__ float f4(const float4 &a, int i) { return i == 0 ? a.x : i == 1 ? a.y : i == 2 ? a.z : a.w; }
 
 // Rows [r0, r0 + R) of a row-major matrix (leading dimension ld) into shared memory with row stride S:
 // columns [0, ncols), zeros in columns [ncols, npad) (npad a multiple of 4) and in rows at or past `rows`.
@@ -368,58 +367,87 @@ __device__ __forceinline__ void gram_reduce64(const float *scr, int LP, int G, i
 // ----------------------------------------------------------------------------- small factorizations
 
 // Upper Cholesky factor of the l x l matrix G64 (ld 32) and its inverse, both FP32 with ld 32 and zeros
-// outside the leading l x l block.  One warp.  FP32 first; if a pivot is not positive the factorization is
-// repeated in FP64 (in place in G64); if that fails too, R is NaN and the problem reports RMC_ENUMERIC.
-__device__ void factor_small(double *G64, int l, float *R, float *Ri, int *status) {
-  const int lane = threadIdx.x & 31;
-  for (int i = 0; i < 32; ++i) R[i * 32 + lane] = (i < l && lane < l && lane >= i) ? (float)G64[i * 32 + lane] : 0.f;
-  __syncwarp();
-  bool ok = true;
+// outside the leading l x l block.  All threads of the CTA: right-looking, each step's trailing update spread
+// over the CTA.  A pivot that is not positive means cond(Y)^2 is beyond FP32: the factorization is repeated on
+// G + sigma I with sigma = 64 l 2^-23 max_i G_ii, just above the Gram matrix's rounding (shifted CholeskyQR:
+// Y R^-1 is then well conditioned though not orthonormal, and every basis the result depends on takes a
+// second, unshifted pass; R = R_b R_a stays exact for B^T = Q2 R).  If that fails too, warp 0 repeats it in
+// FP64 (in place in G64), and then R is NaN and the problem reports RMC_ENUMERIC.  The inverse is formed one
+// column per warp (column j: x = e_j, then x_i /= R_ii and x_c -= R_ci x_i for c < i, from i = j down).
+__device__ bool chol_small_attempt(const double *G64, int l, float shift, float *R, int *flag) {
+  const int t = threadIdx.x;
+  for (int e = t; e < 1024; e += kThreads) {
+    const int i = e >> 5, j = e & 31;
+    R[e] = (i < l && j < l && j >= i) ? (float)G64[i * 32 + j] + (i == j ? shift : 0.f) : 0.f;
+  }
+  if (t == 0) *flag = 0;
+  __syncthreads();
   for (int k = 0; k < l; ++k) {
     const float d = R[k * 32 + k];
-    if (!(d > 0.f) || !(d < INFINITY)) { ok = false; break; }
+    if (!(d > 0.f) || !(d < INFINITY)) {  // every thread sees the same pivot
+      if (t == 0) *flag = 1;
+      break;
+    }
     const float rd = sqrtf(d);
-    const float rkj = (lane > k && lane < l) ? R[k * 32 + lane] / rd : 0.f;
-    __syncwarp();
-    if (lane == k) R[k * 32 + k] = rd;
-    if (lane > k && lane < l) R[k * 32 + lane] = rkj;
-    __syncwarp();
-    if (lane > k && lane < l)
-      for (int i = k + 1; i <= lane; ++i) R[i * 32 + lane] -= R[k * 32 + i] * rkj;
-    __syncwarp();
+    __syncthreads();  // the pivot is read before row k changes
+    if (t >= k && t < l) R[k * 32 + t] = t == k ? rd : R[k * 32 + t] / rd;
+    __syncthreads();
+    for (int e = t; e < 1024; e += kThreads) {
+      const int i = e >> 5, j = e & 31;
+      if (i > k && i <= j && j < l) R[e] = fmaf(-R[k * 32 + i], R[k * 32 + j], R[e]);
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  const bool ok = *flag == 0;
+  __syncthreads();
+  return ok;
+}
+
+__device__ void factor_small(double *G64, int l, float *R, float *Ri, int *flag, int *status) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool ok = chol_small_attempt(G64, l, 0.f, R, flag);  // the same value in every thread
+  if (!ok) {
+    float dmax = 0.f;
+    for (int i = 0; i < l; ++i) dmax = fmaxf(dmax, (float)G64[i * 32 + i]);
+    ok = chol_small_attempt(G64, l, 64.f * (float)l * 1.1920929e-7f * dmax, R, flag);
   }
   if (!ok) {
-    // FP64 retry, in place in G64's upper triangle
-    ok = true;
-    for (int k = 0; k < l; ++k) {
-      const double d = G64[k * 32 + k];
-      if (!(d > 0.0) || !(d < INFINITY)) { ok = false; break; }
-      const double rd = sqrt(d);
-      const double rkj = (lane > k && lane < l) ? G64[k * 32 + lane] / rd : 0.0;
-      __syncwarp();
-      if (lane == k) G64[k * 32 + k] = rd;
-      if (lane > k && lane < l) G64[k * 32 + lane] = rkj;
-      __syncwarp();
-      if (lane > k && lane < l)
-        for (int i = k + 1; i <= lane; ++i) G64[i * 32 + lane] -= G64[k * 32 + i] * rkj;
-      __syncwarp();
+    if (warp == 0) {  // FP64 retry, in place in G64's upper triangle
+      ok = true;
+      for (int k = 0; k < l; ++k) {
+        const double d = G64[k * 32 + k];
+        if (!(d > 0.0) || !(d < INFINITY)) { ok = false; break; }
+        const double rd = sqrt(d);
+        const double rkj = (lane > k && lane < l) ? G64[k * 32 + lane] / rd : 0.0;
+        __syncwarp();
+        if (lane == k) G64[k * 32 + k] = rd;
+        if (lane > k && lane < l) G64[k * 32 + lane] = rkj;
+        __syncwarp();
+        if (lane > k && lane < l)
+          for (int i = k + 1; i <= lane; ++i) G64[i * 32 + lane] -= G64[k * 32 + i] * rkj;
+        __syncwarp();
+      }
+      for (int i = 0; i < 32; ++i)
+        R[i * 32 + lane] = (i < l && lane < l && lane >= i) ? (ok ? (float)G64[i * 32 + lane] : nanf("")) : 0.f;
+      if (!ok && lane == 0) rmc_report(status, RMC_ENUMERIC);
     }
-    for (int i = 0; i < 32; ++i)
-      R[i * 32 + lane] = (i < l && lane < l && lane >= i) ? (ok ? (float)G64[i * 32 + lane] : nanf("")) : 0.f;
-    __syncwarp();
-    if (!ok && lane == 0) rmc_report(status, RMC_ENUMERIC);
+    __syncthreads();
   }
-  // inverse, column `lane`: R x = e_lane by back substitution
-  for (int i = 31; i >= 0; --i) {
-    float v = 0.f;
-    if (lane < l && i <= lane) {
-      float s = (i == lane) ? 1.f : 0.f;
-      for (int c = i + 1; c <= lane; ++c) s -= R[i * 32 + c] * Ri[c * 32 + lane];
-      v = s / R[i * 32 + i];
+  for (int j = warp; j < 32; j += kWarps) {
+    float x = lane == j ? 1.f : 0.f;
+    if (j < l) {
+      for (int i = j; i >= 0; --i) {
+        const float xi = __shfl_sync(0xffffffffu, x, i) / R[i * 32 + i];
+        if (lane == i) x = xi;
+        if (lane < i) x = fmaf(-R[lane * 32 + i], xi, x);
+      }
+    } else {
+      x = 0.f;
     }
-    Ri[i * 32 + lane] = v;
+    Ri[lane * 32 + j] = lane < l ? x : 0.f;
   }
-  __syncwarp();
+  __syncthreads();
 }
 
 // X[r, :] <- X[r, :] M for rows r < rows (LP columns, row stride LP).  M is 32 x 32 (ld 32) with zeros
@@ -562,8 +590,7 @@ __device__ void rsvd_problem(const BatchItem &it, float *sm, Ring &rg, int *flag
     __syncthreads();
     gram_reduce64(ring, LP, g.GY, l, G64);
     __syncthreads();
-    if (warp == 0) factor_small(G64, l, Rout, Riout, status);
-    __syncthreads();
+    factor_small(G64, l, Rout, Riout, flag, status);
   };
 
   // Y = A Z (written to Yg) with the Gram matrix of Y accumulated on the way
@@ -1018,6 +1045,7 @@ __device__ void lsr_problem(const BatchItem &it, float *sm, Ring &rg, int *wsum,
   float *vecs = sm + ((poff(n1, n1) + 63) & ~31);
   float *y = vecs, *xf = vecs + 288, *rres = vecs + 576, *gp = rres + kMaxS;
   double *x64 = reinterpret_cast<double *>(gp + 2 * 288);
+  float *gsum = reinterpret_cast<float *>(x64 + 288);  // up to 64 row groups x 264 columns of SA^T r partials
   bool ok = true;
   float dprev = 0.f;
   for (int kk = 0; kk < n; ++kk) {
@@ -1068,15 +1096,24 @@ __device__ void lsr_problem(const BatchItem &it, float *sm, Ring &rg, int *wsum,
     }
     __syncthreads();
     {
-      const int c = t & 255, h = t >> 8;
-      if (c < n) {
+      // g = SA^T r: thread (column c, row group h) sums rows h, h + H, ... with eight loads in flight
+      const int H = kThreads / n8, c = t % n8, h = t / n8;
+      if (h < H && c < n) {
         float acc = 0.f;
-        for (int i = h; i < s; i += 2) acc = fmaf(SAb[(size_t)i * n8 + c], rres[i], acc);
-        gp[h * 288 + c] = acc;
+#pragma unroll 8
+        for (int i = h; i < s; i += H) acc = fmaf(SAb[(size_t)i * n8 + c], rres[i], acc);
+        gsum[h * 264 + c] = acc;
       }
     }
     __syncthreads();
-    for (int c = t; c < n; c += kThreads) rres[c] = gp[c] + gp[288 + c];  // reuse: SA^T r
+    {
+      const int H = kThreads / n8;
+      for (int c = t; c < n; c += kThreads) {
+        float g = 0.f;
+        for (int h = 0; h < H; ++h) g += gsum[h * 264 + c];
+        rres[c] = g;  // reuse: SA^T r
+      }
+    }
     __syncthreads();
     if (warp == 0) {
       packed_solve<true>(Pk, n, n1, rres, y);

@@ -144,6 +144,18 @@ def test_batch_matches_single_entry_points(R, mixed):
             assert np.linalg.norm(outs[i].cpu().numpy() - xs) <= 1e-4 * np.linalg.norm(xs)
 
 
+def test_batch_square_omega_shifted_cholqr(R):
+    """l = n with a draw of Omega (seed below) that makes A Omega ill conditioned: the FP32 CholeskyQR of the
+    range finder meets a non-positive pivot and the shifted retry keeps the result accurate (no breakdown)."""
+    spec = dict(kind="rsvd", m=893, n=17, k=16, p=1, q=1, seed=20150587454479)
+    A, _ = workloads.batch_problem_numpy(spec)
+    for Ad in (dev(A), dev_strided(A, 3, 1)):
+        r, out = R.rsvd_request(Ad, 16, 1, 1, spec["seed"])
+        R.rmc_batch_run([r])
+        R.rmc_sync()
+        check_rsvd(spec, A, out)
+
+
 def test_batch_workload_sample(R):
     """A 48-problem sample of the batched workload recipe (m up to 8192), every problem against the oracle."""
     specs = workloads.batch_specs(count=48, seed=3, m_range=(512, 8192))
