@@ -805,6 +805,7 @@ __global__ void lsr_resid_kernel(const float *SA, int64_t s, int n, int64_t ld, 
        i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const float *row = SA + i * ld;
     double acc = 0.0;
+#pragma unroll 4
     for (int c = lane; c < n; c += 32) acc = fma((double)row[c], x[c], acc);
 #pragma unroll
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -820,7 +821,8 @@ __global__ void lsr_atr_kernel(const float *SA, int64_t s, int n, int64_t ld, co
   if (c >= n) return;
   const int64_t r0 = blockIdx.y * rows_per, r1 = min(s, r0 + rows_per);
   double acc = 0.0;
-  for (int64_t i = r0; i < r1; ++i) acc = fma((double)SA[i * ld + c], r[i], acc);
+#pragma unroll 8
+  for (int64_t i = r0; i < r1; ++i) acc = fma((double)SA[i * ld + c], r[i], acc);  // eight loads in flight
   part[(int64_t)blockIdx.y * n + c] = acc;
 }
 
@@ -862,6 +864,7 @@ __global__ void __launch_bounds__(1024) lsr_refine_solve_kernel(const float *Rf,
     __syncthreads();
     for (int c = base + bw + t; c < n; c += blockDim.x) {
       float v = ysm[c];
+#pragma unroll 8
       for (int k = 0; k < bw; ++k) v = fmaf(-Rf[(int64_t)(base + k) * n + c], ysm[base + k], v);
       ysm[c] = v;
     }
@@ -888,6 +891,7 @@ __global__ void __launch_bounds__(1024) lsr_refine_solve_kernel(const float *Rf,
     for (int i = t; i < base; i += blockDim.x) {
       float v = ysm[i];
       const float *row = Rf + (int64_t)i * n + base;
+#pragma unroll 8
       for (int k = 0; k < bw; ++k) v = fmaf(-row[k], ysm[base + k], v);
       ysm[i] = v;
     }

@@ -90,7 +90,9 @@ __global__ void __launch_bounds__(kThreads, 1) srht_stage1_kernel(const float *_
                                                                    const int *__restrict__ U_ptr, int64_t umax,
                                                                    int64_t slabs, int64_t N1, float4 *__restrict__ T,
                                                                    bool vec) {
-  extern __shared__ float4 sm[];   // two buffers of kRowsCta float4, swizzled
+  extern __shared__ float4 sm[];   // two buffers of kRowsCta float4, swizzled; sign words; the r2 list
+  uint32_t *sgn = reinterpret_cast<uint32_t *>(sm + 2 * kRowsCta);  // 2 x kRowsCta / 32 sign words
+  uint32_t *r2s = sgn + 2 * (kRowsCta / 32);                          // the needed r2 (U <= kRowsCta entries)
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int64_t nclusters = gridDim.x / csize, cid = blockIdx.x / csize;
@@ -98,11 +100,19 @@ __global__ void __launch_bounds__(kThreads, 1) srht_stage1_kernel(const float *_
   const int64_t N2 = (int64_t)kRowsCta * csize;
   const int t = threadIdx.x;
   const int U = *U_ptr;
+  for (int u = t; u < U; u += kThreads) r2s[u] = r2_list[u];  // no global loads inside the per-item phases
 
-  auto issue = [&](int64_t item, float4 *buf) {
+  auto issue = [&](int64_t item, float4 *buf, uint32_t *sw) {
     const int64_t slab = item % slabs, i1 = item / slabs;
     const int64_t row16 = i1 * N2 + (int64_t)rank * kRowsCta + t * 16;
     const int64_t c0 = slab * 4;
+    if (t < kRowsCta / 32) {  // this tile's sign words, with the tile (rows past m read as +1)
+      const int64_t w = (i1 * N2 + (int64_t)rank * kRowsCta) / 32 + t;
+      const bool in = w * 32 < m;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(sw + t)),
+                   "l"(in ? sign_bits + w : sign_bits), "r"(in ? 4 : 0)
+                   : "memory");
+    }
     if (vec && c0 + 3 < n) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
@@ -118,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 1) srht_stage1_kernel(const float *_
 
   int64_t item = cid;
   int cur = 0;
-  if (item < items) issue(item, sm);
+  if (item < items) issue(item, sm, sgn);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   for (; item < items; item += nclusters, cur ^= 1) {
     float4 *S = sm + cur * kRowsCta;
@@ -126,15 +136,14 @@ __global__ void __launch_bounds__(kThreads, 1) srht_stage1_kernel(const float *_
     __syncthreads();
     // every CTA of the cluster is done reading the other buffer (the previous combine) before it is refilled
     cluster.sync();
-    if (item + nclusters < items) issue(item + nclusters, sm + (cur ^ 1) * kRowsCta);
+    if (item + nclusters < items) issue(item + nclusters, sm + (cur ^ 1) * kRowsCta, sgn + (cur ^ 1) * (kRowsCta / 32));
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 
     const int64_t slab = item % slabs, i1 = item / slabs;
     float4 v[16];
     // phase 1: rows t*16 + j, sign flip, bits 0..3
     {
-      const int64_t row16 = i1 * N2 + (int64_t)rank * kRowsCta + t * 16;
-      const uint32_t gw = row16 < m ? __ldg(sign_bits + row16 / 32) >> (row16 & 31) : 0u;
+      const uint32_t gw = sgn[cur * (kRowsCta / 32) + (t >> 1)] >> ((t & 1) * 16);  // rows t*16 .. t*16 + 15
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         float4 x = S[swz(t * 16 + j)];
@@ -169,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1) srht_stage1_kernel(const float *_
     // combine over the cluster (index bits 12.. of i2) for the needed r2, split across the cluster's CTAs
     float4 *Tout = T + i1 * umax * slabs;
     for (int u = rank + csize * t; u < U; u += csize * kThreads) {
-      const uint32_t r2 = r2_list[u];
+      const uint32_t r2 = r2s[u];
       const int lo = (int)(r2 & (kRowsCta - 1));
       const int hi = (int)(r2 >> 12);
       float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -317,7 +326,7 @@ int rmc_launch_srht(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t 
   const int64_t umax = s < p.N2 ? s : p.N2;
 
   const bool vec = (lda % 4 == 0) && (reinterpret_cast<uintptr_t>(A) % 16 == 0);
-  const size_t smem = 2 * sizeof(float4) * kRowsCta;
+  const size_t smem = 2 * sizeof(float4) * kRowsCta + sizeof(uint32_t) * (2 * (kRowsCta / 32) + (size_t)p.N2);
   RMC_TRY_CUDA(cudaFuncSetAttribute(srht_stage1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(kThreads, 1, 1);
