@@ -711,22 +711,28 @@ __global__ void __launch_bounds__(256) lsr_chol_panel_kernel(float *Rf, int n, i
   }
   if (t == 0) bad = 0;
   __syncthreads();
-  // right-looking over the 32 x 32 block, all threads on each trailing update
-  for (int k = 0; k < b; ++k) {
-    const float d = D[k][k];
-    if (!(d > 0.f) || !(d < INFINITY)) {
-      if (t == 0) bad = 1;
-      break;
+  // right-looking over the 32 x 32 block in one warp's registers: lane j holds column j (col[i] = D[i][j])
+  if (t < 32) {
+    const int lane = t;
+    float col[kPanel];
+#pragma unroll
+    for (int i = 0; i < kPanel; ++i) col[i] = D[i][lane];
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < kPanel; ++k) {
+      const float d = __shfl_sync(0xffffffffu, col[k], k);
+      if (!(d > 0.f) || !(d < INFINITY)) ok = false;  // uniform across the warp
+      const float rd = sqrtf(d), inv = 1.f / rd;
+      col[k] = lane == k ? rd : (lane > k ? col[k] * inv : col[k]);
+#pragma unroll
+      for (int i = k + 1; i < kPanel; ++i) {
+        const float rki = __shfl_sync(0xffffffffu, col[k], i);  // R[k][i]
+        if (lane >= i) col[i] = fmaf(-rki, col[k], col[i]);
+      }
     }
-    const float rd = sqrtf(d);
-    __syncthreads();  // every thread has read the pivot
-    if (t < b) D[k][t] = t == k ? rd : (t > k ? D[k][t] / rd : D[k][t]);
-    __syncthreads();
-    for (int e = t; e < kPanel * kPanel; e += blockDim.x) {
-      const int i = e / kPanel, j = e % kPanel;
-      if (i > k && i <= j && j < b) D[i][j] = fmaf(-D[k][i], D[k][j], D[i][j]);
-    }
-    __syncthreads();
+    if (!ok && lane == 0) bad = 1;
+#pragma unroll
+    for (int i = 0; i < kPanel; ++i) D[i][lane] = col[i];
   }
   __syncthreads();
   if (bad) {
@@ -833,31 +839,39 @@ __global__ void lsr_atr_kernel(const float *SA, int64_t s, int n, int64_t ld, co
 __global__ void __launch_bounds__(1024) lsr_refine_solve_kernel(const float *Rf, int n, const double *part,
                                                                 int chunks, double *xs, bool last, double *xout,
                                                                 int *flags) {
-  extern __shared__ float ysm[];  // n floats
+  // dynamic shared memory: y (n), 1 / R_ii (n), then the 32 x 32 diagonal blocks of R (rows padded to 33)
+  extern __shared__ float ysm[];
   __shared__ float red_dx[32], red_x[32];
-  __shared__ float Dsm[32][33];
   if (flags[0] || flags[2]) return;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nb = (n + 31) / 32;
+  float *rdg = ysm + n;
+  float *Dall = rdg + n;
+  for (int e = t; e < nb * 1024; e += blockDim.x) {  // every diagonal block at once, one load per element
+    const int B = e >> 10, i = (e >> 5) & 31, j = e & 31, base = 32 * B, bw = min(32, n - base);
+    Dall[(B * 32 + i) * 33 + j] =
+        (i < bw && j < bw && i <= j) ? Rf[(int64_t)(base + i) * n + base + j] : (i == j ? 1.f : 0.f);
+  }
   for (int c = t; c < n; c += blockDim.x) {
     double g = 0.0;
     for (int k = 0; k < chunks; ++k) g += part[(int64_t)k * n + c];
     ysm[c] = (float)g;
   }
   __syncthreads();
+  for (int i = t; i < nb * 32; i += blockDim.x) {
+    const float d = Dall[i * 33 + (i & 31)];
+    if (i < n) rdg[i] = 1.f / d;
+  }
+  __syncthreads();
   // forward: R^T y = g
   for (int B = 0; B < nb; ++B) {
     const int base = 32 * B, bw = min(32, n - base);
-    {  // the diagonal block into shared memory (one element per thread), then one warp solves it
-      const int i = t >> 5, j = t & 31;
-      Dsm[i][j] = (i < bw && j < bw && i <= j) ? Rf[(int64_t)(base + i) * n + base + j] : (i == j ? 1.f : 0.f);
-    }
-    __syncthreads();
+    const float *Dsm = Dall + B * 32 * 33;
     if (warp == 0) {
       float v = lane < bw ? ysm[base + lane] : 0.f;
       for (int k = 0; k < bw; ++k) {
-        const float yk = __shfl_sync(0xffffffffu, v, k) / Dsm[k][k];
+        const float yk = __shfl_sync(0xffffffffu, v, k) * rdg[base + k];
         if (lane == k) v = yk;
-        if (lane > k) v = fmaf(-Dsm[k][lane], yk, v);
+        if (lane > k) v = fmaf(-Dsm[k * 33 + lane], yk, v);
       }
       if (lane < bw) ysm[base + lane] = v;
     }
@@ -873,17 +887,13 @@ __global__ void __launch_bounds__(1024) lsr_refine_solve_kernel(const float *Rf,
   // backward: R dx = y
   for (int B = nb - 1; B >= 0; --B) {
     const int base = 32 * B, bw = min(32, n - base);
-    {
-      const int i = t >> 5, j = t & 31;
-      Dsm[i][j] = (i < bw && j < bw && i <= j) ? Rf[(int64_t)(base + i) * n + base + j] : (i == j ? 1.f : 0.f);
-    }
-    __syncthreads();
+    const float *Dsm = Dall + B * 32 * 33;
     if (warp == 0) {
       float v = lane < bw ? ysm[base + lane] : 0.f;
       for (int k = bw - 1; k >= 0; --k) {
-        const float dk = __shfl_sync(0xffffffffu, v, k) / Dsm[k][k];
+        const float dk = __shfl_sync(0xffffffffu, v, k) * rdg[base + k];
         if (lane == k) v = dk;
-        if (lane < k) v = fmaf(-Dsm[lane][k], dk, v);
+        if (lane < k) v = fmaf(-Dsm[lane * 33 + k], dk, v);
       }
       if (lane < bw) ysm[base + lane] = v;
     }
@@ -1247,13 +1257,17 @@ int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n_, i
       }
     }
     RMC_TRY_CUDA(cudaMemsetAsync(b.xs, 0, sizeof(double) * n, st));
+    const size_t refine_smem = sizeof(float) * (2 * (size_t)n + (size_t)((n + 31) / 32) * 32 * 33);
+    if (refine_smem > 48 * 1024)
+      RMC_TRY_CUDA(cudaFuncSetAttribute(lsr_refine_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)refine_smem));
     const int chunks = atr_chunks(s);
     const int64_t rows_per = (s + chunks - 1) / chunks;
     for (int it = 0; it < kRefineSteps; ++it) {
       lsr_resid_kernel<<<rmc_blocks(s * 32, 256, 4096), 256, 0, st>>>(SA, s, n, ldsa, b.xs, b.r, b.flags);
       lsr_atr_kernel<<<dim3((n + 255) / 256, chunks), 256, 0, st>>>(SA, s, n, ldsa, b.r, rows_per, b.part, b.flags);
-      lsr_refine_solve_kernel<<<1, 1024, sizeof(float) * n, st>>>(b.Rf, n, b.part, chunks, b.xs,
-                                                                  it == kRefineSteps - 1, x, b.flags);
+      lsr_refine_solve_kernel<<<1, 1024, refine_smem, st>>>(b.Rf, n, b.part, chunks, b.xs, it == kRefineSteps - 1,
+                                                            x, b.flags);
       rmc_note_launch(3);
     }
   }
