@@ -593,10 +593,45 @@ __device__ void rsvd_problem(const BatchItem &it, float *sm, Ring &rg, int *flag
     factor_small(G64, l, Rout, Riout, flag, status);
   };
 
-  // Y = A Z (written to Yg) with the Gram matrix of Y accumulated on the way
-  auto y_pass = [&](float *Rout, float *Riout) {
+  // W^T = A^T Yg: warp unit (16-column block w_mb of A, k-step group w_rs); w_finish sums the groups in order
+  // and forms Z = (Tinv^T W)^T, dropping the rows c >= n (they hold the dense tile's neighbouring values)
+  const int w_mb = warp % g.MBW, w_rs = warp / g.MBW;
+  const bool w_active = warp < g.MBW * g.RS;
+  auto w_finish = [&](const float (&acc)[TN / 2][4]) {
+    if (w_active) {
+      const int gq = lane >> 2, tq = lane & 3;
+      float *d = ring + (size_t)w_rs * g.nz * LP + (w_mb * 16 + gq) * LP + 2 * tq;
+#pragma unroll
+      for (int nb = 0; nb < TN / 2; ++nb) {
+        *reinterpret_cast<float2 *>(d + nb * 8) = make_float2(acc[nb][0], acc[nb][1]);
+        *reinterpret_cast<float2 *>(d + 8 * LP + nb * 8) = make_float2(acc[nb][2], acc[nb][3]);
+      }
+    }
+    __syncthreads();
+    for (int e = t; e < g.nz * LP; e += kThreads) {
+      float s = 0.f;
+      for (int r = 0; r < g.RS; ++r) s += ring[(size_t)r * g.nz * LP + e];
+      P[e] = s;
+    }
+    __syncthreads();
+    for (int e = t; e < g.nz * LP; e += kThreads) {
+      const int c = e / LP, i = e - c * LP;
+      float s = 0.f;
+      for (int j = 0; j <= i && j < l; ++j) s = fmaf(Tinv[j * 32 + i], P[c * LP + j], s);
+      Z[e] = c < g.n ? s : 0.f;
+    }
+    __syncthreads();
+  };
+
+  // Y = A Z (written to Yg) with the Gram matrix of Y accumulated on the way.  With fuse_w (the intermediate
+  // bases of the power iteration, where Q = Y R^-1 stays implicit anyway), W^T = A^T Y is accumulated from the
+  // same A tiles and Z = (R^-T W)^T formed at the end, which saves the separate pass over A; Tinv = R^-1.
+  auto y_pass = [&](float *Rout, float *Riout, bool fuse_w) {
     float gtot[TN][4];
     zero_acc<TN>(gtot);
+    float wacc[TN / 2][4];
+#pragma unroll
+    for (int nb = 0; nb < TN / 2; ++nb) wacc[nb][0] = wacc[nb][1] = wacc[nb][2] = wacc[nb][3] = 0.f;
     stream_tiles(
         rg, g.m, g.R, status,
         [&](float *st, int r0, uint64_t *bar) {
@@ -620,8 +655,14 @@ __device__ void rsvd_problem(const BatchItem &it, float *sm, Ring &rg, int *flag
           zero_acc<TN>(gt);
           xt_accum<TN>(P, LP, P, LP, g.R, TN, g.GY, gt);
           add_acc<TN>(gtot, gt);
+          if (fuse_w && w_active) at_times_y<TN>(st, g.S, P, g.R, w_mb, w_rs, g.RS, wacc);
         });
     finish_gram(gtot, Rout, Riout);
+    if (fuse_w) {
+      for (int e = t; e < 1024; e += kThreads) Tinv[e] = Riout[e];
+      __syncthreads();
+      w_finish(wacc);
+    }
   };
 
   // Second CholeskyQR pass over Yg: Q1 = Y R1^-1 written back in place, Gram matrix of Q1 accumulated
@@ -651,8 +692,6 @@ __device__ void rsvd_problem(const BatchItem &it, float *sm, Ring &rg, int *flag
     float acc[TN / 2][4];
 #pragma unroll
     for (int nb = 0; nb < TN / 2; ++nb) acc[nb][0] = acc[nb][1] = acc[nb][2] = acc[nb][3] = 0.f;
-    const int mb = warp % g.MBW, rs = warp / g.MBW;
-    const bool active = warp < g.MBW * g.RS;
     stream_tiles(
         rg, g.m, g.R, status,
         [&](float *st, int r0, uint64_t *bar) {
@@ -665,32 +704,9 @@ __device__ void rsvd_problem(const BatchItem &it, float *sm, Ring &rg, int *flag
           }
         },
         [&](float *st, int r0) {
-          if (active) at_times_y<TN>(st, g.S, st + g.yoff, g.R, mb, rs, g.RS, acc);
+          if (w_active) at_times_y<TN>(st, g.S, st + g.yoff, g.R, w_mb, w_rs, g.RS, acc);
         });
-    // W^T partials of each k-step group: scr[rs][c][j] (nz x LP), then summed in group order into P
-    if (active) {
-      const int gq = lane >> 2, tq = lane & 3;
-      float *d = ring + (size_t)rs * g.nz * LP + (mb * 16 + gq) * LP + 2 * tq;
-#pragma unroll
-      for (int nb = 0; nb < TN / 2; ++nb) {
-        *reinterpret_cast<float2 *>(d + nb * 8) = make_float2(acc[nb][0], acc[nb][1]);
-        *reinterpret_cast<float2 *>(d + 8 * LP + nb * 8) = make_float2(acc[nb][2], acc[nb][3]);
-      }
-    }
-    __syncthreads();
-    for (int e = t; e < g.nz * LP; e += kThreads) {
-      float s = 0.f;
-      for (int r = 0; r < g.RS; ++r) s += ring[(size_t)r * g.nz * LP + e];
-      P[e] = s;
-    }
-    __syncthreads();
-    for (int e = t; e < g.nz * LP; e += kThreads) {
-      const int c = e / LP, i = e - c * LP;
-      float s = 0.f;
-      for (int j = 0; j <= i && j < l; ++j) s = fmaf(Tinv[j * 32 + i], P[c * LP + j], s);
-      Z[e] = c < g.n ? s : 0.f;
-    }
-    __syncthreads();
+    w_finish(acc);
   };
 
   // one CholeskyQR pass on Z (nz x LP, in shared memory): Z <- Z R^-1, R kept in Rout
@@ -704,28 +720,27 @@ __device__ void rsvd_problem(const BatchItem &it, float *sm, Ring &rg, int *flag
   };
 
   float *Rscr = P;  // R factors of the CholeskyQR passes that are not kept
-  // ---- range finder
-  y_pass(Rscr, Ri);  // Y = A Omega; R1^-1 in Ri
+  // ---- range finder and power iteration
   if (it.q == 0) {
+    y_pass(Rscr, Ri, false);  // Y = A Omega; R1^-1 in Ri
     for (int e = t; e < 1024; e += kThreads) Tinv[e] = Ri[e];
     __syncthreads();
     q_pass(Tinv, Rscr, Ri);  // Q1 = Y R1^-1; R2^-1 in Ri
     for (int e = t; e < 1024; e += kThreads) Tinv[e] = Ri[e];
     __syncthreads();
   } else {
-    for (int e = t; e < 1024; e += kThreads) Tinv[e] = Ri[e];
-    __syncthreads();
-  }
-  for (int itn = 0; itn < it.q; ++itn) {
-    w_pass();          // Z = (Q^T A)^T
-    z_cholqr(Rscr);    // Z = orth(A^T Q)
-    y_pass(Rscr, Ri);  // Y = A Z
-    for (int e = t; e < 1024; e += kThreads) Tinv[e] = Ri[e];
-    __syncthreads();
-    if (itn == it.q - 1) {
-      q_pass(Tinv, Rscr, Ri);
-      for (int e = t; e < 1024; e += kThreads) Tinv[e] = Ri[e];
-      __syncthreads();
+    y_pass(Rscr, Ri, true);  // Y = A Omega and Z = (Q^T A)^T in one pass
+    for (int itn = 0; itn < it.q; ++itn) {
+      const bool last = itn == it.q - 1;
+      z_cholqr(Rscr);           // Z = orth(A^T Q)
+      y_pass(Rscr, Ri, !last);  // Y = A Z (and the next Z, except for the last basis)
+      if (last) {
+        for (int e = t; e < 1024; e += kThreads) Tinv[e] = Ri[e];
+        __syncthreads();
+        q_pass(Tinv, Rscr, Ri);
+        for (int e = t; e < 1024; e += kThreads) Tinv[e] = Ri[e];
+        __syncthreads();
+      }
     }
   }
   w_pass();  // Z = B^T = (Q^T A)^T, n x l
