@@ -679,17 +679,39 @@ __global__ void copy_column_kernel(const float *v, int64_t s, float *W, int64_t 
 
 // ------------------------------------------------------------- least-squares solve: FP32 factor, refinement
 // The normal-equation matrix SA^T SA is factored in FP32 (Gram with FP32 products summed in FP64 across
-// 32-row slices; blocked right-looking Cholesky over 32-wide panels, many CTAs per step), and x is then refined
-// against SA itself: r = Sb - SA x and g = SA^T r in FP64 (FP32 x FP32 products are exact in FP64), dx from
-// R^T R dx = g.  The fixed point is the least-squares solution of the FP32 [SA, Sb] whatever the rounding of
-// the factor; each step shrinks the error by about cond(SA)^2 x 2^-24.  A pivot that is not positive, or a last
-// step that has not converged, hands the problem to the FP64 path.
+// 32-row slices; blocked right-looking Cholesky over 32-wide panels, many CTAs per step), its inverse is formed
+// as M = R^-1 R^-T (R^-1 by block back substitution, one CTA per 32-column block), and x is then refined
+// against SA itself: r = Sb - SA x and g = SA^T r in FP64 (FP32 x FP32 products are exact in FP64), dx = M g.
+// The fixed point is the least-squares solution of the FP32 [SA, Sb] whatever the rounding of the factor and
+// of M; each step shrinks the error by about cond(SA)^2 x 2^-24.  A pivot that is not positive, or a last step
+// that has not converged, hands the problem to the FP64 path.
+//
+// flags: [0] FP32 path failed (FP64 takes over), [1] FP64 path failed, [2] refinement converged, [4 + 2 it] and
+// [5 + 2 it]: bit patterns of max |dx| and max |x| after refinement step it (non-negative floats order like
+// their bit patterns, so atomicMax on the words takes the maximum).
+constexpr int kLsrFlagWords = 16;
+
+// Step `it` ended the iteration: its correction is below tol ||x|| (and x is finite).
+__device__ __forceinline__ bool lsr_converged(const int *flags, int it, float tol) {
+  const float a = __uint_as_float((unsigned)flags[4 + 2 * it]), b = __uint_as_float((unsigned)flags[5 + 2 * it]);
+  return b < INFINITY && a <= tol * b;
+}
+
+// Common early exit of the refinement kernels of step `it`: failed, or an earlier step converged.
+__device__ __forceinline__ bool lsr_skip(int *flags, int it) {
+  if (flags[0] || flags[2]) return true;
+  if (it > 0 && lsr_converged(flags, it - 1, 1e-9f)) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) flags[2] = 1;
+    return true;
+  }
+  return false;
+}
 
 constexpr int kPanel = 32;
 
 // Rf (n x n, row-major, upper triangle used) = the leading n x n block of G (FP64, ld = ldg).
 __global__ void lsr_rf_init_kernel(const double *G, int ldg, int n, float *Rf, int *flags) {
-  if (blockIdx.x == 0 && threadIdx.x < 4) flags[threadIdx.x] = 0;
+  if (blockIdx.x == 0 && threadIdx.x < kLsrFlagWords) flags[threadIdx.x] = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / n), j = (int)(e - (int64_t)i * n);
@@ -697,9 +719,10 @@ __global__ void lsr_rf_init_kernel(const double *G, int ldg, int n, float *Rf, i
   }
 }
 
-// Panel j0: every CTA factors the 32 x 32 diagonal block (FP32, in shared memory), CTA 0 stores it, and each
-// CTA forms its 256 columns of the panel rows R[j0 : j0+32, c] = R_jj^-T Rf[j0 : j0+32, c] (thread per column).
-__global__ void __launch_bounds__(256) lsr_chol_panel_kernel(float *Rf, int n, int j0, int *fail) {
+// Panel j0: every CTA factors the 32 x 32 diagonal block (FP32, in shared memory), CTA 0 stores it and its
+// inverse (Dinv, 32 x 32 row-major, identity in the padding of a ragged block), and each CTA forms its 256
+// columns of the panel rows R[j0 : j0+32, c] = R_jj^-T Rf[j0 : j0+32, c] (thread per column).
+__global__ void __launch_bounds__(256) lsr_chol_panel_kernel(float *Rf, int n, int j0, float *Dinv, int *fail) {
   __shared__ float D[kPanel][kPanel + 1];
   __shared__ int bad;
   if (*fail) return;
@@ -739,11 +762,26 @@ __global__ void __launch_bounds__(256) lsr_chol_panel_kernel(float *Rf, int n, i
     if (t == 0 && blockIdx.x == 0) *fail = 1;
     return;
   }
-  if (blockIdx.x == 0)
+  if (blockIdx.x == 0) {
     for (int e = t; e < b * b; e += blockDim.x) {
       const int i = e / b, j = e % b;
       if (i <= j) Rf[(int64_t)(j0 + i) * n + j0 + j] = D[i][j];
     }
+    if (t >= 32 && t < 64) {  // column j of D^-1 by back substitution (lane j)
+      const int j = t - 32;
+      float xv[kPanel];
+#pragma unroll
+      for (int i = kPanel - 1; i >= 0; --i) {
+        float v = i == j ? 1.f : 0.f;
+#pragma unroll
+        for (int k = i + 1; k < kPanel; ++k) v = fmaf(-D[i][k], xv[k], v);
+        xv[i] = v / D[i][i];
+      }
+      float *dst = Dinv + (int64_t)(j0 / kPanel) * kPanel * kPanel;
+#pragma unroll
+      for (int i = 0; i < kPanel; ++i) dst[i * kPanel + j] = xv[i];
+    }
+  }
   const int c = j0 + b + blockIdx.x * blockDim.x + t;
   if (c >= n) return;
   float x[kPanel];
@@ -802,10 +840,87 @@ __global__ void __launch_bounds__(256) lsr_chol_update_kernel(float *Rf, int n, 
     }
 }
 
+// Column block J = blockIdx.x of R^-1 (rows 0 .. 32 J + 31) by block back substitution over the 32 x 32 blocks:
+// X_JJ = D_J^-1 and X_IJ = -D_I^-1 sum_{K=I+1..J} R_IK X_KJ for I = J-1 .. 0 (thread (i, j) of the block).
+__global__ void __launch_bounds__(1024) lsr_tri_inv_kernel(const float *Rf, const float *Dinv, int n, float *Ri,
+                                                           const int *fail) {
+  extern __shared__ float X[];  // rows 0 .. 32 (J + 1) - 1 of the column block, then T (32 x 32)
+  if (*fail) return;
+  const int J = blockIdx.x, t = threadIdx.x, i = t >> 5, j = t & 31;
+  const int rows = kPanel * (J + 1), k1 = min(rows, n);
+  float *Tm = X + (size_t)rows * kPanel;
+  X[(kPanel * J + i) * kPanel + j] = Dinv[(int64_t)J * kPanel * kPanel + i * kPanel + j];
+  __syncthreads();
+  for (int I = J - 1; I >= 0; --I) {
+    const float *rrow = Rf + (int64_t)(kPanel * I + i) * n;  // one row per warp: a broadcast load per k
+    float acc = 0.f;
+#pragma unroll 8
+    for (int k = kPanel * (I + 1); k < k1; ++k) acc = fmaf(rrow[k], X[k * kPanel + j], acc);
+    Tm[i * kPanel + j] = acc;
+    __syncthreads();
+    const float *drow = Dinv + (int64_t)I * kPanel * kPanel + i * kPanel;
+    float v = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < kPanel; ++k) v = fmaf(drow[k], Tm[k * kPanel + j], v);
+    X[(kPanel * I + i) * kPanel + j] = -v;
+    __syncthreads();
+  }
+  const int c = kPanel * J + j;
+  if (c < n)
+    for (int r = i; r < k1; r += kPanel) Ri[(int64_t)r * n + c] = X[r * kPanel + j];
+}
+
+// M = R^-1 R^-T (n x n, symmetric): M[a][c] = sum_{k >= max(a, c)} Ri[a][k] Ri[c][k], 64 x 64 tiles of the upper
+// triangle (thread: 4 x 4 outputs), each written to both halves.  Ri is read only on and above its diagonal.
+__global__ void __launch_bounds__(256) lsr_inv_gram_kernel(const float *Ri, int n, float *M, const int *fail) {
+  __shared__ float Pa[kPanel][65], Pc[kPanel][65];
+  if (*fail) return;
+  int p = blockIdx.x, ta = 0;
+  const int T = (n + 63) / 64;
+  while (p >= T - ta) { p -= T - ta; ++ta; }
+  const int tc = ta + p;
+  const int a0 = 64 * ta, c0 = 64 * tc;
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  float acc[4][4] = {};
+  for (int k0 = c0; k0 < n; k0 += kPanel) {
+    __syncthreads();
+    for (int e = t; e < kPanel * 64; e += blockDim.x) {
+      const int q = e >> 5, kk = e & 31, k = k0 + kk;
+      const int ra = a0 + q, rc = c0 + q;
+      Pa[kk][q] = (ra < n && k < n && k >= ra) ? Ri[(int64_t)ra * n + k] : 0.f;
+      Pc[kk][q] = (rc < n && k < n && k >= rc) ? Ri[(int64_t)rc * n + k] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < kPanel; ++k) {
+      float av[4], cv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        av[u] = Pa[k][ty + 16 * u];
+        cv[u] = Pc[k][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], cv[v], acc[u][v]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int ia = a0 + ty + 16 * u, ic = c0 + tx + 16 * v;
+      if (ia < n && ic < n && ia <= ic) {
+        M[(int64_t)ia * n + ic] = acc[u][v];
+        M[(int64_t)ic * n + ia] = acc[u][v];
+      }
+    }
+}
+
 // r = Sb - SA x (FP64), one warp per row of [SA, Sb] (s x (n+1), Sb in column n).
 __global__ void lsr_resid_kernel(const float *SA, int64_t s, int n, int64_t ld, const double *x, double *r,
-                                 const int *flags) {
-  if (flags[0] || flags[2]) return;  // failed, or already converged
+                                 int it, int *flags) {
+  if (lsr_skip(flags, it)) return;
   const int lane = threadIdx.x & 31;
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < s;
        i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -821,8 +936,8 @@ __global__ void lsr_resid_kernel(const float *SA, int64_t s, int n, int64_t ld, 
 
 // part[chunk][c] = sum over the chunk's rows of SA[i, c] r_i (FP64), thread per column.
 __global__ void lsr_atr_kernel(const float *SA, int64_t s, int n, int64_t ld, const double *r, int64_t rows_per,
-                               double *part, const int *flags) {
-  if (flags[0] || flags[2]) return;
+                               double *part, int it, int *flags) {
+  if (lsr_skip(flags, it)) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   const int64_t r0 = blockIdx.y * rows_per, r1 = min(s, r0 + rows_per);
@@ -832,112 +947,54 @@ __global__ void lsr_atr_kernel(const float *SA, int64_t s, int n, int64_t ld, co
   part[(int64_t)blockIdx.y * n + c] = acc;
 }
 
-// One CTA: g = sum of the chunk partials; R^T y = g and R dx = y in 32-row blocks (one warp solves a diagonal
-// block, all threads update the rest); x += dx.  A correction below 1e-9 ||x|| ends the iteration early
-// (flags[2]); on the last step a correction larger than 1e-5 ||x|| (or not finite) sets flags[0] so that the
-// FP64 path takes over.  x is written out when the iteration ends.
-__global__ void __launch_bounds__(1024) lsr_refine_solve_kernel(const float *Rf, int n, const double *part,
-                                                                int chunks, double *xs, bool last, double *xout,
-                                                                int *flags) {
-  // dynamic shared memory: y (n), 1 / R_ii (n), then the 32 x 32 diagonal blocks of R (rows padded to 33)
-  extern __shared__ float ysm[];
-  __shared__ float red_dx[32], red_x[32];
-  if (flags[0] || flags[2]) return;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nb = (n + 31) / 32;
-  float *rdg = ysm + n;
-  float *Dall = rdg + n;
-  for (int e = t; e < nb * 1024; e += blockDim.x) {  // every diagonal block at once, one load per element
-    const int B = e >> 10, i = (e >> 5) & 31, j = e & 31, base = 32 * B, bw = min(32, n - base);
-    Dall[(B * 32 + i) * 33 + j] =
-        (i < bw && j < bw && i <= j) ? Rf[(int64_t)(base + i) * n + base + j] : (i == j ? 1.f : 0.f);
-  }
+// dx = M g for the 32 rows of this CTA (g = sum of the chunk partials, one warp per row), x += dx, and the
+// maxima of |dx| and |x| of step `it` into the flag words.
+__global__ void __launch_bounds__(256) lsr_apply_kernel(const float *M, int n, const double *part, int chunks,
+                                                        double *xs, int it, int *flags) {
+  extern __shared__ float gsm[];  // g (n)
+  if (lsr_skip(flags, it)) return;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int c = t; c < n; c += blockDim.x) {
     double g = 0.0;
     for (int k = 0; k < chunks; ++k) g += part[(int64_t)k * n + c];
-    ysm[c] = (float)g;
+    gsm[c] = (float)g;
   }
   __syncthreads();
-  for (int i = t; i < nb * 32; i += blockDim.x) {
-    const float d = Dall[i * 33 + (i & 31)];
-    if (i < n) rdg[i] = 1.f / d;
-  }
-  __syncthreads();
-  // forward: R^T y = g
-  for (int B = 0; B < nb; ++B) {
-    const int base = 32 * B, bw = min(32, n - base);
-    const float *Dsm = Dall + B * 32 * 33;
-    if (warp == 0) {
-      float v = lane < bw ? ysm[base + lane] : 0.f;
-      for (int k = 0; k < bw; ++k) {
-        const float yk = __shfl_sync(0xffffffffu, v, k) * rdg[base + k];
-        if (lane == k) v = yk;
-        if (lane > k) v = fmaf(-Dsm[k * 33 + lane], yk, v);
-      }
-      if (lane < bw) ysm[base + lane] = v;
-    }
-    __syncthreads();
-    for (int c = base + bw + t; c < n; c += blockDim.x) {
-      float v = ysm[c];
-#pragma unroll 8
-      for (int k = 0; k < bw; ++k) v = fmaf(-Rf[(int64_t)(base + k) * n + c], ysm[base + k], v);
-      ysm[c] = v;
-    }
-    __syncthreads();
-  }
-  // backward: R dx = y
-  for (int B = nb - 1; B >= 0; --B) {
-    const int base = 32 * B, bw = min(32, n - base);
-    const float *Dsm = Dall + B * 32 * 33;
-    if (warp == 0) {
-      float v = lane < bw ? ysm[base + lane] : 0.f;
-      for (int k = bw - 1; k >= 0; --k) {
-        const float dk = __shfl_sync(0xffffffffu, v, k) * rdg[base + k];
-        if (lane == k) v = dk;
-        if (lane < k) v = fmaf(-Dsm[lane * 33 + k], dk, v);
-      }
-      if (lane < bw) ysm[base + lane] = v;
-    }
-    __syncthreads();
-    for (int i = t; i < base; i += blockDim.x) {
-      float v = ysm[i];
-      const float *row = Rf + (int64_t)i * n + base;
-#pragma unroll 8
-      for (int k = 0; k < bw; ++k) v = fmaf(-row[k], ysm[base + k], v);
-      ysm[i] = v;
-    }
-    __syncthreads();
-  }
-  float mdx = 0.f, mx = 0.f;
-  for (int c = t; c < n; c += blockDim.x) {
-    const double nx = xs[c] + (double)ysm[c];
-    xs[c] = nx;
-    mdx = fmaxf(mdx, isfinite(ysm[c]) ? fabsf(ysm[c]) : INFINITY);
-    mx = fmaxf(mx, fabsf((float)nx));
-  }
+  unsigned mdx = 0u, mx = 0u;
+  for (int rr = warp; rr < kPanel; rr += blockDim.x >> 5) {
+    const int r = blockIdx.x * kPanel + rr;
+    if (r >= n) break;
+    const float *mrow = M + (int64_t)r * n;
+    float acc = 0.f;
+#pragma unroll 4
+    for (int c = lane; c < n; c += 32) acc = fmaf(mrow[c], gsm[c], acc);
 #pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    mdx = fmaxf(mdx, __shfl_xor_sync(0xffffffffu, mdx, o));
-    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const double nx = xs[r] + (double)acc;
+      xs[r] = nx;
+      const float adx = isfinite(acc) ? fabsf(acc) : INFINITY;
+      const float ax = isfinite(nx) ? fabsf((float)nx) : INFINITY;
+      mdx = max(mdx, __float_as_uint(adx));
+      mx = max(mx, __float_as_uint(ax));
+    }
   }
   if (lane == 0) {
-    red_dx[warp] = mdx;
-    red_x[warp] = mx;
+    atomicMax(reinterpret_cast<unsigned *>(&flags[4 + 2 * it]), mdx);
+    atomicMax(reinterpret_cast<unsigned *>(&flags[5 + 2 * it]), mx);
   }
-  __syncthreads();
-  __shared__ int verdict;  // 0: continue, 1: converged, 2: failed
-  if (t == 0) {
-    float a = 0.f, b = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      a = fmaxf(a, red_dx[w]);
-      b = fmaxf(b, red_x[w]);
-    }
-    verdict = (a <= 1e-9f * b) ? 1 : !last ? 0 : (a <= 1e-5f * b) ? 1 : 2;
-    if (verdict == 1) flags[2] = 1;
-    if (verdict == 2) flags[0] = 1;
+}
+
+// End of the refinement: x is written out if a step converged (correction below 1e-9 ||x||) or the last one is
+// below 1e-5 ||x||; otherwise flags[0] hands the problem to the FP64 path.
+__global__ void lsr_refine_finish_kernel(const double *xs, int n, int last, double *xout, int *flags) {
+  if (flags[0]) return;
+  const bool ok = flags[2] || lsr_converged(flags, last, 1e-5f);
+  if (!ok) {
+    if (threadIdx.x == 0) flags[0] = 1;
+    return;
   }
-  __syncthreads();
-  if (verdict != 1) return;
-  for (int c = t; c < n; c += blockDim.x) xout[c] = xs[c];
+  for (int c = threadIdx.x; c < n; c += blockDim.x) xout[c] = xs[c];
 }
 
 // ----------------------------------------------------------------------------------------- host helpers
@@ -1203,23 +1260,27 @@ int rmc_launch_rsvd_finish(rmc_ctx *ctx, const float *Q, int64_t m, int64_t l, c
 
 constexpr int kRefineSteps = 4;
 
-static int atr_chunks(int64_t s) { return (int)std::min<int64_t>(64, std::max<int64_t>(1, s / 64)); }
+static int atr_chunks(int64_t s) { return (int)std::min<int64_t>(64, std::max<int64_t>(1, s / 32)); }
 
 struct LsrBufs {
   double *G, *xs, *r, *part, *gpart;
-  float *Rf;
-  int *flags;  // [0] FP32 path failed (FP64 takes over), [1] FP64 path failed, [2] refinement converged
+  float *Rf, *Dinv, *Ri, *M;
+  int *flags;  // kLsrFlagWords words, see the refinement kernels
 };
 
 static LsrBufs lsr_carve(WsCarve &w, int64_t s, int64_t n, int num_sms) {
   LsrBufs b;
   const int l = (int)n + 1;
+  const int64_t nb = (n + kPanel - 1) / kPanel;
   b.G = w.take<double>((size_t)l * l);
-  b.flags = w.take<int>(4);
+  b.flags = w.take<int>(kLsrFlagWords);
   b.xs = w.take<double>(n);
   b.r = w.take<double>(s);
   b.part = w.take<double>((size_t)atr_chunks(s) * n);
   b.Rf = w.take<float>((size_t)n * n);
+  b.Dinv = w.take<float>((size_t)nb * kPanel * kPanel);
+  b.Ri = w.take<float>((size_t)n * n);
+  b.M = w.take<float>((size_t)n * n);
   b.gpart = reinterpret_cast<double *>(w.take<char>(gram_ws(s, l, num_sms)));
   return b;
 }
@@ -1248,7 +1309,7 @@ int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n_, i
     rmc_note_launch();
     for (int j0 = 0; j0 < n; j0 += kPanel) {
       const int bw = std::min(kPanel, n - j0), rest = n - j0 - bw;
-      lsr_chol_panel_kernel<<<std::max(1, (rest + 255) / 256), 256, 0, st>>>(b.Rf, n, j0, &b.flags[0]);
+      lsr_chol_panel_kernel<<<std::max(1, (rest + 255) / 256), 256, 0, st>>>(b.Rf, n, j0, b.Dinv, &b.flags[0]);
       rmc_note_launch();
       if (rest > 0) {
         const int T = (rest + 63) / 64;
@@ -1256,20 +1317,28 @@ int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n_, i
         rmc_note_launch();
       }
     }
+    // M = R^-1 R^-T
+    const int nb = (n + kPanel - 1) / kPanel;
+    const size_t tri_smem = sizeof(float) * ((size_t)nb * kPanel * kPanel + kPanel * kPanel);
+    if (tri_smem > 48 * 1024)
+      RMC_TRY_CUDA(cudaFuncSetAttribute(lsr_tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)tri_smem));
+    lsr_tri_inv_kernel<<<nb, 1024, tri_smem, st>>>(b.Rf, b.Dinv, n, b.Ri, &b.flags[0]);
+    const int T64 = (n + 63) / 64;
+    lsr_inv_gram_kernel<<<T64 * (T64 + 1) / 2, 256, 0, st>>>(b.Ri, n, b.M, &b.flags[0]);
+    rmc_note_launch(2);
     RMC_TRY_CUDA(cudaMemsetAsync(b.xs, 0, sizeof(double) * n, st));
-    const size_t refine_smem = sizeof(float) * (2 * (size_t)n + (size_t)((n + 31) / 32) * 32 * 33);
-    if (refine_smem > 48 * 1024)
-      RMC_TRY_CUDA(cudaFuncSetAttribute(lsr_refine_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)refine_smem));
     const int chunks = atr_chunks(s);
     const int64_t rows_per = (s + chunks - 1) / chunks;
     for (int it = 0; it < kRefineSteps; ++it) {
-      lsr_resid_kernel<<<rmc_blocks(s * 32, 256, 4096), 256, 0, st>>>(SA, s, n, ldsa, b.xs, b.r, b.flags);
-      lsr_atr_kernel<<<dim3((n + 255) / 256, chunks), 256, 0, st>>>(SA, s, n, ldsa, b.r, rows_per, b.part, b.flags);
-      lsr_refine_solve_kernel<<<1, 1024, refine_smem, st>>>(b.Rf, n, b.part, chunks, b.xs, it == kRefineSteps - 1,
-                                                            x, b.flags);
+      lsr_resid_kernel<<<rmc_blocks(s * 32, 256, 4096), 256, 0, st>>>(SA, s, n, ldsa, b.xs, b.r, it, b.flags);
+      lsr_atr_kernel<<<dim3((n + 255) / 256, chunks), 256, 0, st>>>(SA, s, n, ldsa, b.r, rows_per, b.part, it,
+                                                                    b.flags);
+      lsr_apply_kernel<<<nb, 256, sizeof(float) * n, st>>>(b.M, n, b.part, chunks, b.xs, it, b.flags);
       rmc_note_launch(3);
     }
+    lsr_refine_finish_kernel<<<1, 256, 0, st>>>(b.xs, n, kRefineSteps - 1, x, b.flags);
+    rmc_note_launch();
   }
   // FP64 path (every kernel returns at once unless flags[0] is set): FP64 Gram, FP64 Cholesky of the augmented
   // matrix, back substitution

@@ -5,40 +5,36 @@
 //     C[r] = (1/sqrt(s)) sum_{i1} (H_N1)[r1, i1] T[i1, r2],   T[i1, r2] = sum_{i2} (H_N2)[r2, i2] g_i A[i],
 // and only the r2 that occur among the s sampled rows are needed.
 //
-// Stage 1 (persistent CTAs, in clusters of C CTAs per block of N2 = 4096 C rows; C = 1 is used): each CTA takes
-//   (4-column slab, block) items in turn, streams the next item's 4096 x 4 tile into shared memory with cp.async
-//   while it transforms the current one (sign flip, then its 12 index bits in three register phases of four
-//   bits separated by shared-memory transposes), and writes the transformed rows whose index r2 occurs in the
-//   sample to T[i1, slot(r2), slab].  (With C > 1 the cluster would first combine its CTAs over DSMEM.)
+// Stage 1 (persistent CTAs, one 4096-row block of one 4-column slab per item, N2 = 4096): each CTA takes items in
+//   turn, streams the next item's 4096 x 4 tile into shared memory with cp.async while it transforms the current
+//   one (sign flip, then its 12 index bits in three register phases of four bits separated by shared-memory
+//   transposes), and writes the transformed rows whose index r2 occurs in the sample to T[i1, slot(r2), slab].
 // Stage 2: C[r] = (1/sqrt(s)) sum over the N1 = N / N2 blocks of +-T[i1, slot(r2)], one thread per (row,
 //   4 columns), eight loads in flight.
 // A is read once; T holds N1 * |R2| rows (|R2| <= min(s, N2)), written once and read about s / |R2| times.
 #include <algorithm>
 
-#include <cooperative_groups.h>
-
 #include "rmc_internal.cuh"
 #include "philox.cuh"
 
-namespace cg = cooperative_groups;
 using namespace rmc;
 
 namespace {
 
 constexpr int kRowsCta = 4096;   // rows transformed by one CTA (12 index bits)
-constexpr int kThreads = 256;    // 16 rows x 4 columns per thread
+constexpr int kThreads = 512;    // per phase: 16 rows x 2 columns per thread
 
 // shared-memory slot of local row r: XOR the low 3 bits with bits 4..6 (conflict-free float4 phases)
 __device__ __forceinline__ int swz(int r) { return r ^ ((r >> 4) & 7); }
 
-__device__ __forceinline__ void bfly(float4 &a, float4 &b) {
-  const float4 x = a, y = b;
-  a = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
-  b = make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
+__device__ __forceinline__ void bfly(float2 &a, float2 &b) {
+  const float2 x = a, y = b;
+  a = make_float2(x.x + y.x, x.y + y.y);
+  b = make_float2(x.x - y.x, x.y - y.y);
 }
 
 // 16-point transform over the register index (4 bits).
-__device__ __forceinline__ void fwht16(float4 (&v)[16]) {
+__device__ __forceinline__ void fwht16(float2 (&v)[16]) {
 #pragma unroll
   for (int h = 1; h < 16; h <<= 1)
 #pragma unroll
@@ -79,13 +75,14 @@ __device__ __forceinline__ void cp_async16(float4 *dst, const void *src, int byt
                : "memory");
 }
 
-// Persistent stage 1.  Cluster k of the grid (C CTAs) takes items k, k + #clusters, ... where an item is one
-// (slab, i1) pair; CTA `rank` of the cluster transforms rows [i1 N2 + rank 4096, + 4096) of the slab.  Each CTA
-// double-buffers its 4096 x 4 tile in shared memory: the rows of the next item stream in with cp.async while
-// the current one is transformed and combined.  T out: [N1][umax][slabs] float4, rows u < *U valid.
+// Persistent stage 1.  CTA k takes items k, k + gridDim.x, ... where an item is one (slab, i1) pair: rows
+// [i1 4096, +4096) of the 4-column slab.  Each CTA double-buffers its 4096 x 4 tile in shared memory: the rows of
+// the next item stream in with cp.async while the current one is transformed.  Thread (q, h) = (t / 2, t % 2)
+// transforms column pair h (a float2) of 16 rows per phase, so 16 warps share the work.  T out:
+// [N1][umax][slabs] float4, rows u < *U valid.
 __global__ void __launch_bounds__(kThreads, 1) srht_stage1_kernel(const float *__restrict__ A, int64_t m, int64_t n,
                                                                    int64_t lda, const float *__restrict__ b,
-                                                                   const uint32_t *__restrict__ sign_bits, int csize,
+                                                                   const uint32_t *__restrict__ sign_bits,
                                                                    const uint32_t *__restrict__ r2_list,
                                                                    const int *__restrict__ U_ptr, int64_t umax,
                                                                    int64_t slabs, int64_t N1, float4 *__restrict__ T,
@@ -93,21 +90,17 @@ __global__ void __launch_bounds__(kThreads, 1) srht_stage1_kernel(const float *_
   extern __shared__ float4 sm[];   // two buffers of kRowsCta float4, swizzled; sign words; the r2 list
   uint32_t *sgn = reinterpret_cast<uint32_t *>(sm + 2 * kRowsCta);  // 2 x kRowsCta / 32 sign words
   uint32_t *r2s = sgn + 2 * (kRowsCta / 32);                          // the needed r2 (U <= kRowsCta entries)
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank();
-  const int64_t nclusters = gridDim.x / csize, cid = blockIdx.x / csize;
   const int64_t items = slabs * N1;
-  const int64_t N2 = (int64_t)kRowsCta * csize;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, q = t >> 1, h = t & 1;
   const int U = *U_ptr;
   for (int u = t; u < U; u += kThreads) r2s[u] = r2_list[u];  // no global loads inside the per-item phases
 
   auto issue = [&](int64_t item, float4 *buf, uint32_t *sw) {
     const int64_t slab = item % slabs, i1 = item / slabs;
-    const int64_t row16 = i1 * N2 + (int64_t)rank * kRowsCta + t * 16;
+    const int64_t row8 = i1 * kRowsCta + t * 8;
     const int64_t c0 = slab * 4;
     if (t < kRowsCta / 32) {  // this tile's sign words, with the tile (rows past m read as +1)
-      const int64_t w = (i1 * N2 + (int64_t)rank * kRowsCta) / 32 + t;
+      const int64_t w = i1 * (kRowsCta / 32) + t;
       const bool in = w * 32 < m;
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(sw + t)),
                    "l"(in ? sign_bits + w : sign_bits), "r"(in ? 4 : 0)
@@ -115,84 +108,69 @@ __global__ void __launch_bounds__(kThreads, 1) srht_stage1_kernel(const float *_
     }
     if (vec && c0 + 3 < n) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int64_t row = row16 + j;
-        cp_async16(buf + swz(t * 16 + j), row < m ? (const void *)(A + row * lda + c0) : (const void *)A,
+      for (int j = 0; j < 8; ++j) {
+        const int64_t row = row8 + j;
+        cp_async16(buf + swz(t * 8 + j), row < m ? (const void *)(A + row * lda + c0) : (const void *)A,
                    row < m ? 16 : 0);
       }
     } else {  // the slab holding b, or unaligned rows: plain loads
 #pragma unroll
-      for (int j = 0; j < 16; ++j) buf[swz(t * 16 + j)] = load_slab(A, m, n, lda, b, row16 + j, c0, vec);
+      for (int j = 0; j < 8; ++j) buf[swz(t * 8 + j)] = load_slab(A, m, n, lda, b, row8 + j, c0, vec);
     }
   };
 
-  int64_t item = cid;
+  int64_t item = blockIdx.x;
   int cur = 0;
   if (item < items) issue(item, sm, sgn);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
-  for (; item < items; item += nclusters, cur ^= 1) {
+  for (; item < items; item += gridDim.x, cur ^= 1) {
     float4 *S = sm + cur * kRowsCta;
+    float2 *S2 = reinterpret_cast<float2 *>(S) + h;   // column pair h of float4 slot k: S2[2 k]
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    // the tile is in, and every thread is done with the other buffer (the previous combine) before it is refilled
     __syncthreads();
-    // every CTA of the cluster is done reading the other buffer (the previous combine) before it is refilled
-    cluster.sync();
-    if (item + nclusters < items) issue(item + nclusters, sm + (cur ^ 1) * kRowsCta, sgn + (cur ^ 1) * (kRowsCta / 32));
+    if (item + gridDim.x < items) issue(item + gridDim.x, sm + (cur ^ 1) * kRowsCta, sgn + (cur ^ 1) * (kRowsCta / 32));
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 
     const int64_t slab = item % slabs, i1 = item / slabs;
-    float4 v[16];
-    // phase 1: rows t*16 + j, sign flip, bits 0..3
+    float2 v[16];
+    // phase 1: rows q*16 + j, sign flip, bits 0..3
     {
-      const uint32_t gw = sgn[cur * (kRowsCta / 32) + (t >> 1)] >> ((t & 1) * 16);  // rows t*16 .. t*16 + 15
+      const uint32_t gw = sgn[cur * (kRowsCta / 32) + (q >> 1)] >> ((q & 1) * 16);  // rows q*16 .. q*16 + 15
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        float4 x = S[swz(t * 16 + j)];
-        if ((gw >> j) & 1u) x = make_float4(-x.x, -x.y, -x.z, -x.w);
+        float2 x = S2[2 * swz(q * 16 + j)];
+        if ((gw >> j) & 1u) x = make_float2(-x.x, -x.y);
         v[j] = x;
       }
       fwht16(v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) S[swz(t * 16 + j)] = v[j];
+      for (int j = 0; j < 16; ++j) S2[2 * swz(q * 16 + j)] = v[j];
     }
     __syncthreads();
     // phase 2: bits 4..7 (each thread rewrites exactly the slots it read)
     {
-      const int lo = t & 15, hi = t >> 4;
+      const int lo = q & 15, hi = q >> 4;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = S[swz(lo | (j << 4) | (hi << 8))];
+      for (int j = 0; j < 16; ++j) v[j] = S2[2 * swz(lo | (j << 4) | (hi << 8))];
       fwht16(v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) S[swz(lo | (j << 4) | (hi << 8))] = v[j];
+      for (int j = 0; j < 16; ++j) S2[2 * swz(lo | (j << 4) | (hi << 8))] = v[j];
     }
     __syncthreads();
     // phase 3: bits 8..11
     {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = S[swz(t | (j << 8))];
+      for (int j = 0; j < 16; ++j) v[j] = S2[2 * swz(q | (j << 8))];
       fwht16(v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) S[swz(t | (j << 8))] = v[j];
+      for (int j = 0; j < 16; ++j) S2[2 * swz(q | (j << 8))] = v[j];
     }
-    // every CTA of the cluster has its 4096-point transform of this item in shared memory
-    cluster.sync();
-    // combine over the cluster (index bits 12.. of i2) for the needed r2, split across the cluster's CTAs
+    __syncthreads();
+    // the transformed rows whose index occurs among the sampled low parts r2
     float4 *Tout = T + i1 * umax * slabs;
-    for (int u = rank + csize * t; u < U; u += csize * kThreads) {
-      const uint32_t r2 = r2s[u];
-      const int lo = (int)(r2 & (kRowsCta - 1));
-      const int hi = (int)(r2 >> 12);
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int c = 0; c < csize; ++c) {
-        const float4 *peer = cluster.map_shared_rank(S, c);
-        const float4 x = peer[swz(lo)];
-        const float sg = (__popc(hi & c) & 1) ? -1.f : 1.f;
-        acc = make_float4(fmaf(sg, x.x, acc.x), fmaf(sg, x.y, acc.y), fmaf(sg, x.z, acc.z), fmaf(sg, x.w, acc.w));
-      }
-      Tout[(int64_t)u * slabs + slab] = acc;
-    }
+    for (int u = t; u < U; u += kThreads) Tout[(int64_t)u * slabs + slab] = S[swz((int)r2s[u])];
   }
-  // keep this CTA's shared memory alive until every peer has read it
-  cluster.sync();
 }
 
 // C[k, :] for sampled row r = idx[k]: (1/sqrt(s)) sum_{i1} (-1)^popc(r1 & i1) T[i1, slot(r2)].
@@ -259,18 +237,16 @@ __global__ void __launch_bounds__(1024) srht_compact_r2_kernel(const uint32_t *m
 
 struct SrhtPlan {
   int64_t N, N2, N1, slabs;
-  int csize;
 };
 
 SrhtPlan srht_plan(int64_t m, int64_t ntot) {
   SrhtPlan p;
   p.N = 1;
   while (p.N < m) p.N <<= 1;
-  // One CTA per 4096-row block: a cluster that combines several blocks over DSMEM moves about as many bytes
-  // between shared memories as it reads from HBM and waits on two cluster barriers per tile, which measured
-  // slower than writing the needed rows of each block and combining N / 4096 blocks in stage 2.
-  p.csize = 1;
-  p.N2 = (int64_t)kRowsCta * p.csize;
+  // One CTA per 4096-row block: combining several blocks in a thread-block cluster over DSMEM moves about as many
+  // bytes between shared memories as the CTAs read from HBM and adds two cluster barriers per tile, which measured
+  // slower than writing the needed rows of each block and combining the N / 4096 blocks in stage 2.
+  p.N2 = kRowsCta;
   p.N1 = p.N > p.N2 ? p.N / p.N2 : 1;
   p.slabs = (ntot + 3) / 4;
   return p;
@@ -328,33 +304,21 @@ int rmc_launch_srht(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t 
   const bool vec = (lda % 4 == 0) && (reinterpret_cast<uintptr_t>(A) % 16 == 0);
   const size_t smem = 2 * sizeof(float4) * kRowsCta + sizeof(uint32_t) * (2 * (kRowsCta / 32) + (size_t)p.N2);
   RMC_TRY_CUDA(cudaFuncSetAttribute(srht_stage1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(kThreads, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = p.csize;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  // as many clusters as are co-resident (one CTA per SM), each looping over (slab, i1) items
+  // as many CTAs as are co-resident (one per SM), each looping over (slab, i1) items
   const int64_t items = p.slabs * p.N1;
-  cfg.gridDim = dim3((unsigned)p.csize, 1, 1);
-  int nclusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&nclusters, srht_stage1_kernel, &cfg) != cudaSuccess || nclusters < 1) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, srht_stage1_kernel, kThreads, smem) != cudaSuccess ||
+      per_sm < 1) {
     (void)cudaGetLastError();
-    nclusters = std::max(1, ctx->num_sms / (2 * p.csize));
+    per_sm = 1;
   }
-  if (nclusters > items) nclusters = (int)items;
-  cfg.gridDim = dim3((unsigned)(nclusters * p.csize), 1, 1);
+  const int64_t grid = std::min<int64_t>(items, (int64_t)per_sm * ctx->num_sms);
   rmc_note_launch(2);
   {
     RmcProf prof(ctx, RMC_K_SRHT);
-    RMC_TRY_CUDA(cudaLaunchKernelEx(&cfg, srht_stage1_kernel, A, m, n, lda, b, (const uint32_t *)bf.sign_bits,
-                                    p.csize, (const uint32_t *)bf.list, (const int *)bf.U, umax, p.slabs, p.N1,
-                                    bf.T, vec));
+    srht_stage1_kernel<<<(unsigned)grid, kThreads, smem, st>>>(A, m, n, lda, b, (const uint32_t *)bf.sign_bits,
+                                                               (const uint32_t *)bf.list, (const int *)bf.U, umax,
+                                                               p.slabs, p.N1, bf.T, vec);
   }
   const float scale = 1.0f / sqrtf((float)s);
   RmcProf prof(ctx, RMC_K_SRHT_REDUCE);
