@@ -78,22 +78,21 @@ __device__ __forceinline__ void cp_async16(float4 *dst, const void *src, int byt
 // Persistent stage 1.  CTA k takes items k, k + gridDim.x, ... where an item is one (slab, i1) pair: rows
 // [i1 4096, +4096) of the 4-column slab.  Each CTA double-buffers its 4096 x 4 tile in shared memory: the rows of
 // the next item stream in with cp.async while the current one is transformed.  Thread (q, h) = (t / 2, t % 2)
-// transforms column pair h (a float2) of 16 rows per phase, so 16 warps share the work.  T out:
-// [N1][umax][slabs] float4, rows u < *U valid.
+// transforms column pair h (a float2) of 16 rows per phase, so 16 warps share the work, and the last phase writes
+// the rows that occur in the sample straight from registers.  T out: [N1][umax][slabs] float4.
 __global__ void __launch_bounds__(kThreads, 1) srht_stage1_kernel(const float *__restrict__ A, int64_t m, int64_t n,
                                                                    int64_t lda, const float *__restrict__ b,
                                                                    const uint32_t *__restrict__ sign_bits,
-                                                                   const uint32_t *__restrict__ r2_list,
-                                                                   const int *__restrict__ U_ptr, int64_t umax,
+                                                                   const uint32_t *__restrict__ mark,
+                                                                   const uint32_t *__restrict__ slot, int64_t umax,
                                                                    int64_t slabs, int64_t N1, float4 *__restrict__ T,
                                                                    bool vec) {
-  extern __shared__ float4 sm[];   // two buffers of kRowsCta float4, swizzled; sign words; the r2 list
+  extern __shared__ float4 sm[];   // two buffers of kRowsCta float4, swizzled; sign words; row -> slot table
   uint32_t *sgn = reinterpret_cast<uint32_t *>(sm + 2 * kRowsCta);  // 2 x kRowsCta / 32 sign words
-  uint32_t *r2s = sgn + 2 * (kRowsCta / 32);                          // the needed r2 (U <= kRowsCta entries)
+  int *rslot = reinterpret_cast<int *>(sgn + 2 * (kRowsCta / 32));   // slot of local row r2 in T, or -1
   const int64_t items = slabs * N1;
   const int t = threadIdx.x, q = t >> 1, h = t & 1;
-  const int U = *U_ptr;
-  for (int u = t; u < U; u += kThreads) r2s[u] = r2_list[u];  // no global loads inside the per-item phases
+  for (int r = t; r < kRowsCta; r += kThreads) rslot[r] = mark[r] ? (int)slot[r] : -1;
 
   auto issue = [&](int64_t item, float4 *buf, uint32_t *sw) {
     const int64_t slab = item % slabs, i1 = item / slabs;
@@ -158,18 +157,18 @@ __global__ void __launch_bounds__(kThreads, 1) srht_stage1_kernel(const float *_
       for (int j = 0; j < 16; ++j) S2[2 * swz(lo | (j << 4) | (hi << 8))] = v[j];
     }
     __syncthreads();
-    // phase 3: bits 8..11
+    // phase 3: bits 8..11, then the rows whose index occurs among the sampled low parts r2 go to T
     {
 #pragma unroll
       for (int j = 0; j < 16; ++j) v[j] = S2[2 * swz(q | (j << 8))];
       fwht16(v);
+      float2 *Tout = reinterpret_cast<float2 *>(T + i1 * umax * slabs + slab) + h;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) S2[2 * swz(q | (j << 8))] = v[j];
+      for (int j = 0; j < 16; ++j) {
+        const int u = rslot[q | (j << 8)];
+        if (u >= 0) Tout[(int64_t)u * slabs * 2] = v[j];
+      }
     }
-    __syncthreads();
-    // the transformed rows whose index occurs among the sampled low parts r2
-    float4 *Tout = T + i1 * umax * slabs;
-    for (int u = t; u < U; u += kThreads) Tout[(int64_t)u * slabs + slab] = S[swz((int)r2s[u])];
   }
 }
 
@@ -317,8 +316,8 @@ int rmc_launch_srht(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t 
   {
     RmcProf prof(ctx, RMC_K_SRHT);
     srht_stage1_kernel<<<(unsigned)grid, kThreads, smem, st>>>(A, m, n, lda, b, (const uint32_t *)bf.sign_bits,
-                                                               (const uint32_t *)bf.list, (const int *)bf.U, umax,
-                                                               p.slabs, p.N1, bf.T, vec);
+                                                               (const uint32_t *)bf.mark, (const uint32_t *)bf.slot,
+                                                               umax, p.slabs, p.N1, bf.T, vec);
   }
   const float scale = 1.0f / sqrtf((float)s);
   RmcProf prof(ctx, RMC_K_SRHT_REDUCE);

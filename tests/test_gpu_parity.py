@@ -145,6 +145,18 @@ def test_lsr_large_n(R, n):
     assert relfro(x.cpu().numpy(), xo) < 1e-4
 
 
+@pytest.mark.parametrize("n", [33, 250, 256])
+def test_lsr_single_cta_factor(R, n):
+    """n <= 256: the factorization, R^-1 and M = R^-1 R^-T in one CTA's shared memory (ragged and full last
+    32-column block)."""
+    m, s = 8 * n, 4 * n
+    A, b, _ = workloads.tall_lsr_numpy(m, n, seed=n + 1)
+    x = R.rmc_lsr_sketch(dev(A), dev(b), s, "countsketch", seed=11)
+    R.rmc_sync()
+    xo = lsr.lsr_sketch(A, b, s, "countsketch", 11)
+    assert relfro(x.cpu().numpy(), xo) < 1e-4
+
+
 def test_lsr_noise_free_exact(R):
     A, _, xt = workloads.tall_lsr_numpy(5000, 12, seed=3, noise_std=0.0)
     b = (A.astype(np.float64) @ xt).astype(np.float32)
