@@ -239,7 +239,7 @@ int rmc_server_drain(rmc_server *srv);
 
 /* Kernel tags for rmc_profile_read. */
 #define RMC_K_COUNTSKETCH  0   /* count-sketch gather-accumulate pass over A                         */
-#define RMC_K_SRHT         1   /* SRHT stage 1: sign flip + in-cluster FWHT of A's row blocks        */
+#define RMC_K_SRHT         1   /* SRHT stage 1: sign flip + FWHT of A's 4096-row blocks              */
 #define RMC_K_SRHT_REDUCE  2   /* SRHT stage 2: combination of the row blocks for the sampled rows   */
 #define RMC_K_GAUSSIAN     3   /* Gaussian sketch product with in-kernel Philox draws                */
 #define RMC_K_MATMUL_AN    4   /* Y = A X                                                            */
@@ -255,6 +255,16 @@ int rmc_server_drain(rmc_server *srv);
 int rmc_profile_begin(rmc_ctx *ctx);
 int rmc_profile_read(rmc_ctx *ctx, int tag, int64_t *launches, double *total_ms);
 int rmc_profile_end(rmc_ctx *ctx);
+
+/* Launch intervals, for kernels that run concurrently on several streams (a launch's event pair then also
+ * spans the time it waits for another stream's CTAs to leave the SMs).  rmc_profile_reference records one
+ * process-wide reference event on the context's stream.  rmc_profile_spans waits for the stream and writes, for
+ * each launch of `tag` recorded on this context since rmc_profile_begin and completed after the reference was
+ * recorded, its start and stop times in milliseconds relative to that reference (host arrays of `max` entries;
+ * *count = the number written; at most 4096 per context).  Errors: RMC_EINVAL (no reference recorded, bad
+ * argument), RMC_ECUDA. */
+int rmc_profile_reference(rmc_ctx *ctx);
+int rmc_profile_spans(rmc_ctx *ctx, int tag, double *start_ms, double *stop_ms, int max, int *count);
 
 /* Number of kernels this library has launched in the process so far (all contexts). */
 int rmc_launch_counter(uint64_t *launches);

@@ -49,6 +49,9 @@ _SIGS.update({
     "rmc_profile_begin": [_p],
     "rmc_profile_read": [_p, _int, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)],
     "rmc_profile_end": [_p],
+    "rmc_profile_reference": [_p],
+    "rmc_profile_spans": [_p, _int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _int,
+                          ctypes.POINTER(_int)],
     "rmc_launch_counter": [ctypes.POINTER(_u64)],
     "rmc_countsketch_noalloc": [_p, _p, _i64, _i64, _i64, _i64, _u64, _p, _i64],
 })
@@ -290,6 +293,25 @@ def rmc_profile_read(tag):
         total_n += n.value
         total_ms += ms.value
     return total_n, total_ms
+
+
+def rmc_profile_reference():
+    """Record the process-wide reference event of rmc_profile_spans on the current stream's context."""
+    _check(lib.rmc_profile_reference(context().bind()), "rmc_profile_reference")
+
+
+def rmc_profile_spans(tag):
+    """[(start_ms, stop_ms)] of every launch of one kernel tag since rmc_profile_begin that completed after the
+    reference, relative to the reference, over the contexts of the current device."""
+    out = []
+    cap = 4096
+    t0 = (ctypes.c_double * cap)()
+    t1 = (ctypes.c_double * cap)()
+    for c in _device_contexts():
+        n = ctypes.c_int()
+        _check(lib.rmc_profile_spans(c.handle, tag, t0, t1, cap, ctypes.byref(n)), "rmc_profile_spans")
+        out.extend((t0[i], t1[i]) for i in range(n.value))
+    return out
 
 
 def rmc_profile_end():

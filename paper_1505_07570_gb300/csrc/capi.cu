@@ -76,6 +76,9 @@ int rmc_destroy(rmc_ctx *ctx) {
     }
     delete[] ctx->prof_recs;
   }
+  delete[] ctx->span_tag;
+  delete[] ctx->span_start;
+  delete[] ctx->span_stop;
   if (ctx->ws) cudaFree(ctx->ws);
   cudaFree(ctx->d_status);
   cudaFreeHost(ctx->h_status);
@@ -360,7 +363,12 @@ RmcProf::~RmcProf() {
   if (rec >= 0) cudaEventRecord(ctx->prof_recs[rec].stop, ctx->stream);
 }
 
-// Fold finished records into the per-tag totals and recycle their events.
+// Process-wide reference event of the launch intervals (recorded by rmc_profile_reference).
+static cudaEvent_t g_prof_ref = nullptr;
+static bool g_prof_ref_recorded = false;
+
+// Fold finished records into the per-tag totals (and, once a reference is recorded, the interval list) and
+// recycle their events.
 static int prof_drain(rmc_ctx *ctx) {
   RMC_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
   for (int r = 0; r < ctx->prof_used; ++r) {
@@ -369,6 +377,19 @@ static int prof_drain(rmc_ctx *ctx) {
     const int tag = ctx->prof_recs[r].tag;
     ctx->prof_launches[tag] += 1;
     ctx->prof_ms[tag] += ms;
+    if (g_prof_ref_recorded && ctx->prof_nspans < ctx->prof_cap) {
+      float t0 = 0.f, t1 = 0.f;
+      // a launch recorded before the reference has no interval (the elapsed time would be negative)
+      if (cudaEventElapsedTime(&t0, g_prof_ref, ctx->prof_recs[r].start) == cudaSuccess &&
+          cudaEventElapsedTime(&t1, g_prof_ref, ctx->prof_recs[r].stop) == cudaSuccess && t0 >= 0.f) {
+        ctx->span_tag[ctx->prof_nspans] = tag;
+        ctx->span_start[ctx->prof_nspans] = t0;
+        ctx->span_stop[ctx->prof_nspans] = t1;
+        ++ctx->prof_nspans;
+      } else {
+        (void)cudaGetLastError();
+      }
+    }
   }
   ctx->prof_used = 0;
   return RMC_OK;
@@ -382,6 +403,10 @@ int rmc_profile_begin(rmc_ctx *ctx) {
     const int cap = 4096;
     ctx->prof_recs = new (std::nothrow) RmcProfRec[cap];
     if (!ctx->prof_recs) return RMC_ENOMEM;
+    ctx->span_tag = new (std::nothrow) int[cap];
+    ctx->span_start = new (std::nothrow) double[cap];
+    ctx->span_stop = new (std::nothrow) double[cap];
+    if (!ctx->span_tag || !ctx->span_start || !ctx->span_stop) return RMC_ENOMEM;
     for (int r = 0; r < cap; ++r) {
       RMC_TRY_CUDA(cudaEventCreate(&ctx->prof_recs[r].start));
       RMC_TRY_CUDA(cudaEventCreate(&ctx->prof_recs[r].stop));
@@ -390,6 +415,7 @@ int rmc_profile_begin(rmc_ctx *ctx) {
   }
   RMC_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->prof_used = 0;
+  ctx->prof_nspans = 0;
   for (int t = 0; t < RMC_K_NTAGS; ++t) {
     ctx->prof_launches[t] = 0;
     ctx->prof_ms[t] = 0.0;
@@ -403,6 +429,30 @@ int rmc_profile_read(rmc_ctx *ctx, int tag, int64_t *launches, double *total_ms)
   RMC_TRY(prof_drain(ctx));
   *launches = ctx->prof_launches[tag];
   *total_ms = ctx->prof_ms[tag];
+  return RMC_OK;
+}
+
+int rmc_profile_reference(rmc_ctx *ctx) {
+  if (!ctx) return RMC_EINVAL;
+  if (!g_prof_ref) RMC_TRY_CUDA(cudaEventCreate(&g_prof_ref));
+  RMC_TRY_CUDA(cudaEventRecord(g_prof_ref, ctx->stream));
+  g_prof_ref_recorded = true;
+  return RMC_OK;
+}
+
+int rmc_profile_spans(rmc_ctx *ctx, int tag, double *start_ms, double *stop_ms, int max, int *count) {
+  if (!ctx || tag < 0 || tag >= RMC_K_NTAGS || !count || max < 0 || (max > 0 && (!start_ms || !stop_ms)))
+    return RMC_EINVAL;
+  if (!g_prof_ref_recorded) return RMC_EINVAL;
+  RMC_TRY(prof_drain(ctx));
+  int n = 0;
+  for (int i = 0; i < ctx->prof_nspans && n < max; ++i)
+    if (ctx->span_tag[i] == tag) {
+      start_ms[n] = ctx->span_start[i];
+      stop_ms[n] = ctx->span_stop[i];
+      ++n;
+    }
+  *count = n;
   return RMC_OK;
 }
 

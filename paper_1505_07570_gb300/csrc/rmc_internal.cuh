@@ -28,6 +28,9 @@ struct rmc_ctx {
   RmcProfRec *prof_recs;
   int64_t prof_launches[RMC_K_NTAGS];
   double prof_ms[RMC_K_NTAGS];
+  int prof_nspans;      // drained launch intervals relative to the process-wide reference event
+  int *span_tag;
+  double *span_start, *span_stop;
   // pinned staging for host-built descriptors (batched launches); reused once stage_ev has completed
   void *h_stage;
   size_t h_stage_bytes;

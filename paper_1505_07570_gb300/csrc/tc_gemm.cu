@@ -38,14 +38,37 @@ constexpr int kThreads = 32 * (kRngWarp0 + kRngWarps);
 constexpr int kTmemCols = kMT * kN;               // 512
 constexpr size_t kSmemBytes = 1024 + (size_t)kStgStages * kBBytes + (size_t)kStages * kStageBytes + 256;
 
-// Box-Muller with the fast hardware approximations: the operands are rounded to TF32 (10-bit mantissa)
-// before they reach the tensor cores, far coarser than these functions' ~2^-21 error.
+// Approximate special functions (PTX .approx with flush-to-zero).  Every argument here is a normal number (u in
+// [2^-24, 1), -2 ln u >= 2^-24, angles in (-pi, pi)), so the subnormal handling of the default forms is skipped.
+__device__ __forceinline__ float lg2_ftz(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sin_ftz(float x) {
+  float y;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float cos_ftz(float x) {
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Box-Muller with the hardware approximations: the operands are rounded to TF32 (10-bit mantissa) before they
+// reach the tensor cores, far coarser than these approximations' ~2^-21 error.  -2 ln u = (-2 ln 2) log2 u; the
+// angle is shifted by -pi into (-pi, pi) and both outputs negated to compensate.
 __device__ __forceinline__ float2 box_muller_fast(uint32_t wa, uint32_t wb) {
-  const float t = -2.0f * __logf(unit_f32(wa));
-  const float r = t * rsqrtf(t);
-  float sn, cs;
-  __sincosf(6.283185307179586f * (unit_f32(wb) - 0.5f), &sn, &cs);   // angle - pi, in (-pi, pi)
-  return make_float2(-r * cs, -r * sn);
+  const float t = -1.3862943611198906f * lg2_ftz(unit_f32(wa));
+  const float r = t * rsqrt_ftz(t);
+  const float a = 6.283185307179586f * (unit_f32(wb) - 0.5f);
+  return make_float2(-r * cos_ftz(a), -r * sin_ftz(a));
 }
 
 // Round to TF32 (10-bit mantissa), to nearest with ties away from zero, as cvt.rna.tf32.f32 does, with integer

@@ -77,3 +77,13 @@ def test_reference_arm_runs_on_rank_zero_only():
     assert printed[1] == ""  # rank 1 exits 0 without work
     line = json.loads(printed[0].splitlines()[-1])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+
+
+def test_union_of_launch_intervals():
+    """The roofline's device time for launches that overlap on several streams: the union of their intervals."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.union_ms([]) == 0.0
+    assert bench.union_ms([(0.0, 2.0), (1.0, 3.0)]) == pytest.approx(3.0)      # overlapping
+    assert bench.union_ms([(5.0, 6.0), (0.0, 1.0)]) == pytest.approx(2.0)      # disjoint, unsorted
+    assert bench.union_ms([(0.0, 4.0), (1.0, 2.0), (3.0, 5.0)]) == pytest.approx(5.0)  # nested + chained
