@@ -200,14 +200,14 @@ __global__ void srht_stage2_kernel(const float4 *__restrict__ T, int64_t N1, int
   }
 }
 
-// Distinct low parts r2 = idx & (N2 - 1) of the sample: mark, then compact in one block (N2 <= 32768).
+// Distinct low parts r2 = idx & (N2 - 1) of the sample: mark, then number them in ascending order in one block
+// (N2 <= 32768): slot[r2] = the row of T that holds r2.
 __global__ void srht_mark_r2_kernel(const int64_t *idx, int64_t s, int64_t N2, uint32_t *mark) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < s; k += (int64_t)gridDim.x * blockDim.x)
     mark[idx[k] & (N2 - 1)] = 1u;
 }
 
-__global__ void __launch_bounds__(1024) srht_compact_r2_kernel(const uint32_t *mark, int64_t N2, uint32_t *slot,
-                                                               uint32_t *list, int *U_out) {
+__global__ void __launch_bounds__(1024) srht_compact_r2_kernel(const uint32_t *mark, int64_t N2, uint32_t *slot) {
   __shared__ uint32_t part[1024];
   const int per = (int)((N2 + 1023) / 1024);
   const int lo = threadIdx.x * per;
@@ -225,13 +225,8 @@ __global__ void __launch_bounds__(1024) srht_compact_r2_kernel(const uint32_t *m
   uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
   for (int k = 0; k < per; ++k) {
     const int64_t r = lo + k;
-    if (r < N2 && mark[r]) {
-      slot[r] = run;
-      list[run] = (uint32_t)r;
-      ++run;
-    }
+    if (r < N2 && mark[r]) slot[r] = run++;
   }
-  if (threadIdx.x == 1023) *U_out = (int)part[1023];
 }
 
 struct SrhtPlan {
@@ -254,8 +249,7 @@ SrhtPlan srht_plan(int64_t m, int64_t ntot) {
 struct SrhtBufs {
   int64_t *idx;
   uint32_t *sign_bits;
-  uint32_t *mark, *slot, *list;
-  int *U;
+  uint32_t *mark, *slot;
   float4 *T;
   void *sample_ws;
 };
@@ -266,8 +260,6 @@ SrhtBufs srht_carve(WsCarve &w, const SrhtPlan &p, int64_t s) {
   b.sign_bits = w.take<uint32_t>(p.N / 32 + 1);
   b.mark = w.take<uint32_t>(p.N2);
   b.slot = w.take<uint32_t>(p.N2);
-  b.list = w.take<uint32_t>(p.N2);
-  b.U = w.take<int>(4);
   const int64_t umax = s < p.N2 ? s : p.N2;
   b.T = w.take<float4>(p.N1 * umax * p.slabs);
   b.sample_ws = w.take<char>(rmc_srht_sample_ws(p.N));
@@ -294,7 +286,7 @@ int rmc_launch_srht(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t 
   RMC_TRY(rmc_launch_srht_sample(ctx, seed, instance, p.N, s, bf.idx, bf.sample_ws));
   RMC_TRY_CUDA(cudaMemsetAsync(bf.mark, 0, sizeof(uint32_t) * p.N2, st));
   srht_mark_r2_kernel<<<rmc_blocks(s, 256, 1024), 256, 0, st>>>(bf.idx, s, p.N2, bf.mark);
-  srht_compact_r2_kernel<<<1, 1024, 0, st>>>(bf.mark, p.N2, bf.slot, bf.list, bf.U);
+  srht_compact_r2_kernel<<<1, 1024, 0, st>>>(bf.mark, p.N2, bf.slot);
   srht_signs_kernel<<<rmc_blocks(m, 256, 4096), 256, 0, st>>>(seed, instance, m, bf.sign_bits);
   rmc_note_launch(3);
   RMC_LAUNCH_CHECK();
