@@ -54,3 +54,27 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.rmc_sketch(None, None, 0, 0, 0, 0, 0, 0, 0, None, 0) == 1     # RMC_EINVAL
     assert lib.rmc_create(None, None, 0) == 1
     assert lib.rmc_destroy(None) == 0
+
+
+def test_profile_hooks_reject_bad_arguments_without_gpu(lib):
+    lib.rmc_profile_reference.restype = ctypes.c_int
+    lib.rmc_profile_spans.restype = ctypes.c_int
+    n = ctypes.c_int(-1)
+    assert lib.rmc_profile_reference(None) == 1                                 # RMC_EINVAL
+    assert lib.rmc_profile_spans(None, 3, None, None, 0, ctypes.byref(n)) == 1  # RMC_EINVAL
+    assert lib.rmc_profile_begin(None) == 1
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/*.h is a C ABI: every header compiles as C99 on its own (no C++ or CUDA types leak in)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    for h in HEADERS:
+        src = tmp_path / "use.c"
+        src.write_text('#include "%s"\nint main(void) { return 0; }\n' % h)
+        r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-fsyntax-only", str(src)], capture_output=True,
+                           text=True)
+        assert r.returncode == 0, r.stderr
