@@ -63,7 +63,7 @@ extern "C" {
 /* ------------------------------------------------------------- GEMM operand precision (accumulate FP32) */
 #define RMC_FP32  0   /* FP32 operands on the CUDA cores (the plain form)                                 */
 #define RMC_TF32  1   /* TF32 operands on the tensor cores (tcgen05.mma kind::tf32), FP32 accumulation    */
-#define RMC_BF16  2   /* BF16 operands on the tensor cores (tcgen05.mma kind::f16), FP32 accumulation     */
+#define RMC_BF16  2   /* reserved for BF16 operands (tcgen05.mma kind::f16): not built, rejected with RMC_EINVAL */
 
 typedef struct rmc_ctx rmc_ctx;
 
@@ -100,7 +100,8 @@ int rmc_workspace_bytes(const rmc_ctx *ctx, size_t *bytes);
  *                   unnormalised Hadamard matrix H_N (Sylvester order), s sampled rows without replacement
  *                   kept in ascending index order, scaled by 1/sqrt(s) (Sec. 3.2.2); 1 <= s <= N.
  *         RMC_COUNTSKETCH: C[h(i), :] += g(i) A[i, :] for every row i (Algorithm 3.1); any s >= 1.
- *   prec  GEMM operand precision of the Gaussian kind (RMC_FP32, RMC_TF32, RMC_BF16); ignored otherwise.
+ *   prec  GEMM operand precision of the Gaussian kind (RMC_FP32 or RMC_TF32); ignored otherwise, but
+ *         always checked (any other value is RMC_EINVAL).
  *         The tensor-core forms stream A with TMA and need 16-byte aligned rows (A and lda * 4 multiples of
  *         16 bytes); other layouts run the FP32 CUDA-core kernel.
  *   seed  64-bit Philox key; the same (seed, m, s, kind) always gives the same S.
@@ -208,7 +209,7 @@ int rmc_batch_run(rmc_ctx *ctx, const rmc_request *reqs, int nreq);
 typedef struct rmc_serve_request {
   rmc_request req;
   int sketch;   /* LSR: RMC_GAUSSIAN, RMC_SRHT or RMC_COUNTSKETCH (RSVD: ignored)                        */
-  int prec;     /* RMC_FP32, RMC_TF32 or RMC_BF16: operand precision of the products with A                 */
+  int prec;     /* RMC_FP32 or RMC_TF32: operand precision of the products with A                            */
 } rmc_serve_request;
 
 typedef struct rmc_server rmc_server;
@@ -278,20 +279,21 @@ int rmc_launch_counter(uint64_t *launches);
  * for callers that must not allocate device memory at call time: a serving loop that reserves all of its
  * HBM up front and keeps allocation (which can synchronise the device) off its request path, or a host
  * framework whose device memory belongs to its own allocator.  Such a caller cannot use a context either,
- * since rmc_create allocates.  The paper has no counterpart; this is a deployment form of Algorithm 3.1.
+ * since rmc_create allocates.  The paper has no counterpart.
  *
  * Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.  The sorting scratch lives in
  * one file-scope __device__ array of RMC_NOALLOC_SCRATCH_BYTES (32 MiB), which every GPU that loads the
- * library holds until the process exits.  The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress, with the device current); make that first call before any stream capture.
- * All calls share the one array and it keeps the previous call's contents (the counters are cleared on
- * the stream before use), so calls whose work overlaps on the GPU -- on different streams, or from
- * different host threads -- race on it and must be serialised by the caller.
+ * library holds until the process exits.  Every call looks up that array's device address on the current
+ * device (cudaGetSymbolAddress); the first call on a device may load the module there, so make that first
+ * call before any stream capture.  All calls share the one array and it keeps the previous call's contents
+ * (the counters are cleared on the stream before use), so calls whose work overlaps on the GPU -- on
+ * different streams, or from different host threads -- race on it and must be serialised by the caller.
  *   cuda_stream: the cudaStream_t to enqueue on (NULL = legacy default stream), on the current device.
  *   A, C: device pointers as for rmc_sketch (A m x n, lda >= n; C s x n, ldc >= n).
  * Returns RMC_OK once enqueued; RMC_EINVAL for bad arguments; RMC_ESCRATCH when the call would need more
  * than RMC_NOALLOC_SCRATCH_BYTES (about 8 m + 4 s ceil(m / 1024) bytes; e.g. m = 2^20 rows fit up to
- * s = 4096); RMC_ECUDA if the address lookup or a launch fails.  Nothing is enqueued on error. */
+ * s = 4096); RMC_ECUDA if the address lookup or a launch fails.  Nothing is enqueued on RMC_EINVAL or
+ * RMC_ESCRATCH. */
 int rmc_countsketch_noalloc(void *cuda_stream, const float *A, int64_t m, int64_t n, int64_t lda, int64_t s,
                             uint64_t seed, float *C, int64_t ldc);
 

@@ -120,3 +120,17 @@ def lstsq_normal(A, b):
     for i in range(n - 1, -1, -1):
         x[i] = (Ab[i, n] - Ab[i, i + 1:n] @ x[i + 1:]) / Ab[i, i]
     return x
+
+
+def upper_inverse(R):
+    """R^-1 for an upper-triangular R with non-zero diagonal, by back substitution on each column of I
+    (column j solves R x = e_j from the last row up)."""
+    R = np.asarray(R, dtype=np.float64)
+    n = R.shape[0]
+    X = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        for i in range(n - 1, -1, -1):
+            X[i, j] = (e[i] - R[i, i + 1:] @ X[i + 1:, j]) / R[i, i]
+    return X

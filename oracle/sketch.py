@@ -170,3 +170,25 @@ def sketch_matrix(m, s, kind, seed, instance=0):
     """The explicit m x s sketching matrix S of any kind (tiny inputs only)."""
     kind = KINDS.get(kind, kind)
     return {"gaussian": gaussian_S, "srht": srht_S, "countsketch": countsketch_S}[kind](m, s, seed, instance)
+
+
+# ---------------------------------------------------------------- column count sketch (Sec. 3.2.3, Ch. 3 form)
+
+def countsketch_columns(A, s, seed, instance=0):
+    """C = A S with S an n x s count sketch (the column orientation of Ch. 3, Algorithm 3.1 over the columns):
+    C starts at zero; for each column j in increasing order, C[:, h(j)] += g(j) A[:, j], with the hashes of
+    stream 2 drawn for the n column indices.  Equal to countsketch(A^T, s)^T."""
+    A = np.asarray(A, dtype=np.float64)
+    bucket, sign = philox.countsketch_hash(seed, A.shape[1], s, instance)
+    C = np.zeros((A.shape[0], s))
+    for j in range(A.shape[1]):
+        C[:, bucket[j]] += sign[j] * A[:, j]
+    return C
+
+
+# ---------------------------------------------------------------- Gaussian projection + count sketch (Sec. 3.2.4)
+
+def gaussian_countsketch(A, s_cs, s, seed, instance_cs=2, instance_gp=3):
+    """S = S_cs S_gp (m x s): a count sketch to s_cs rows followed by a Gaussian projection to s rows, in the
+    row orientation: C = S_gp^T (S_cs^T A)."""
+    return gaussian_sketch(countsketch(A, s_cs, seed, instance_cs), s, seed, instance_gp)

@@ -127,9 +127,30 @@ def _ptr(t):
 
 
 def _mat(t, name):
+    """A CUDA float32 matrix with unit column stride on the current device (the library launches on the
+    current device and the current torch stream)."""
     import torch
     if not (t.is_cuda and t.dtype == torch.float32 and t.dim() == 2 and t.stride(1) == 1):
         raise ValueError("%s must be a CUDA float32 matrix with unit column stride" % name)
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError("%s is on %s but the current device is cuda:%d" % (name, t.device,
+                                                                          torch.cuda.current_device()))
+    if t.shape[0] > 1 and t.stride(0) < t.shape[1]:
+        raise ValueError("%s rows overlap (row stride %d < %d columns)" % (name, t.stride(0), t.shape[1]))
+    return t
+
+
+def _out(t, shape, dtype, like, name):
+    """A caller-supplied output: the exact shape and dtype, on ``like``'s device, unit column stride and
+    row-major rows that do not overlap, so that the kernels never write past its allocation."""
+    if not (t.is_cuda and t.dtype == dtype and tuple(t.shape) == tuple(shape) and t.device == like.device):
+        raise ValueError("%s must be a %s CUDA tensor of shape %s on %s (got %s %s on %s)"
+                         % (name, dtype, tuple(shape), like.device, t.dtype, tuple(t.shape), t.device))
+    if len(shape) == 2:
+        if t.stride(1) != 1 or (shape[0] > 1 and t.stride(0) < shape[1]):
+            raise ValueError("%s must be row-major with unit column stride" % name)
+    elif not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
     return t
 
 
@@ -163,7 +184,8 @@ def rmc_sketch(A, s, kind, seed, prec="fp32", out=None):
     import torch
     _mat(A, "A")
     m, n = A.shape
-    C = out if out is not None else torch.empty(s, n, device=A.device, dtype=torch.float32)
+    C = (_out(out, (s, n), torch.float32, A, "out") if out is not None
+         else torch.empty(s, n, device=A.device, dtype=torch.float32))
     _check(lib.rmc_sketch(context().bind(), _ptr(A), m, n, A.stride(0), s, _kind(kind), seed, _prec(prec),
                           _ptr(C), C.stride(0)), "rmc_sketch")
     return C
@@ -176,7 +198,10 @@ def rmc_lsr_sketch(A, b, s, kind, seed, prec="fp32", out=None):
     m, n = A.shape
     if not (b.is_cuda and b.dtype == torch.float32 and b.is_contiguous() and b.numel() == m):
         raise ValueError("b must be a contiguous CUDA float32 vector of length m")
-    x = out if out is not None else torch.empty(n, device=A.device, dtype=torch.float64)
+    if b.device != A.device:
+        raise ValueError("b must be on the device of A")
+    x = (_out(out, (n,), torch.float64, A, "out") if out is not None
+         else torch.empty(n, device=A.device, dtype=torch.float64))
     _check(lib.rmc_lsr_sketch(context().bind(), _ptr(A), m, n, A.stride(0), _ptr(b), s, _kind(kind), seed,
                               _prec(prec), _ptr(x)), "rmc_lsr_sketch")
     return x
@@ -332,7 +357,8 @@ def rmc_countsketch_noalloc(A, s, seed, out=None):
     import torch
     _mat(A, "A")
     m, n = A.shape
-    C = out if out is not None else torch.empty(s, n, device=A.device, dtype=torch.float32)
+    C = (_out(out, (s, n), torch.float32, A, "out") if out is not None
+         else torch.empty(s, n, device=A.device, dtype=torch.float32))
     _check(lib.rmc_countsketch_noalloc(_p(torch.cuda.current_stream().cuda_stream), _ptr(A), m, n, A.stride(0),
                                        s, seed, _ptr(C), C.stride(0)), "rmc_countsketch_noalloc")
     return C

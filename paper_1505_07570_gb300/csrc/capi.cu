@@ -134,7 +134,7 @@ int rmc_workspace_bytes(const rmc_ctx *ctx, size_t *bytes) {
 static int check_sketch_args(const float *A, int64_t m, int64_t n, int64_t lda, int64_t s, int kind, int prec) {
   if (!A || m < 1 || n < 1 || bad_ld(lda, n) || s < 1) return RMC_EINVAL;
   if (kind != RMC_GAUSSIAN && kind != RMC_SRHT && kind != RMC_COUNTSKETCH) return RMC_EINVAL;
-  if (prec != RMC_FP32 && prec != RMC_TF32 && prec != RMC_BF16) return RMC_EINVAL;
+  if (!rmc_prec_ok(prec)) return RMC_EINVAL;
   if (kind == RMC_SRHT && s > next_pow2(m)) return RMC_EINVAL;
   if (m > (int64_t(1) << 31) || s > (int64_t(1) << 31)) return RMC_EINVAL;
   return RMC_OK;
@@ -236,7 +236,7 @@ static void rsvd_carve(WsCarve &w, int64_t m, int64_t n, int64_t l, size_t scrat
   *scr = w.take<char>(scratch);
 }
 
-static int rsvd_gemm_prec(int prec) { return prec == RMC_BF16 ? RMC_TF32 : prec; }  // products read FP32 A
+static int rsvd_gemm_prec(int prec) { return prec; }
 
 size_t rmc_rsvd_plan_bytes(rmc_ctx *ctx, int64_t m, int64_t n, int64_t l, int prec) {
   float *Om, *Y, *Z, *B, *Ub, *sg, *Vb;
@@ -253,7 +253,7 @@ int rmc_rsvd(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, in
   const int64_t l = int64_t(k) + p;
   if (k < 1 || p < 0 || q < 0 || m < 1 || n < 1 || bad_ld(lda, n) || l > m || l > n || l > 256) return RMC_EINVAL;
   if (bad_ld(ldu, k) || bad_ld(ldv, k)) return RMC_EINVAL;
-  if (prec != RMC_FP32 && prec != RMC_TF32 && prec != RMC_BF16) return RMC_EINVAL;
+  if (!rmc_prec_ok(prec)) return RMC_EINVAL;
   const int gp = rsvd_gemm_prec(prec);
 
   float *Om, *Y, *Z, *B, *Ub, *sg, *Vb;

@@ -4,7 +4,7 @@
 // rmc.h).  The reduction runs over the m rows of A, so the work is split over row ranges (split-K) and the
 // partial products are summed in a fixed order afterwards.
 //   RMC_FP32: CUDA-core FMAs (the plain form), this file.
-//   RMC_TF32 / RMC_BF16: tcgen05 tensor-core kernel (tc_gemm.cu).
+//   RMC_TF32: tcgen05 tensor-core kernel (tc_gemm.cu).
 #include "rmc_internal.cuh"
 #include "philox.cuh"
 

@@ -2,43 +2,32 @@
 //
 // The scratch that the count-sketch path normally takes from a context's workspace (row hashes, the
 // bucket-by-chunk counters, the row permutation) lives here in one file-scope device array.  Host code
-// cannot use the array's name as a device address, so its address is looked up once per device with
-// cudaGetSymbolAddress and cached.  All calls share the array: overlapping calls race on it.
-#include <mutex>
-
+// cannot use the array's name as a device address, so every call looks the address up with
+// cudaGetSymbolAddress on the current device (a host-side query that enqueues nothing), which stays correct
+// after the device or this module has been torn down and reloaded.  All calls share the array: overlapping
+// calls race on it.
 #include "rmc_internal.cuh"
 
 namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[RMC_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
-int g_num_sms[kMaxDevices] = {};
-
-// First call on a device (that device current): find the array's device address and the SM count.
+// The array's device address and the SM count of the current device.
 int noalloc_setup(int device, void **scratch, int *num_sms) {
-  if (device < 0 || device >= kMaxDevices) return RMC_EINVAL;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[device]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      (void)cudaGetLastError();
-      return RMC_ECUDA;
-    }
-    int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    if (e != cudaSuccess || sms < 1) {
-      (void)cudaGetLastError();
-      return RMC_ECUDA;
-    }
-    g_num_sms[device] = sms;
-    g_scratch_ptr[device] = p;
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    (void)cudaGetLastError();
+    return RMC_ECUDA;
   }
-  *scratch = g_scratch_ptr[device];
-  *num_sms = g_num_sms[device];
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess || sms < 1) {
+    (void)cudaGetLastError();
+    return RMC_ECUDA;
+  }
+  *scratch = p;
+  *num_sms = sms;
   return RMC_OK;
 }
 

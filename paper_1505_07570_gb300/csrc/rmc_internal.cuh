@@ -48,6 +48,9 @@ struct RmcProf {
   ~RmcProf();
 };
 
+// Operand precisions that have a built path (RMC_BF16 is reserved in the header and rejected).
+static inline bool rmc_prec_ok(int prec) { return prec == RMC_FP32 || prec == RMC_TF32; }
+
 #define RMC_TRY_CUDA(expr)                                   \
   do {                                                       \
     cudaError_t e_ = (expr);                                 \

@@ -49,7 +49,7 @@ struct Done {
 bool valid_single(const rmc_serve_request &q) {
   const rmc_request &r = q.req;
   if (!r.A || r.m < 1 || r.n < 1 || r.lda < r.n || r.m > (int64_t(1) << 31)) return false;
-  if (q.prec != RMC_FP32 && q.prec != RMC_TF32 && q.prec != RMC_BF16) return false;
+  if (!rmc_prec_ok(q.prec)) return false;
   if (r.kind == RMC_REQ_LSR) {
     if (q.sketch != RMC_GAUSSIAN && q.sketch != RMC_SRHT && q.sketch != RMC_COUNTSKETCH) return false;
     if (q.sketch == RMC_SRHT) {

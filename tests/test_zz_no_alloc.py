@@ -24,7 +24,8 @@ def relfro(a, b):
 
 def test_noalloc_matches_context_path_two_calls_in_a_row():
     import paper_1505_07570_gb300 as rmc
-    # Two different problems back to back: the second call must not see the first call's scratch.
+    # Two different problems back to back: the second call must not see the first call's scratch.  Both
+    # paths run the same deterministic kernels in the same order, so the sketches are bit-identical.
     cases = [(200000, 96, 2048, 31), (50000, 33, 500, 7)]
     for m, n, s, seed in cases:
         A = torch.from_numpy(workloads.gaussian(m, n, seed=m)).cuda()
@@ -34,7 +35,33 @@ def test_noalloc_matches_context_path_two_calls_in_a_row():
         torch.cuda.synchronize()
         rmc.rmc_sync()
         assert got.data_ptr() == out.data_ptr()
-        assert relfro(got.cpu().numpy(), ref.cpu().numpy()) < 1e-5
+        assert torch.equal(got, ref)
+
+
+def test_noalloc_padded_strides_on_a_side_stream_match_the_oracle():
+    """lda > n and ldc > n, enqueued on a stream of its own, against the oracle's count sketch."""
+    import paper_1505_07570_gb300 as rmc
+    from oracle import sketch
+    m, n, s, seed = 3000, 21, 64, 5
+    A = workloads.gaussian(m, n, seed=9)
+    Ad = torch.zeros(m, n + 3, device="cuda")
+    Ad[:, :n] = torch.from_numpy(A).cuda()
+    Cd = torch.full((s, n + 5), float("nan"), device="cuda")
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        rmc.rmc_countsketch_noalloc(Ad[:, :n], s, seed, out=Cd[:, :n])
+    side.synchronize()
+    got = Cd.cpu().numpy()
+    assert np.all(np.isnan(got[:, n:]))            # the padding of C is untouched
+    assert relfro(got[:, :n], sketch.countsketch(A, s, seed)) < 1e-6
+
+
+def test_noalloc_rejects_an_output_of_the_wrong_size():
+    import paper_1505_07570_gb300 as rmc
+    A = torch.zeros(1000, 8, device="cuda")
+    with pytest.raises(ValueError):
+        rmc.rmc_countsketch_noalloc(A, 64, 1, out=torch.empty(63, 8, device="cuda"))
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
