@@ -367,6 +367,9 @@ def run_ours(args, world, rank, local):
             isolated[name] = roofline_of(name, {"launches": cnt, "ms_total": ms})
     rmc.rmc_profile_end()
 
+    precise_info = None
+    if world == 1 and not args.no_rsvd:
+        precise_info = precise_measure(torch, rmc, A, b)
     rsvd_info = None
     if world == 1 and not args.no_rsvd:
         del A_h, b_h
@@ -393,7 +396,7 @@ def run_ours(args, world, rank, local):
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernels, "kernels_isolated": isolated,
-        "rsvd": rsvd_info, "batch": batch_info, "serve": serve_info,
+        "lsr_precise": precise_info, "rsvd": rsvd_info, "batch": batch_info, "serve": serve_info,
     }
     print(json.dumps(line))
     if world > 1:
@@ -417,12 +420,19 @@ def run_probe(kind):
     A, b, _ = workloads.tall_lsr_torch(1 << 18, N_COLS, seed=SEED)
     if kind == "rsvd":
         A = workloads.factor_rank_torch(16384, 4096, 512, seed=SEED)
+    if kind == "rsvd_full":
+        del A, b
+        A = workloads.factor_rank_torch(65536, 16384, 2048, seed=SEED)
 
     def once():
         if kind == "lsr":
             return rmc.rmc_lsr_sketch(A, b, 1024, "countsketch", SEED)
+        if kind == "lsr_precise":
+            return rmc.rmc_lsr_precise(A, b, 1024, "countsketch", SEED, max_iters=4, tol=0.0)
         if kind == "rsvd":
             return rmc.rmc_rsvd(A, 100, 20, 1, SEED, prec="tf32")[1]
+        if kind == "rsvd_full":
+            return rmc.rmc_rsvd(A, 100, 20, 0, SEED, prec=GAUSS_PREC)[1]
         prec = GAUSS_PREC if kind == "gaussian" else "fp32"
         return rmc.rmc_sketch(A, 1024, kind, SEED, prec=prec)
 
@@ -437,6 +447,64 @@ def run_probe(kind):
     rmc.rmc_sync()
     print(json.dumps({"probe": kind, "ms_per_call": e0.elapsed_time(e1) / 2, "checksum": float(out.double().sum())}))
     return 0
+
+
+def precise_measure(torch, rmc, A, b, s=4096):
+    """Machine-precision least squares (Algorithm 4.1) on the tall regression workload, every kind at s = 4096:
+    call time, steps taken, and the residual + gradient pass over A as a roofline entry (algorithmic bytes
+    per pass: A and b read once).  The error is the normal-equation residual ||A^T (b - A x)|| / (||A|| ||b||)
+    evaluated in FP64 on the device, zero at the exact solution whatever the size."""
+    m, n = A.shape
+    pk = peaks()
+    out = {"workload": "tall-lsr %dx%d, s=%d, tol 1e-15, at most 60 steps" % (m, n, s), "calls": {}}
+    A64 = A.double()
+    b64 = b.double()
+    anorm = float(torch.linalg.matrix_norm(A64, ord="fro"))
+    bnorm = float(torch.linalg.vector_norm(b64))
+    for kind in ("countsketch", "srht", "gaussian"):
+        prec = GAUSS_PREC if kind == "gaussian" else "fp32"
+        rmc.rmc_lsr_precise(A, b, s, kind, SEED, prec=prec, max_iters=60)
+        rmc.rmc_sync()
+        rmc.rmc_profile_begin()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x, it = rmc.rmc_lsr_precise(A, b, s, kind, SEED, prec=prec, max_iters=60, want_iters=True)
+        e1.record()
+        rmc.rmc_sync()
+        npass, pass_ms = rmc.rmc_profile_read(rmc.K_LSR_PASS)
+        rmc.rmc_profile_end()
+        steps = int(it.item())
+        # launches after convergence return at once, so the pass time is spread over the steps that ran
+        per_pass_bytes = 4.0 * (m * n + m)
+        g = A64.T @ (b64 - A64 @ x)
+        out["calls"][kind] = {
+            "ms": e0.elapsed_time(e1), "steps": steps, "pass_launches": npass, "pass_ms_total": pass_ms,
+            "pass_ms_per_step": pass_ms / max(1, steps),
+            "pass_gbs": per_pass_bytes * steps / (pass_ms / 1e3) / 1e9 if steps else None,
+            "pass_frac_hbm_of_measured": (per_pass_bytes * steps / (pass_ms / 1e3) / 1e9 / pk["hbm_gbs"]
+                                          if steps else None),
+            "normal_eq_residual": float(torch.linalg.vector_norm(g)) / (anorm * bnorm)}
+    del A64, b64
+    torch.cuda.empty_cache()
+    return out
+
+
+def lanczos_measure(torch, rmc, A, k=100, s=120, q=2):
+    """Block Lanczos (Algorithm 5.1) on the large randomized-SVD workload: block size s, q blocks (2q passes)."""
+    m, n = A.shape
+    out = {"workload": "block lanczos %dx%d k=%d s=%d q=%d" % (m, n, k, s, q), "calls": {}}
+    for prec in ("tf32", "fp32"):
+        rmc.rmc_block_lanczos(A, k, s, q, SEED, prec=prec)
+        rmc.rmc_sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, sigma, _ = rmc.rmc_block_lanczos(A, k, s, q, SEED, prec=prec)
+        e1.record()
+        rmc.rmc_sync()
+        ms = e0.elapsed_time(e1)
+        out["calls"][prec] = {"ms": ms, "passes": 2 * q, "hbm_gbs": 2 * q * 4.0 * m * n / ms / 1e6,
+                              "sigma1": float(sigma[0]), "sigma100": float(sigma[-1])}
+    return out
 
 
 def rsvd_measure(torch, rmc):
@@ -461,7 +529,11 @@ def rsvd_measure(torch, rmc):
             ms = e0.elapsed_time(e1) / reps
             flops = (2 * q + 2) * 2.0 * m * n * (k + p)
             out["calls"]["%s_q%d" % (prec, q)] = {"ms": ms, "product_tflops": flops / ms / 1e9,
+                                                  "hbm_gbs": (2 * q + 2) * 4.0 * m * n / ms / 1e6,
+                                                  "frac_hbm_of_measured": (2 * q + 2) * 4.0 * m * n / ms / 1e6
+                                                  / peaks()["hbm_gbs"],
                                                   "sigma1": float(sigma[0]), "sigma100": float(sigma[-1])}
+    out["block_lanczos"] = lanczos_measure(torch, rmc, A)
     del A
     torch.cuda.empty_cache()
     return out
@@ -608,7 +680,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--probe", choices=["countsketch", "srht", "gaussian", "lsr", "rsvd", "batch", "peaks"], default=None,
+    ap.add_argument("--probe", choices=["countsketch", "srht", "gaussian", "lsr", "lsr_precise", "rsvd", "rsvd_full",
+                                        "batch", "peaks"], default=None,
                     help="run one small case of one kernel family (for profiler captures) and exit")
     ap.add_argument("--no-rsvd", action="store_true", help="skip the large randomized-SVD measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-problems measurement")

@@ -130,6 +130,32 @@ int rmc_lsr_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t l
 int rmc_rsvd(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, int k, int p, int q,
              uint64_t seed, int prec, float *U, int64_t ldu, float *sigma, float *V, int64_t ldv);
 
+/* ------------------------------------------------------------------------------- beyond the three calls */
+
+/* Machine-precision least squares by sketch preconditioning (Algorithm 4.1, Sec. 4.3):
+ *   Y = S^T A and S^T b from one sketch of [A, b] (kind, seed, prec as for rmc_lsr_sketch);
+ *   Y = Q_Y R_Y (CholeskyQR2, FP64 Gram);  T = R_Y^-1 (FP64);  z = Q_Y^T S^T b;
+ *   up to max_iters times:  r = b - A (T z);  z += theta T^T (A^T r);   x = T z (FP64, n entries).
+ * A T is never formed: each step is ONE pass over A that forms r row by row with a compensated (Dot2) dot
+ * product and accumulates A^T r from the same rows.  theta <= 0 selects 2 / ((1 - e)^-2 + (1 + e)^-2) with
+ * e = min(0.9, sqrt(n / s)), the best fixed step for the singular values of A T that a Gaussian sketch of size s
+ * gives.  The iteration stops early once a step changes z by at most tol * max|z| (max norms); *iters (device
+ * int, optional: NULL) receives the number of steps taken.  Requires n <= s, n <= 256, n <= m.
+ * Errors: RMC_EINVAL, RMC_ENOMEM, RMC_ECUDA; RMC_ENUMERIC at rmc_sync when S^T A is rank deficient. */
+int rmc_lsr_precise(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b, int64_t s,
+                    int kind, uint64_t seed, int prec, double theta, int max_iters, double tol, double *x,
+                    int *iters);
+
+/* k-SVD by block Lanczos (Algorithm 5.1 and the listing of Sec. 5.1): C = A Omega (Omega n x s, the Gaussian
+ * stream of rmc_rsvd), K = [C, (A A^T) C, ..., (A A^T)^(q-1) C] (m x s q), Q = orth(K), B = Q^T A,
+ * B = U_B diag(sigma) V_B^T; U = Q U_B[:, :k] (m x k, ldu), sigma[k] descending, V = V_B[:, :k] (n x k, ldv),
+ * signed as rmc_rsvd signs them.  Each Krylov block is orthonormalised and projected off the earlier blocks
+ * as it is formed (same span, stable basis).  2q passes over A.  prec: RMC_FP32 or RMC_TF32 for the products
+ * with A.  Requires 1 <= k <= s q, s q <= min(m, n), s q <= 256, q >= 1.  With q = 1 the result is rmc_rsvd's
+ * with p = s - k and no power iteration.  Errors as rmc_rsvd. */
+int rmc_block_lanczos(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, int k, int s, int q,
+                      uint64_t seed, int prec, float *U, int64_t ldu, float *sigma, float *V, int64_t ldv);
+
 /* ------------------------------------------------- steps of the path, exposed for step-level checks */
 
 /* Philox4x32-10 words of one stream: out[4*t + w] = word w of block (first + t), t < count (device, u32). */
@@ -248,7 +274,8 @@ int rmc_server_drain(rmc_server *srv);
 #define RMC_K_GRAM         6   /* FP64 Gram matrix of CholeskyQR2 / the least-squares solve          */
 #define RMC_K_SMALL        7   /* Cholesky, triangular inverse, Jacobi SVD (single-block kernels)    */
 #define RMC_K_BATCH        8   /* persistent batch kernel of rmc_batch_run                           */
-#define RMC_K_NTAGS        9
+#define RMC_K_LSR_PASS     9   /* residual + gradient pass over A of rmc_lsr_precise                 */
+#define RMC_K_NTAGS       10
 
 /* While profiling is on, the kernels above are bracketed by CUDA events recorded on the context's stream.
  * rmc_profile_begin clears the records; rmc_profile_read waits for the stream and returns, for one tag, the

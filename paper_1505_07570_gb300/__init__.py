@@ -54,10 +54,14 @@ _SIGS.update({
                           ctypes.POINTER(_int)],
     "rmc_launch_counter": [ctypes.POINTER(_u64)],
     "rmc_countsketch_noalloc": [_p, _p, _i64, _i64, _i64, _i64, _u64, _p, _i64],
+    "rmc_lsr_precise": [_p, _p, _i64, _i64, _i64, _p, _i64, _int, _u64, _int, ctypes.c_double, _int,
+                        ctypes.c_double, _p, _p],
+    "rmc_block_lanczos": [_p, _p, _i64, _i64, _i64, _int, _int, _int, _u64, _int, _p, _i64, _p, _p, _i64],
 })
 RMC_ESCRATCH = 8
 RMC_NOALLOC_SCRATCH_BYTES = 32 << 20
-K_COUNTSKETCH, K_SRHT, K_SRHT_REDUCE, K_GAUSSIAN, K_MATMUL_AN, K_MATMUL_AT, K_GRAM, K_SMALL, K_BATCH = range(9)
+(K_COUNTSKETCH, K_SRHT, K_SRHT_REDUCE, K_GAUSSIAN, K_MATMUL_AN, K_MATMUL_AT, K_GRAM, K_SMALL, K_BATCH,
+ K_LSR_PASS) = range(10)
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
     _f.argtypes = _args
@@ -217,6 +221,38 @@ def rmc_rsvd(A, k, p, q, seed, prec="fp32"):
     V = torch.empty(n, k, device=A.device, dtype=torch.float32)
     _check(lib.rmc_rsvd(context().bind(), _ptr(A), m, n, A.stride(0), k, p, q, seed, _prec(prec), _ptr(U),
                         U.stride(0), _ptr(sigma), _ptr(V), V.stride(0)), "rmc_rsvd")
+    return U, sigma, V
+
+
+def rmc_lsr_precise(A, b, s, kind, seed, prec="fp32", theta=0.0, max_iters=30, tol=1e-15, out=None,
+                    want_iters=False):
+    """Machine-precision least squares (Algorithm 4.1): x (FP64, n entries); with want_iters also the number
+    of preconditioned steps taken (a device int tensor)."""
+    import torch
+    _mat(A, "A")
+    m, n = A.shape
+    if not (b.is_cuda and b.dtype == torch.float32 and b.is_contiguous() and b.numel() == m
+            and b.device == A.device):
+        raise ValueError("b must be a contiguous CUDA float32 vector of length m on the device of A")
+    x = (_out(out, (n,), torch.float64, A, "out") if out is not None
+         else torch.empty(n, device=A.device, dtype=torch.float64))
+    it = torch.zeros(1, device=A.device, dtype=torch.int32) if want_iters else None
+    _check(lib.rmc_lsr_precise(context().bind(), _ptr(A), m, n, A.stride(0), _ptr(b), s, _kind(kind), seed,
+                               _prec(prec), float(theta), int(max_iters), float(tol), _ptr(x),
+                               _ptr(it) if want_iters else None), "rmc_lsr_precise")
+    return (x, it) if want_iters else x
+
+
+def rmc_block_lanczos(A, k, s, q, seed, prec="fp32"):
+    """U (m x k), sigma (k), V (n x k) of the block Lanczos k-SVD (Algorithm 5.1), block size s, q blocks."""
+    import torch
+    _mat(A, "A")
+    m, n = A.shape
+    U = torch.empty(m, k, device=A.device, dtype=torch.float32)
+    sigma = torch.empty(k, device=A.device, dtype=torch.float32)
+    V = torch.empty(n, k, device=A.device, dtype=torch.float32)
+    _check(lib.rmc_block_lanczos(context().bind(), _ptr(A), m, n, A.stride(0), k, s, q, seed, _prec(prec),
+                                 _ptr(U), U.stride(0), _ptr(sigma), _ptr(V), V.stride(0)), "rmc_block_lanczos")
     return U, sigma, V
 
 

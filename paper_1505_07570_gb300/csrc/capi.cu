@@ -131,7 +131,7 @@ int rmc_workspace_bytes(const rmc_ctx *ctx, size_t *bytes) {
 
 // ------------------------------------------------------------------------------------------------ sketch
 
-static int check_sketch_args(const float *A, int64_t m, int64_t n, int64_t lda, int64_t s, int kind, int prec) {
+int rmc_check_sketch_args(const float *A, int64_t m, int64_t n, int64_t lda, int64_t s, int kind, int prec) {
   if (!A || m < 1 || n < 1 || bad_ld(lda, n) || s < 1) return RMC_EINVAL;
   if (kind != RMC_GAUSSIAN && kind != RMC_SRHT && kind != RMC_COUNTSKETCH) return RMC_EINVAL;
   if (!rmc_prec_ok(prec)) return RMC_EINVAL;
@@ -140,7 +140,7 @@ static int check_sketch_args(const float *A, int64_t m, int64_t n, int64_t lda, 
   return RMC_OK;
 }
 
-static size_t sketch_ws(rmc_ctx *ctx, int64_t m, int64_t ntot, int64_t s, int kind, int prec) {
+size_t rmc_sketch_plan_bytes(rmc_ctx *ctx, int64_t m, int64_t ntot, int64_t s, int kind, int prec) {
   switch (kind) {
     case RMC_GAUSSIAN: return rmc_gauss_ws(m, ntot, s, prec, ctx->num_sms);
     case RMC_SRHT: return rmc_srht_ws(m, ntot, s);
@@ -149,7 +149,7 @@ static size_t sketch_ws(rmc_ctx *ctx, int64_t m, int64_t ntot, int64_t s, int ki
 }
 
 // Sketch A (and b, when given, as one more column of the same operator) into C (and Cb).
-static int run_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b, int64_t s,
+int rmc_run_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b, int64_t s,
                       int kind, uint64_t seed, int prec, float *C, int64_t ldc, float *Cb, void *ws) {
   switch (kind) {
     case RMC_GAUSSIAN:
@@ -164,15 +164,15 @@ static int run_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_
 int rmc_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, int64_t s, int kind, uint64_t seed,
                int prec, float *C, int64_t ldc) {
   if (!ctx || !C || bad_ld(ldc, n)) return RMC_EINVAL;
-  RMC_TRY(check_sketch_args(A, m, n, lda, s, kind, prec));
-  RMC_TRY(rmc_ws_reserve(ctx, sketch_ws(ctx, m, n, s, kind, prec)));
-  return run_sketch(ctx, A, m, n, lda, nullptr, s, kind, seed, prec, C, ldc, nullptr, ctx->ws);
+  RMC_TRY(rmc_check_sketch_args(A, m, n, lda, s, kind, prec));
+  RMC_TRY(rmc_ws_reserve(ctx, rmc_sketch_plan_bytes(ctx, m, n, s, kind, prec)));
+  return rmc_run_sketch(ctx, A, m, n, lda, nullptr, s, kind, seed, prec, C, ldc, nullptr, ctx->ws);
 }
 
 // Workspace plan of rmc_lsr_sketch: [S^T A, S^T b] (s x (n+1)), S^T b, then the larger of the sketch's and
 // the solve's scratch.
 static size_t lsr_rest_bytes(rmc_ctx *ctx, int64_t m, int64_t n, int64_t s, int kind, int prec) {
-  size_t rest = sketch_ws(ctx, m, n + 1, s, kind, prec);
+  size_t rest = rmc_sketch_plan_bytes(ctx, m, n + 1, s, kind, prec);
   const size_t solve = rmc_lsr_solve_ws(s, n, ctx->num_sms);
   return solve > rest ? solve : rest;
 }
@@ -194,7 +194,7 @@ size_t rmc_lsr_plan_bytes(rmc_ctx *ctx, int64_t m, int64_t n, int64_t s, int kin
 int rmc_lsr_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b, int64_t s,
                    int kind, uint64_t seed, int prec, double *x) {
   if (!ctx || !b || !x) return RMC_EINVAL;
-  RMC_TRY(check_sketch_args(A, m, n, lda, s, kind, prec));
+  RMC_TRY(rmc_check_sketch_args(A, m, n, lda, s, kind, prec));
   if (s < n || n > 1024) return RMC_EINVAL;
   const size_t rest_bytes = lsr_rest_bytes(ctx, m, n, s, kind, prec);
   float *SAb, *Sb;
@@ -206,7 +206,7 @@ int rmc_lsr_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t l
   w.base = static_cast<char *>(ctx->ws);
   lsr_carve(w, n, s, rest_bytes, &SAb, &Sb, &rest);
   // [S^T A, S^T b] is kept as one s x (n+1) matrix; S^T b is sketched into its own vector first.
-  RMC_TRY(run_sketch(ctx, A, m, n, lda, b, s, kind, seed, prec, SAb, n + 1, Sb, rest));
+  RMC_TRY(rmc_run_sketch(ctx, A, m, n, lda, b, s, kind, seed, prec, SAb, n + 1, Sb, rest));
   return rmc_launch_lsr_solve(ctx, SAb, s, n, n + 1, Sb, x, rest);
 }
 

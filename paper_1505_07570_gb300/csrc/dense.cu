@@ -382,10 +382,12 @@ __global__ void tri_mul_kernel(const double *A, const double *B, int l, double *
 }
 
 // ------------------------------------------------------------- row block times a small matrix (in place)
-// out[r, 0:lo] = in[r, 0:li] M (M li x lo, row stride ldm, FP32), 32 rows per block.  in and out may alias:
-// every block reads its rows into shared memory before writing them.
+// out[r, 0:lo] = in[r, 0:li] M (M li x lo, row stride ldm, FP32), 32 rows per block; with SUB,
+// out[r, 0:lo] -= in[r, 0:li] M.  in and out may alias: every block reads its rows into shared memory before
+// writing them.
 constexpr int RB = 32;
 
+template <bool SUB>
 __global__ void __launch_bounds__(256) rowblock_mul_kernel(const float *in, int64_t m, int li, int64_t ldi,
                                                            const float *__restrict__ M, int lo, int64_t ldm,
                                                            float *out, int64_t ldo) {
@@ -419,7 +421,10 @@ __global__ void __launch_bounds__(256) rowblock_mul_kernel(const float *in, int6
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int c = c0 + lane + 32 * t;
-        if (r < m && c < lo) out[r * ldo + c] = acc[i][t];
+        if (r < m && c < lo) {
+          if (SUB) out[r * ldo + c] -= acc[i][t];
+          else out[r * ldo + c] = acc[i][t];
+        }
       }
     }
   }
@@ -1035,17 +1040,27 @@ int launch_gram(rmc_ctx *ctx, const float *Y, int64_t m, int l, int64_t ldy, dou
 }
 
 int launch_rowblock(cudaStream_t st, const float *in, int64_t m, int li, int64_t ldi, const float *M, int lo,
-                    int64_t ldm, float *out, int64_t ldo) {
+                    int64_t ldm, float *out, int64_t ldo, bool subtract = false) {
   const size_t smem = sizeof(float) * RB * li;
-  if (smem > 48 * 1024)
-    RMC_TRY_CUDA(cudaFuncSetAttribute(rowblock_mul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  rowblock_mul_kernel<<<rmc_blocks(m, RB), 256, smem, st>>>(in, m, li, ldi, M, lo, ldm, out, ldo);
+  if (smem > 48 * 1024) {
+    RMC_TRY_CUDA(cudaFuncSetAttribute(rowblock_mul_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    RMC_TRY_CUDA(cudaFuncSetAttribute(rowblock_mul_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+  }
+  if (subtract) rowblock_mul_kernel<true><<<rmc_blocks(m, RB), 256, smem, st>>>(in, m, li, ldi, M, lo, ldm, out, ldo);
+  else rowblock_mul_kernel<false><<<rmc_blocks(m, RB), 256, smem, st>>>(in, m, li, ldi, M, lo, ldm, out, ldo);
   rmc_note_launch();
   RMC_LAUNCH_CHECK();
   return RMC_OK;
 }
 
 }  // namespace
+
+int rmc_launch_rowblock(cudaStream_t st, const float *in, int64_t m, int li, int64_t ldi, const float *M, int lo,
+                        int64_t ldm, float *out, int64_t ldo, bool subtract) {
+  return launch_rowblock(st, in, m, li, ldi, M, lo, ldm, out, ldo, subtract);
+}
 
 // ------------------------------------------------------------------------------------------- matmuls
 

@@ -139,11 +139,21 @@ size_t rmc_lsr_solve_ws(int64_t s, int64_t n, int num_sms);
 int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n, int64_t ldsa, const float *Sb,
                          double *x, void *ws);
 
+// out[r, 0:lo] = in[r, 0:li] M (or -= with subtract), rows independent; in and out may alias.
+int rmc_launch_rowblock(cudaStream_t st, const float *in, int64_t m, int li, int64_t ldi, const float *M, int lo,
+                        int64_t ldm, float *out, int64_t ldo, bool subtract = false);
 int rmc_launch_transpose(cudaStream_t st, const float *in, int64_t rows, int64_t cols, int64_t ldi, float *out,
                          int64_t ldo);
 int rmc_launch_rsvd_finish(rmc_ctx *ctx, const float *Q, int64_t m, int64_t l, const float *Ub, const float *sg,
                            const float *Vb, int64_t n, int k, float *U, int64_t ldu, float *sigma, float *V,
                            int64_t ldv, void *ws);
+
+// capi.cu: argument checks, workspace and launch of one sketch of A (and of b as one more column, into Cb)
+extern "C" int rmc_check_sketch_args(const float *A, int64_t m, int64_t n, int64_t lda, int64_t s, int kind,
+                                     int prec);
+extern "C" size_t rmc_sketch_plan_bytes(rmc_ctx *ctx, int64_t m, int64_t ntot, int64_t s, int kind, int prec);
+extern "C" int rmc_run_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b, int64_t s,
+                              int kind, uint64_t seed, int prec, float *C, int64_t ldc, float *Cb, void *ws);
 
 // capi.cu / batch.cu: device workspace of one call (what rmc_ws_reserve will be asked for)
 extern "C" size_t rmc_lsr_plan_bytes(rmc_ctx *ctx, int64_t m, int64_t n, int64_t s, int kind, int prec);
