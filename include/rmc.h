@@ -156,11 +156,49 @@ int rmc_lsr_precise(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t 
 int rmc_block_lanczos(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, int k, int s, int q,
                       uint64_t seed, int prec, float *U, int64_t ldu, float *sigma, float *V, int64_t ldv);
 
+/* Faster randomized k-SVD (Algorithm 5.3 and the listing of Sec. 5.3) on the GaussianProjection + CountSketch
+ * composite of Sec. 3.2.4, two passes over A:
+ *   C = A S (S an n x s count sketch over the columns, Philox instance 1);
+ *   L = P^T A, D = P^T C with P = P_cs P_gp (a count sketch of the rows to p_cs, instance 2, then a Gaussian
+ *   projection to p rows, instance 3; prec selects its FP32 or TF32 form);
+ *   D = Q_D R_D;  Q_D^T L = U_bar diag(sigma_bar) V_bar^T (top k);  C R_D^-1 U_bar diag(sigma_bar) =
+ *   U diag(sigma) V_hat^T;  V = V_bar V_hat.
+ * Outputs as rmc_rsvd (U m x k, sigma[k] descending, V n x k, the same sign rule).  Requires
+ * 1 <= k <= s <= 256, s <= p <= p_cs, s <= n, k <= m.  Errors as rmc_rsvd (RMC_ENUMERIC at rmc_sync when R_D
+ * is singular). */
+int rmc_rsvd_fast(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, int k, int s, int p_cs, int p,
+                  uint64_t seed, int prec, float *U, int64_t ldu, float *sigma, float *V, int64_t ldv);
+
+/* The Nystrom method on the Gaussian RBF kernel (Sec. 6.4 and its listing; kernel of Sec. 6.1):
+ *   S = the s landmarks, uniform without replacement in ascending order (the SRHT sample rule of stream 3,
+ *       drawn over [0, n) with instance 0);
+ *   C = K(:, S), K_ij = exp(-||x_i - x_j||^2 / (2 sigma^2)) (n x s; the n x n kernel matrix is never formed);
+ *   W = C(S, :) = U_W diag(lam) U_W^T (one-sided Jacobi directly on W);
+ *   L = C U_W[:, :k] diag(lam[:k])^-1/2 (n x k, ldl), so that K ~ L L^T.
+ * X: n points of dimension d (row-major FP32, ldx).  k = 0 selects ceil(0.8 s), the listing's choice.  Each
+ * column of U_W is signed so its largest-magnitude entry is positive.  lam (device, k floats) and landmarks
+ * (device, s int64) are optional outputs (NULL to skip).  Requires 1 <= s <= min(n, 256), 1 <= k <= s.
+ * RMC_ENUMERIC at rmc_sync when one of the k kept eigenvalues is not positive. */
+int rmc_nystrom(rmc_ctx *ctx, const float *X, int64_t n, int64_t d, int64_t ldx, double sigma, int64_t s, int k,
+                uint64_t seed, float *L, int64_t ldl, float *lam, int64_t *landmarks);
+
+/* The RBF kernel block K (n1 x n2, ldk): K_ij = exp(-||x_i - y_j||^2 / (2 sigma^2)) for the rows x_i of X and
+ * y_j of Y (dimension d), the rbf function of Sec. 6.1, with the squared distance summed coordinate by
+ * coordinate.  n2 <= 4,194,240. */
+int rmc_rbf(rmc_ctx *ctx, const float *X, int64_t n1, int64_t ldx, const float *Y, int64_t n2, int64_t ldy,
+            int64_t d, double sigma, float *K, int64_t ldk);
+
 /* ------------------------------------------------- steps of the path, exposed for step-level checks */
 
 /* Philox4x32-10 words of one stream: out[4*t + w] = word w of block (first + t), t < count (device, u32). */
 int rmc_philox(rmc_ctx *ctx, uint64_t seed, uint32_t stream, uint32_t instance, uint64_t first,
                int64_t count, uint32_t *out);
+
+/* Count sketch of the COLUMNS (the C = A S of Ch. 3 with Algorithm 3.1 over the columns): C (m x s, ldc) gets
+ * C[:, h(j)] += g(j) A[:, j] for every column j, with h, g the stream-2 hashes of the column indices under
+ * `instance`; each C[i, b] is summed in column order (deterministic).  1 <= s <= 256. */
+int rmc_countsketch_columns(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, int64_t s,
+                            uint64_t seed, uint32_t instance, float *C, int64_t ldc);
 
 /* The rows x cols standard-normal matrix of stream 0 (row-major, leading dimension ld), FP32. */
 int rmc_gaussian_matrix(rmc_ctx *ctx, uint64_t seed, uint32_t instance, int64_t rows, int64_t cols,
@@ -275,7 +313,8 @@ int rmc_server_drain(rmc_server *srv);
 #define RMC_K_SMALL        7   /* Cholesky, triangular inverse, Jacobi SVD (single-block kernels)    */
 #define RMC_K_BATCH        8   /* persistent batch kernel of rmc_batch_run                           */
 #define RMC_K_LSR_PASS     9   /* residual + gradient pass over A of rmc_lsr_precise                 */
-#define RMC_K_NTAGS       10
+#define RMC_K_RBF         10   /* RBF kernel block of rmc_nystrom / rmc_rbf                          */
+#define RMC_K_NTAGS       11
 
 /* While profiling is on, the kernels above are bracketed by CUDA events recorded on the context's stream.
  * rmc_profile_begin clears the records; rmc_profile_read waits for the stream and returns, for one tag, the

@@ -56,12 +56,16 @@ _SIGS.update({
     "rmc_countsketch_noalloc": [_p, _p, _i64, _i64, _i64, _i64, _u64, _p, _i64],
     "rmc_lsr_precise": [_p, _p, _i64, _i64, _i64, _p, _i64, _int, _u64, _int, ctypes.c_double, _int,
                         ctypes.c_double, _p, _p],
+    "rmc_rsvd_fast": [_p, _p, _i64, _i64, _i64, _int, _int, _int, _int, _u64, _int, _p, _i64, _p, _p, _i64],
+    "rmc_countsketch_columns": [_p, _p, _i64, _i64, _i64, _i64, _u64, _u32, _p, _i64],
+    "rmc_nystrom": [_p, _p, _i64, _i64, _i64, ctypes.c_double, _i64, _int, _u64, _p, _i64, _p, _p],
+    "rmc_rbf": [_p, _p, _i64, _i64, _p, _i64, _i64, _i64, ctypes.c_double, _p, _i64],
     "rmc_block_lanczos": [_p, _p, _i64, _i64, _i64, _int, _int, _int, _u64, _int, _p, _i64, _p, _p, _i64],
 })
 RMC_ESCRATCH = 8
 RMC_NOALLOC_SCRATCH_BYTES = 32 << 20
 (K_COUNTSKETCH, K_SRHT, K_SRHT_REDUCE, K_GAUSSIAN, K_MATMUL_AN, K_MATMUL_AT, K_GRAM, K_SMALL, K_BATCH,
- K_LSR_PASS) = range(10)
+ K_LSR_PASS, K_RBF) = range(11)
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
     _f.argtypes = _args
@@ -254,6 +258,57 @@ def rmc_block_lanczos(A, k, s, q, seed, prec="fp32"):
     _check(lib.rmc_block_lanczos(context().bind(), _ptr(A), m, n, A.stride(0), k, s, q, seed, _prec(prec),
                                  _ptr(U), U.stride(0), _ptr(sigma), _ptr(V), V.stride(0)), "rmc_block_lanczos")
     return U, sigma, V
+
+
+def rmc_rsvd_fast(A, k, s, p_cs, p, seed, prec="fp32"):
+    """U (m x k), sigma (k), V (n x k) of the faster randomized k-SVD (Algorithm 5.3)."""
+    import torch
+    _mat(A, "A")
+    m, n = A.shape
+    U = torch.empty(m, k, device=A.device, dtype=torch.float32)
+    sigma = torch.empty(k, device=A.device, dtype=torch.float32)
+    V = torch.empty(n, k, device=A.device, dtype=torch.float32)
+    _check(lib.rmc_rsvd_fast(context().bind(), _ptr(A), m, n, A.stride(0), k, s, p_cs, p, seed, _prec(prec),
+                             _ptr(U), U.stride(0), _ptr(sigma), _ptr(V), V.stride(0)), "rmc_rsvd_fast")
+    return U, sigma, V
+
+
+def rmc_countsketch_columns(A, s, seed, instance=0):
+    """C = A S with S an n x s count sketch over the columns (m x s)."""
+    import torch
+    _mat(A, "A")
+    m, n = A.shape
+    C = torch.empty(m, s, device=A.device, dtype=torch.float32)
+    _check(lib.rmc_countsketch_columns(context().bind(), _ptr(A), m, n, A.stride(0), s, seed, instance, _ptr(C),
+                                       C.stride(0)), "rmc_countsketch_columns")
+    return C
+
+
+def rmc_nystrom(X, sigma, s, seed, k=0):
+    """L (n x k), the eigenvalues lam (k) of the landmark block and the landmark indices (s) of the Nystrom
+    method (Sec. 6.4) on the RBF kernel of width sigma; k = 0 takes ceil(0.8 s)."""
+    import math
+    import torch
+    _mat(X, "X")
+    n, d = X.shape
+    kk = k if k else int(math.ceil(0.8 * s))
+    L = torch.empty(n, kk, device=X.device, dtype=torch.float32)
+    lam = torch.empty(kk, device=X.device, dtype=torch.float32)
+    idx = torch.empty(s, device=X.device, dtype=torch.int64)
+    _check(lib.rmc_nystrom(context().bind(), _ptr(X), n, d, X.stride(0), float(sigma), s, kk, seed, _ptr(L),
+                           L.stride(0), _ptr(lam), _ptr(idx)), "rmc_nystrom")
+    return L, lam, idx
+
+
+def rmc_rbf(X, Y, sigma):
+    """K_ij = exp(-||x_i - y_j||^2 / (2 sigma^2)) (n1 x n2)."""
+    import torch
+    _mat(X, "X")
+    _mat(Y, "Y")
+    K = torch.empty(X.shape[0], Y.shape[0], device=X.device, dtype=torch.float32)
+    _check(lib.rmc_rbf(context().bind(), _ptr(X), X.shape[0], X.stride(0), _ptr(Y), Y.shape[0], Y.stride(0),
+                       X.shape[1], float(sigma), _ptr(K), K.stride(0)), "rmc_rbf")
+    return K
 
 
 def rmc_philox(seed, stream, instance, first, count):

@@ -1261,6 +1261,42 @@ int rmc_launch_svd_wide(rmc_ctx *ctx, const float *B, int64_t l_, int64_t n, int
   return launch_rowblock(st, Bt, n, l, l, M, l, l, Vb, ldv);                 // Vb = Q2 M
 }
 
+// SVD of a square l x l matrix by one-sided Jacobi on its columns, with no QR first (for symmetric PSD
+// matrices whose condition number is beyond a Cholesky-based QR, e.g. the landmark block of a kernel matrix):
+// W (row-major FP64) = Ml diag(sigma) Vr^T with Ml the left and Vr the right singular vectors (row-major FP32,
+// columns ordered by descending sigma).  FP64 rotations for l <= 32, FP32 above, as the small SVD of rmc_rsvd.
+size_t rmc_jacobi_square_ws(int64_t l) { return 2 * sizeof(double) * (size_t)l * l + 256; }
+
+int rmc_launch_jacobi_square(rmc_ctx *ctx, const double *Wrm, int l, float *Ml, float *sigma, float *Vr, void *ws) {
+  cudaStream_t st = ctx->stream;
+  double *W = static_cast<double *>(ws);
+  double *V = W + (size_t)l * l;
+  const size_t smem64 = 2 * sizeof(double) * (size_t)l * l, smem32 = 2 * sizeof(float) * (size_t)l * l;
+  RmcProf prof(ctx, RMC_K_SMALL);
+  rmc_note_launch(3);
+  if (jacobi_in_fp64(l)) {
+    const double tol = 8 * 2.220446049250313e-16 * sqrt((double)l);
+    to_colmajor_kernel<double><<<rmc_blocks(l * l, 256), 256, 0, st>>>(Wrm, l, W);
+    jacobi_smem_kernel<double><<<1, 1024, smem64, st>>>(W, V, l, tol, 60, ctx->d_status);
+    jacobi_finish_kernel<double><<<1, 256, sizeof(double) * l, st>>>(W, V, l, Vr, Ml, sigma);
+  } else {
+    const float tol = 4 * 1.1920929e-7f * sqrtf((float)l);
+    float *Wf = reinterpret_cast<float *>(W), *Vf = Wf + (size_t)l * l;
+    to_colmajor_kernel<float><<<rmc_blocks(l * l, 256), 256, 0, st>>>(Wrm, l, Wf);
+    if (smem32 <= 200 * 1024) {
+      if (smem32 > 48 * 1024)
+        RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_smem_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem32));
+      jacobi_smem_kernel<float><<<1, 1024, smem32, st>>>(Wf, Vf, l, tol, 60, ctx->d_status);
+    } else {
+      jacobi_kernel<float><<<1, 1024, 0, st>>>(Wf, Vf, l, tol, 60, ctx->d_status);
+    }
+    jacobi_finish_kernel<float><<<1, 256, sizeof(double) * l, st>>>(Wf, Vf, l, Vr, Ml, sigma);
+  }
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
 int rmc_launch_rsvd_finish(rmc_ctx *ctx, const float *Q, int64_t m, int64_t l, const float *Ub, const float *sg,
                            const float *Vb, int64_t n, int k, float *U, int64_t ldu, float *sigma, float *V,
                            int64_t ldv, void *ws) {

@@ -142,6 +142,8 @@ int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n, in
 // out[r, 0:lo] = in[r, 0:li] M (or -= with subtract), rows independent; in and out may alias.
 int rmc_launch_rowblock(cudaStream_t st, const float *in, int64_t m, int li, int64_t ldi, const float *M, int lo,
                         int64_t ldm, float *out, int64_t ldo, bool subtract = false);
+size_t rmc_jacobi_square_ws(int64_t l);
+int rmc_launch_jacobi_square(rmc_ctx *ctx, const double *Wrm, int l, float *Ml, float *sigma, float *Vr, void *ws);
 int rmc_launch_transpose(cudaStream_t st, const float *in, int64_t rows, int64_t cols, int64_t ldi, float *out,
                          int64_t ldo);
 int rmc_launch_rsvd_finish(rmc_ctx *ctx, const float *Q, int64_t m, int64_t l, const float *Ub, const float *sg,
@@ -161,6 +163,10 @@ extern "C" size_t rmc_rsvd_plan_bytes(rmc_ctx *ctx, int64_t m, int64_t n, int64_
 size_t rmc_batch_plan_bytes(const rmc_request *reqs, int nreq);
 // batch.cu: the limits of one batched problem (false when the problem must go to the single-problem path)
 bool rmc_batch_request_ok(const rmc_request &r);
+
+// nystrom.cu
+int rmc_launch_rbf(rmc_ctx *ctx, const float *X, int64_t n1, int64_t ldx, const float *Y, int64_t n2, int64_t ldy,
+                   int64_t d, double sigma, float *C, int64_t ldc);
 
 // tc_gemm.cu (tcgen05 tensor-core kernels)
 int rmc_tc_available(void);

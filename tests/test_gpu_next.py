@@ -131,3 +131,74 @@ def test_block_lanczos_converges_toward_lapack(R):
     _, s, _ = R.rmc_block_lanczos(dev(A), 10, 20, 6, seed=1)
     R.rmc_sync()
     np.testing.assert_allclose(s.cpu().numpy(), sv, rtol=1e-4)
+
+
+# ---------------------------------------------------------------------- Sec. 3.2.4 and Algorithm 5.3
+
+@pytest.mark.parametrize("m,n,s,pad", [(300, 2000, 64, 0), (1000, 1030, 200, 3), (17, 5, 3, 0), (2049, 4096, 256, 0)])
+def test_countsketch_columns_parity(R, m, n, s, pad):
+    from oracle import sketch
+    A = workloads.gaussian(m, n, seed=n)
+    Ad = torch.zeros(m, n + pad, device="cuda")
+    Ad[:, :n] = dev(A)
+    C = R.rmc_countsketch_columns(Ad[:, :n], s, seed=13, instance=1)
+    R.rmc_sync()
+    assert relfro(C.cpu().numpy(), sketch.countsketch_columns(A, s, 13, instance=1)) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+@pytest.mark.parametrize("m,n,k,s,p_cs,p", [(3000, 800, 10, 40, 600, 160), (4096, 2048, 20, 64, 1500, 300)])
+def test_rsvd_fast_parity(R, prec, m, n, k, s, p_cs, p):
+    A = workloads.factor_rank_numpy(m, n, 300, seed=m + k)
+    U, sg, V = R.rmc_rsvd_fast(dev(A), k, s, p_cs, p, seed=9, prec=prec)
+    R.rmc_sync()
+    Uo, so, Vo = rsvd.faster_rsvd(A, k, s, p_cs, p, 9)
+    tol = 1e-4 if prec == "fp32" else 3e-3
+    np.testing.assert_allclose(sg.cpu().numpy(), so, rtol=tol)
+    A64 = A.astype(np.float64)
+    err = np.linalg.norm(A64 - (U.cpu().numpy() * sg.cpu().numpy()) @ V.cpu().numpy().T)
+    erro = np.linalg.norm(A64 - (Uo * so) @ Vo.T)
+    assert abs(err - erro) <= 0.01 * erro
+    if prec == "fp32":
+        np.testing.assert_allclose(np.abs(np.sum(V.cpu().numpy() * Vo, axis=0)), 1.0, atol=1e-3)
+
+
+def test_rsvd_fast_recovers_an_exact_rank_matrix(R):
+    sig = np.linspace(5, 1, 8)
+    A = workloads.exact_rank(3000, 400, 8, seed=2, sigma=sig)
+    U, s, V = R.rmc_rsvd_fast(dev(A), 8, 16, 256, 64, seed=4)
+    R.rmc_sync()
+    np.testing.assert_allclose(s.cpu().numpy(), sig, rtol=1e-4)
+
+
+# -------------------------------------------------------------------------------------------- Sec. 6.4
+
+@pytest.mark.parametrize("n1,n2,d,sigma", [(300, 70, 5, 1.3), (1000, 256, 33, 4.0), (65, 1, 1, 0.5)])
+def test_rbf_parity(R, n1, n2, d, sigma):
+    from oracle import kernel
+    g = np.random.default_rng(n1)
+    X = g.standard_normal((n1, d)).astype(np.float32)
+    Y = g.standard_normal((n2, d)).astype(np.float32)
+    K = R.rmc_rbf(dev(X), dev(Y), sigma)
+    R.rmc_sync()
+    np.testing.assert_allclose(K.cpu().numpy(), kernel.rbf(X, Y, sigma), rtol=2e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("n,d,s,sigma", [(500, 8, 40, 2.0), (20000, 16, 128, 4.0), (3001, 3, 25, 1.0)])
+def test_nystrom_parity(R, n, d, s, sigma):
+    """L against the oracle's (each column's sign is a reproducibility rule only, so columns are compared up to
+    sign), the landmark eigenvalues, and L L^T against the oracle's C W_k^+ C^T on sampled entries."""
+    from oracle import kernel
+    X = np.random.default_rng(n).standard_normal((n, d)).astype(np.float32)
+    L, lam, idx = R.rmc_nystrom(dev(X), sigma, s, seed=21)
+    R.rmc_sync()
+    Lo, So, lamo, _ = kernel.nystrom(X, sigma, s, 21)
+    np.testing.assert_array_equal(idx.cpu().numpy(), So)
+    np.testing.assert_allclose(lam.cpu().numpy(), lamo, rtol=1e-4, atol=1e-6 * lamo[0])
+    Lg = L.cpu().numpy().astype(np.float64)
+    sgn = np.sign(np.sum(Lg * Lo, axis=0))
+    # the small eigenvalues of W carry the FP32 rounding of W divided by lam: compare relative to the column norm
+    err = np.linalg.norm(Lg * sgn - Lo, axis=0) / np.linalg.norm(Lo, axis=0)
+    assert np.all(err < 2e-3 * np.sqrt(lamo[0] / lamo)), err
+    rows = np.random.default_rng(1).choice(n, 50, replace=False)
+    np.testing.assert_allclose(Lg[rows] @ Lg[rows].T, Lo[rows] @ Lo[rows].T, atol=1e-3)
