@@ -420,7 +420,7 @@ def run_probe(kind):
     A, b, _ = workloads.tall_lsr_torch(1 << 18, N_COLS, seed=SEED)
     if kind == "rsvd":
         A = workloads.factor_rank_torch(16384, 4096, 512, seed=SEED)
-    if kind == "rsvd_full":
+    if kind in ("rsvd_full", "lanczos_full"):
         del A, b
         A = workloads.factor_rank_torch(65536, 16384, 2048, seed=SEED)
 
@@ -432,7 +432,9 @@ def run_probe(kind):
         if kind == "rsvd":
             return rmc.rmc_rsvd(A, 100, 20, 1, SEED, prec="tf32")[1]
         if kind == "rsvd_full":
-            return rmc.rmc_rsvd(A, 100, 20, 0, SEED, prec=GAUSS_PREC)[1]
+            return rmc.rmc_rsvd(A, 100, 20, int(os.environ.get("RMC_PROBE_Q", "0")), SEED, prec=GAUSS_PREC)[1]
+        if kind == "lanczos_full":
+            return rmc.rmc_block_lanczos(A, 100, 120, 2, SEED, prec=GAUSS_PREC)[1]
         prec = GAUSS_PREC if kind == "gaussian" else "fp32"
         return rmc.rmc_sketch(A, 1024, kind, SEED, prec=prec)
 
@@ -515,12 +517,13 @@ def rsvd_measure(torch, rmc):
     m, n, k, p = 65536, 16384, 100, 20
     A = workloads.factor_rank_torch(m, n, 2048, seed=SEED)
     out = {"workload": "rsvd 65536x16384 rank-2048 sigma_i=1/i, k=100 p=20", "calls": {}}
-    for prec in ["tf32", "fp32"]:
+    ref = {}
+    for prec in ["fp32", "tf32x3", "tf32"]:
         for q in [0, 1, 2]:
             rmc.rmc_rsvd(A, k, p, q, SEED, prec=prec)
             rmc.rmc_sync()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 3 if prec == "tf32" else 1
+            reps = 1 if prec == "fp32" else 3
             e0.record()
             for _ in range(reps):
                 _, sigma, _ = rmc.rmc_rsvd(A, k, p, q, SEED, prec=prec)
@@ -533,6 +536,12 @@ def rsvd_measure(torch, rmc):
                                                   "frac_hbm_of_measured": (2 * q + 2) * 4.0 * m * n / ms / 1e6
                                                   / peaks()["hbm_gbs"],
                                                   "sigma1": float(sigma[0]), "sigma100": float(sigma[-1])}
+            if prec == "fp32":
+                ref[q] = sigma.double()
+            else:
+                # largest relative difference of the k singular values from the FP32-product form's
+                out["calls"]["%s_q%d" % (prec, q)]["sigma_maxrel_vs_fp32"] = float(
+                    ((sigma.double() - ref[q]).abs() / ref[q]).max())
     out["block_lanczos"] = lanczos_measure(torch, rmc, A)
     del A
     torch.cuda.empty_cache()
@@ -680,7 +689,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--probe", choices=["countsketch", "srht", "gaussian", "lsr", "lsr_precise", "rsvd", "rsvd_full",
+    ap.add_argument("--probe", choices=["countsketch", "srht", "gaussian", "lsr", "lsr_precise", "rsvd", "rsvd_full", "lanczos_full",
                                         "batch", "peaks"], default=None,
                     help="run one small case of one kernel family (for profiler captures) and exit")
     ap.add_argument("--no-rsvd", action="store_true", help="skip the large randomized-SVD measurement")

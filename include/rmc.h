@@ -64,6 +64,10 @@ extern "C" {
 #define RMC_FP32  0   /* FP32 operands on the CUDA cores (the plain form)                                 */
 #define RMC_TF32  1   /* TF32 operands on the tensor cores (tcgen05.mma kind::tf32), FP32 accumulation    */
 #define RMC_BF16  2   /* reserved for BF16 operands (tcgen05.mma kind::f16): not built, rejected with RMC_EINVAL */
+#define RMC_TF32X3 3  /* 3xTF32 on the tensor cores: each FP32 operand split into a TF32 head and remainder,
+                         three kind::tf32 MMAs per step (head*head + head*rest + rest*head), FP32 accumulation:
+                         about 2^-21 relative error per product (FP32-level), for the products with A of
+                         rmc_rsvd, rmc_block_lanczos, rmc_matmul_an/at (not the Gaussian sketch: RMC_EINVAL) */
 
 typedef struct rmc_ctx rmc_ctx;
 
@@ -124,7 +128,8 @@ int rmc_lsr_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t l
  *   B = Q^T A (l x n); B = U_B diag(sigma) V_B^T (FP64 one-sided Jacobi on the R factor of B^T);
  *   U = Q U_B[:, :k] (m x k, ldu), sigma[k] descending, V = V_B[:, :k] (n x k, ldv).
  * Each column pair (u_i, v_i) is signed so the largest-magnitude entry of v_i is positive.
- * prec selects the operand precision of the products with A.  Requires 1 <= k, l <= min(m, n), l <= 256,
+ * prec selects the operand precision of the products with A (RMC_FP32, RMC_TF32 or RMC_TF32X3).
+ * Requires 1 <= k, l <= min(m, n), l <= 256,
  * q >= 0.  Errors: RMC_EINVAL, RMC_ENOMEM, RMC_ECUDA; RMC_ENUMERIC at rmc_sync (breakdown of CholeskyQR2
  * or no Jacobi convergence). */
 int rmc_rsvd(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, int k, int p, int q,
@@ -160,7 +165,8 @@ int rmc_block_lanczos(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_
  * composite of Sec. 3.2.4, two passes over A:
  *   C = A S (S an n x s count sketch over the columns, Philox instance 1);
  *   L = P^T A, D = P^T C with P = P_cs P_gp (a count sketch of the rows to p_cs, instance 2, then a Gaussian
- *   projection to p rows, instance 3; prec selects its FP32 or TF32 form);
+ *   projection to p rows, instance 3; prec RMC_TF32 runs it on the tensor cores, RMC_FP32 and
+ *   RMC_TF32X3 in FP32);
  *   D = Q_D R_D;  Q_D^T L = U_bar diag(sigma_bar) V_bar^T (top k);  C R_D^-1 U_bar diag(sigma_bar) =
  *   U diag(sigma) V_hat^T;  V = V_bar V_hat.
  * Outputs as rmc_rsvd (U m x k, sigma[k] descending, V n x k, the same sign rule).  Requires
@@ -228,7 +234,7 @@ int rmc_svd_wide(rmc_ctx *ctx, const float *B, int64_t l, int64_t n, int64_t ldb
  * and the C = A' * C; C = A * C power step of the Sec. 5.1 listing):
  *   rmc_matmul_an:  Y (m x l, ldy) = A (m x n) * X, with X n x l (ldx).
  *   rmc_matmul_at:  W (l x n, ldw) = X^T * A,       with X m x l (ldx).
- * prec: RMC_FP32 (CUDA cores) or RMC_TF32 (tensor cores); FP32 accumulation.  1 <= l <= 256. */
+ * prec: RMC_FP32 (CUDA cores), RMC_TF32 or RMC_TF32X3 (tensor cores); FP32 accumulation.  1 <= l <= 256. */
 int rmc_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X,
                   int64_t l, int64_t ldx, int prec, float *Y, int64_t ldy);
 int rmc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X,

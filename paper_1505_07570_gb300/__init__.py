@@ -15,10 +15,10 @@ from .build import LIB as _LIB_PATH
 
 RMC_OK, RMC_EINVAL, RMC_EALIGN, RMC_ENOMEM, RMC_ENUMERIC, RMC_ETIMEOUT, RMC_ECUDA, RMC_PENDING = range(8)
 RMC_GAUSSIAN, RMC_SRHT, RMC_COUNTSKETCH = 0, 1, 2
-RMC_FP32, RMC_TF32, RMC_BF16 = 0, 1, 2
+RMC_FP32, RMC_TF32, RMC_BF16, RMC_TF32X3 = 0, 1, 2, 3
 
 KIND = {"gaussian": RMC_GAUSSIAN, "srht": RMC_SRHT, "countsketch": RMC_COUNTSKETCH}
-PREC = {"fp32": RMC_FP32, "tf32": RMC_TF32, "bf16": RMC_BF16}
+PREC = {"fp32": RMC_FP32, "tf32": RMC_TF32, "bf16": RMC_BF16, "tf32x3": RMC_TF32X3}
 
 if not os.path.exists(_LIB_PATH):
     raise ImportError("librmc.so is not built (expected at %s); run __graft_entry__.build()" % _LIB_PATH)

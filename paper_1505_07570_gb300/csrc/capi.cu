@@ -135,6 +135,7 @@ int rmc_check_sketch_args(const float *A, int64_t m, int64_t n, int64_t lda, int
   if (!A || m < 1 || n < 1 || bad_ld(lda, n) || s < 1) return RMC_EINVAL;
   if (kind != RMC_GAUSSIAN && kind != RMC_SRHT && kind != RMC_COUNTSKETCH) return RMC_EINVAL;
   if (!rmc_prec_ok(prec)) return RMC_EINVAL;
+  if (kind == RMC_GAUSSIAN && prec == RMC_TF32X3) return RMC_EINVAL;   // no split form of the drawn sketch
   if (kind == RMC_SRHT && s > next_pow2(m)) return RMC_EINVAL;
   if (m > (int64_t(1) << 31) || s > (int64_t(1) << 31)) return RMC_EINVAL;
   return RMC_OK;
@@ -327,7 +328,7 @@ int rmc_svd_wide(rmc_ctx *ctx, const float *B, int64_t l, int64_t n, int64_t ldb
 int rmc_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
                   int64_t ldx, int prec, float *Y, int64_t ldy) {
   if (!ctx || !A || !X || !Y || m < 1 || n < 1 || l < 1 || l > 256 || bad_ld(lda, n) || bad_ld(ldx, l) ||
-      bad_ld(ldy, l) || (prec != RMC_FP32 && prec != RMC_TF32))
+      bad_ld(ldy, l) || !rmc_prec_ok(prec))
     return RMC_EINVAL;
   RMC_TRY(rmc_ws_reserve(ctx, rmc_matmul_ws(m, n, l, 0, prec, ctx->num_sms)));
   return rmc_launch_matmul_an(ctx, A, m, n, lda, X, l, ldx, prec, Y, ldy, ctx->ws);
@@ -336,7 +337,7 @@ int rmc_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t ld
 int rmc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
                   int64_t ldx, int prec, float *W, int64_t ldw) {
   if (!ctx || !A || !X || !W || m < 1 || n < 1 || l < 1 || l > 256 || bad_ld(lda, n) || bad_ld(ldx, l) ||
-      bad_ld(ldw, n) || (prec != RMC_FP32 && prec != RMC_TF32))
+      bad_ld(ldw, n) || !rmc_prec_ok(prec))
     return RMC_EINVAL;
   RMC_TRY(rmc_ws_reserve(ctx, rmc_matmul_ws(m, n, l, 1, prec, ctx->num_sms)));
   return rmc_launch_matmul_at(ctx, A, m, n, lda, X, l, ldx, prec, W, ldw, ctx->ws);

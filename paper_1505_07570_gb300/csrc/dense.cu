@@ -1074,10 +1074,10 @@ static int matmul_at_splits(int64_t m, int64_t n, int64_t l, int num_sms) {
 }
 
 int rmc_tc_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
-                     int64_t ldx, float *Y, int64_t ldy, void *ws);
+                     int64_t ldx, float *Y, int64_t ldy, bool x3, void *ws);
 int rmc_tc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
-                     int64_t ldx, float *W, int64_t ldw, void *ws);
-size_t rmc_tc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, int num_sms);
+                     int64_t ldx, float *W, int64_t ldw, bool x3, void *ws);
+size_t rmc_tc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, bool x3, int num_sms);
 
 size_t rmc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, int prec, int num_sms) {
   size_t simt = 0;
@@ -1085,8 +1085,8 @@ size_t rmc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, int prec, int n
     const int splits = matmul_at_splits(m, n, l, num_sms);
     simt = splits > 1 ? sizeof(float) * (size_t)splits * l * n : 0;
   }
-  if (prec != RMC_TF32) return simt;
-  const size_t tc = rmc_tc_matmul_ws(m, n, l, which, num_sms);
+  if (prec != RMC_TF32 && prec != RMC_TF32X3) return simt;
+  const size_t tc = rmc_tc_matmul_ws(m, n, l, which, prec == RMC_TF32X3, num_sms);
   return tc > simt ? tc : simt;
 }
 
@@ -1097,7 +1097,8 @@ static bool tma_rows_ok(const float *A, int64_t lda) {
 
 int rmc_launch_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
                          int64_t ldx, int prec, float *Y, int64_t ldy, void *ws) {
-  if (prec == RMC_TF32 && tma_rows_ok(A, lda)) return rmc_tc_matmul_an(ctx, A, m, n, lda, X, l, ldx, Y, ldy, ws);
+  if ((prec == RMC_TF32 || prec == RMC_TF32X3) && tma_rows_ok(A, lda))
+    return rmc_tc_matmul_an(ctx, A, m, n, lda, X, l, ldx, Y, ldy, prec == RMC_TF32X3, ws);
   dim3 grid((unsigned)((l + GT - 1) / GT), (unsigned)((m + GT - 1) / GT));
   {
     RmcProf prof(ctx, RMC_K_MATMUL_AN);
@@ -1110,7 +1111,8 @@ int rmc_launch_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int
 
 int rmc_launch_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
                          int64_t ldx, int prec, float *W, int64_t ldw, void *ws) {
-  if (prec == RMC_TF32 && tma_rows_ok(A, lda)) return rmc_tc_matmul_at(ctx, A, m, n, lda, X, l, ldx, W, ldw, ws);
+  if ((prec == RMC_TF32 || prec == RMC_TF32X3) && tma_rows_ok(A, lda))
+    return rmc_tc_matmul_at(ctx, A, m, n, lda, X, l, ldx, W, ldw, prec == RMC_TF32X3, ws);
   const int splits = matmul_at_splits(m, n, l, ctx->num_sms);
   int64_t rows = (m + splits - 1) / splits;
   rows = (rows + GK - 1) / GK * GK;

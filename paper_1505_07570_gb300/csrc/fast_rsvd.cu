@@ -205,6 +205,7 @@ FastBufs fast_carve(WsCarve &w, int64_t m, int64_t n, int s, int p_cs, int p, in
 }
 
 size_t fast_scratch(rmc_ctx *ctx, int64_t m, int64_t n, int s, int p_cs, int p, int k, int prec) {
+  if (prec == RMC_TF32X3) prec = RMC_FP32;
   const size_t c[] = {rmc_countsketch_ws(m, p_cs), rmc_gauss_ws(p_cs, n, p, prec, ctx->num_sms),
                       rmc_gauss_ws(p_cs, s, p, prec, ctx->num_sms), rmc_cholqr2_ws(p, s, ctx->num_sms),
                       rmc_matmul_ws(p, n, s, 1, RMC_FP32, ctx->num_sms), rmc_svd_wide_ws(s, n, ctx->num_sms),
@@ -293,8 +294,9 @@ extern "C" int rmc_rsvd_fast(rmc_ctx *ctx, const float *A, int64_t m, int64_t n,
   // pass 2: P_cs^T A and P_cs^T C (one row hash for both), then the Gaussian projection of each to p rows
   RMC_TRY(rmc_launch_countsketch(ctx, A, m, n, lda, nullptr, p_cs, seed, kInstPcs, f.PA, n, nullptr, f.scr));
   RMC_TRY(rmc_launch_countsketch(ctx, f.C, m, s, s, nullptr, p_cs, seed, kInstPcs, f.PC, s, nullptr, f.scr));
-  RMC_TRY(rmc_launch_gauss_sketch(ctx, f.PA, p_cs, n, n, nullptr, p, seed, kInstPgp, prec, f.L, n, nullptr, f.scr));
-  RMC_TRY(rmc_launch_gauss_sketch(ctx, f.PC, p_cs, s, s, nullptr, p, seed, kInstPgp, prec, f.D, s, nullptr, f.scr));
+  const int gp = prec == RMC_TF32X3 ? RMC_FP32 : prec;     // the drawn sketch has no split form
+  RMC_TRY(rmc_launch_gauss_sketch(ctx, f.PA, p_cs, n, n, nullptr, p, seed, kInstPgp, gp, f.L, n, nullptr, f.scr));
+  RMC_TRY(rmc_launch_gauss_sketch(ctx, f.PC, p_cs, s, s, nullptr, p, seed, kInstPgp, gp, f.D, s, nullptr, f.scr));
   // D = Q_D R_D;  Q_D^T L = Ub diag(sb) Vb^T
   RMC_TRY(rmc_launch_cholqr2(ctx, f.D, p, s, s, f.RD, f.scr, 2, true));
   RMC_TRY(rmc_launch_matmul_at(ctx, f.L, p, n, n, f.D, s, s, RMC_FP32, f.Mt, n, f.scr));

@@ -49,7 +49,7 @@ struct RmcProf {
 };
 
 // Operand precisions that have a built path (RMC_BF16 is reserved in the header and rejected).
-static inline bool rmc_prec_ok(int prec) { return prec == RMC_FP32 || prec == RMC_TF32; }
+static inline bool rmc_prec_ok(int prec) { return prec == RMC_FP32 || prec == RMC_TF32 || prec == RMC_TF32X3; }
 
 #define RMC_TRY_CUDA(expr)                                   \
   do {                                                       \

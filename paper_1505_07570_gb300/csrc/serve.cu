@@ -52,6 +52,7 @@ bool valid_single(const rmc_serve_request &q) {
   if (!rmc_prec_ok(q.prec)) return false;
   if (r.kind == RMC_REQ_LSR) {
     if (q.sketch != RMC_GAUSSIAN && q.sketch != RMC_SRHT && q.sketch != RMC_COUNTSKETCH) return false;
+    if (q.sketch == RMC_GAUSSIAN && q.prec == RMC_TF32X3) return false;
     if (q.sketch == RMC_SRHT) {
       int64_t N = 1;
       while (N < r.m) N <<= 1;
@@ -69,7 +70,8 @@ bool valid_single(const rmc_serve_request &q) {
 bool batchable(const rmc_serve_request &q) {
   if (!rmc_batch_request_ok(q.req)) return false;
   if (q.req.kind == RMC_REQ_LSR) return q.sketch == RMC_COUNTSKETCH;
-  return q.prec == RMC_FP32;  // the batched kernel computes its products in FP32
+  // the batched kernel computes its products at FP32 accuracy (3xTF32 on mma.sync)
+  return q.prec == RMC_FP32 || q.prec == RMC_TF32X3;
 }
 
 }  // namespace

@@ -448,34 +448,64 @@ namespace {
 // through TMA; one CTA owns 128 rows of Y and runs the whole reduction over the n columns of A.
 // W = X^T A (rmc_matmul_at): X^T tiles by TMA (K-major), A tiles staged by TMA and transposed on chip (as in
 // the Gaussian kernel); split-K over the rows of A with a fixed-order reduction.
+//
+// X3 (RMC_TF32X3): every FP32 operand v is split into a TF32 head h (v with its 13 low mantissa bits cleared,
+// exactly what the tensor core reads) and the remainder v - h (exact in FP32), and each k-step issues three
+// MMAs into the same accumulator: A_h X_h + A_h X_l + A_l X_h.  The dropped A_l X_l and the TF32 reading of the
+// remainders leave about 2^-21 relative error per product instead of TF32's 2^-11.  X's head and remainder are
+// split once in global memory; A's are split on chip (converter warps for Y = A X, the transposer warps for
+// W = X^T A, which write both parts of the transposed tile).
 
-constexpr int kAnStages = 4;
-constexpr int kAnThreads = 256;   // warp 0 TMA, warp 1 MMA, warps 4-7 epilogue
+// v with its 13 low mantissa bits cleared (the TF32 head), and the exact remainder.
+__device__ __forceinline__ float tf32_head(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
 
-template <int NPAD>
+__device__ __forceinline__ void split4(float4 v, float4 &h, float4 &l) {
+  h = make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
+  l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+}
+
+constexpr int kAnThreads = 256;   // warp 0 TMA, warp 1 MMA, warps 4-7 epilogue (X3: warps 2-7 also split A)
+constexpr int kAnConvWarps = 6;   // warps 2-7
+constexpr size_t kSmemCap = 227 * 1024;
+
+template <int NPAD, bool X3>
+struct AnCfg {
+  static constexpr int kA = 128 * 128;                 // 128 rows x 32 TF32
+  static constexpr int kX = NPAD * 128;                // NPAD rows x 32 TF32
+  static constexpr int kStage = (X3 ? 2 : 1) * (kA + kX);
+  static constexpr int kFit = (int)((kSmemCap - 2048) / kStage);
+  static constexpr int kStages = kFit > 4 ? 4 : kFit;
+  static constexpr size_t kSmem = 1024 + (size_t)kStages * kStage + 256;
+};
+
+template <int NPAD, bool X3>
 __global__ void __launch_bounds__(kAnThreads, 1) tc_an_kernel(const __grid_constant__ CUtensorMap tmap_a,
                                                               const __grid_constant__ CUtensorMap tmap_xt,
+                                                              const __grid_constant__ CUtensorMap tmap_xl,
                                                               int64_t m, int64_t n, int64_t l, float *Y,
                                                               int64_t ldy, int *status) {
-  constexpr int kABytesAn = 128 * 128;            // 128 rows x 32 TF32
-  constexpr int kXBytes = NPAD * 128;              // NPAD rows x 32 TF32
-  constexpr int kStage = kABytesAn + kXBytes;
+  using Cfg = AnCfg<NPAD, X3>;
+  constexpr int kS = Cfg::kStages;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~uintptr_t(1023));
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kAnStages * kStage);
-  uint64_t *empty = full + kAnStages;
-  uint64_t *done = empty + kAnStages;
+  // stage: A head | X^T head | (X3) A remainder | X^T remainder
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kS * Cfg::kStage);
+  uint64_t *conv = full + kS;
+  uint64_t *empty = conv + kS;
+  uint64_t *done = empty + kS;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t row0 = (int64_t)blockIdx.x * 128;
   const int num_it = (int)((n + kKStage - 1) / kKStage);
   constexpr uint32_t kCols = NPAD < 32 ? 32 : NPAD;
+  constexpr int kHalf = Cfg::kA + Cfg::kX;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kAnStages; ++i) {
+    for (int i = 0; i < kS; ++i) {
       tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&conv[i], kAnConvWarps);
       tc::mbar_init(&empty[i], 1);
     }
     tc::mbar_init(done, 1);
@@ -485,6 +515,7 @@ __global__ void __launch_bounds__(kAnThreads, 1) tc_an_kernel(const __grid_const
   if (warp == 0 && lane == 0) {
     tc::prefetch_tmap(&tmap_a);
     tc::prefetch_tmap(&tmap_xt);
+    if (X3) tc::prefetch_tmap(&tmap_xl);
   }
   if (warp == 1) tc::tmem_alloc(tmem_slot, kCols);
   tc::tc_fence_before();
@@ -496,63 +527,86 @@ __global__ void __launch_bounds__(kAnThreads, 1) tc_an_kernel(const __grid_const
     if (lane == 0) {
       int issued = 0;
       for (int it = 0; it < num_it; ++it) {
-        const int st = it % kAnStages;
-        if (*abort_flag || !tc::mbar_wait(&empty[st], ((it / kAnStages) & 1) ^ 1)) {
+        const int st = it % kS;
+        if (*abort_flag || !tc::mbar_wait(&empty[st], ((it / kS) & 1) ^ 1)) {
           *abort_flag = 1;
           rmc_report(status, RMC_ETIMEOUT);
           break;
         }
-        unsigned char *stage = smem + st * kStage;
-        tc::mbar_arrive_expect_tx(&full[st], kStage);
+        unsigned char *stage = smem + st * Cfg::kStage;
+        tc::mbar_arrive_expect_tx(&full[st], X3 ? Cfg::kA + 2 * Cfg::kX : Cfg::kA + Cfg::kX);
         tc::tma_load_2d(stage, &tmap_a, it * kKStage, (int32_t)row0, &full[st]);
-        tc::tma_load_2d(stage + kABytesAn, &tmap_xt, it * kKStage, 0, &full[st]);
+        tc::tma_load_2d(stage + Cfg::kA, &tmap_xt, it * kKStage, 0, &full[st]);
+        if (X3) tc::tma_load_2d(stage + kHalf + Cfg::kA, &tmap_xl, it * kKStage, 0, &full[st]);
         ++issued;
       }
-      for (int it = issued > kAnStages ? issued - kAnStages : 0; it < issued; ++it)
-        (void)tc::mbar_wait(&full[it % kAnStages], (it / kAnStages) & 1);
+      for (int it = issued > kS ? issued - kS : 0; it < issued; ++it)
+        (void)tc::mbar_wait(&full[it % kS], (it / kS) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = tc::instr_desc(2, 2, 0, 0, NPAD, 128);
       for (int it = 0; it < num_it; ++it) {
-        const int st = it % kAnStages;
-        if (*abort_flag || !tc::mbar_wait(&full[st], (it / kAnStages) & 1)) {
+        const int st = it % kS;
+        if (*abort_flag || !tc::mbar_wait(X3 ? &conv[st] : &full[st], (it / kS) & 1)) {
           *abort_flag = 1;
           rmc_report(status, RMC_ETIMEOUT);
           break;
         }
         tc::tc_fence_after();
-        const uint32_t a_addr = tc::smem_u32(smem + st * kStage);
-        const uint32_t x_addr = a_addr + kABytesAn;
+        const uint32_t a_addr = tc::smem_u32(smem + st * Cfg::kStage);
+        const uint32_t x_addr = a_addr + Cfg::kA;
 #pragma unroll
         for (int kk = 0; kk < kKStage / 8; ++kk) {
-          const uint64_t adesc = tc::smem_desc(a_addr + kk * 32, 16, 1024, tc::kSwizzle128B);
-          const uint64_t bdesc = tc::smem_desc(x_addr + kk * 32, 16, 1024, tc::kSwizzle128B);
-          tc::mma_tf32(tmem, adesc, bdesc, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+          const uint64_t ah = tc::smem_desc(a_addr + kk * 32, 16, 1024, tc::kSwizzle128B);
+          const uint64_t xh = tc::smem_desc(x_addr + kk * 32, 16, 1024, tc::kSwizzle128B);
+          tc::mma_tf32(tmem, ah, xh, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+          if (X3) {
+            const uint64_t al = tc::smem_desc(a_addr + kHalf + kk * 32, 16, 1024, tc::kSwizzle128B);
+            const uint64_t xl = tc::smem_desc(x_addr + kHalf + kk * 32, 16, 1024, tc::kSwizzle128B);
+            tc::mma_tf32(tmem, ah, xl, idesc, 1u);
+            tc::mma_tf32(tmem, al, xh, idesc, 1u);
+          }
         }
         tc::mma_commit(&empty[st]);
       }
       tc::mma_commit(done);
     }
-  } else if (warp >= 4) {
-    const int q = warp & 3;
-    int ok = 1;
-    if (lane == 0) {
-      ok = tc::mbar_wait(done, 0);
-      if (!ok) rmc_report(status, RMC_ETIMEOUT);
+  } else {
+    if (X3) {
+      // warps 2-7: split each landed A tile into its TF32 head (in place) and remainder (second half)
+      const int ct = threadIdx.x - 64;
+      for (int it = 0; it < num_it; ++it) {
+        const int st = it % kS;
+        if (!warp_wait(&full[st], (it / kS) & 1, abort_flag, status)) break;
+        unsigned char *a_tile = smem + st * Cfg::kStage;
+        for (int c = ct; c < Cfg::kA / 16; c += 32 * kAnConvWarps) {
+          float4 *hp = reinterpret_cast<float4 *>(a_tile) + c;
+          float4 h, lo;
+          split4(*hp, h, lo);
+          *hp = h;
+          *(reinterpret_cast<float4 *>(a_tile + kHalf) + c) = lo;
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&conv[st]);
+      }
     }
-    ok = __shfl_sync(0xffffffffu, ok, 0) && !*abort_flag;
-    tc::tc_fence_after();
-    const int64_t row = row0 + q * 32 + lane;
-    if (ok) {
+    if (warp >= 4) {
+      const int q = warp & 3;
+      const bool ok = warp_wait(done, 0, abort_flag, status);
+      tc::tc_fence_after();
+      const int64_t row = row0 + q * 32 + lane;
+      if (ok) {
 #pragma unroll 1
-      for (int c0 = 0; c0 < NPAD; c0 += 32) {
-        float v[32];
-        tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-        if (row < m) {
+        for (int c0 = 0; c0 < NPAD; c0 += 32) {
+          float v[32];
+          tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+          if (row < m) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (c0 + i < l) Y[row * ldy + c0 + i] = v[i];
+            for (int i = 0; i < 32; ++i)
+              if (c0 + i < l) Y[row * ldy + c0 + i] = v[i];
+          }
         }
       }
     }
@@ -566,21 +620,34 @@ __global__ void __launch_bounds__(kAnThreads, 1) tc_an_kernel(const __grid_const
 }
 
 // W = X^T A over a row range of A: A_op = X^T tiles (MT x 128 rows of l, K-major via TMA), B_op = A tile
-// (256 columns) staged by TMA and transposed to K-major by warps 2-3.  Partial sums per row range.
-template <int MT>
+// (NC columns) staged by TMA and transposed to K-major by warps 2-3.  Partial sums per row range.  X3: the
+// X^T remainder arrives by a second TMA, the transposers write the A tile's head and remainder.
+template <int MT, bool X3>
+struct AtCfg {
+  static constexpr int NC = X3 ? 128 : 256;            // columns of A per CTA (the MMA's N)
+  static constexpr int kStg = NC * kKStage * 4;        // staging / transposed tile bytes
+  static constexpr int kXt = MT * kOmegaBytes;         // MT x (128 rows x 32 TF32)
+  static constexpr int kHalf = kXt + kStg;
+  static constexpr int kStage = (X3 ? 2 : 1) * kHalf;
+  static constexpr size_t kSmem = 1024 + (size_t)kStgStages * kStg + (size_t)kStages * kStage + 256;
+  static_assert(kSmem <= kSmemCap, "tc_at_kernel shared memory");
+};
+
+template <int MT, bool X3>
 __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __grid_constant__ CUtensorMap tmap_a,
                                                                      const __grid_constant__ CUtensorMap tmap_xt,
+                                                                     const __grid_constant__ CUtensorMap tmap_xl,
                                                                      int64_t m, int64_t n, int64_t l,
                                                                      int64_t rows_per_split, float *part,
                                                                      int *status) {
-  constexpr int kXtBytes = MT * kOmegaBytes;           // MT x (128 rows x 32 TF32)
-  constexpr int kStageAt = kXtBytes + kBBytes;
+  using Cfg = AtCfg<MT, X3>;
+  constexpr int NC = Cfg::NC;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~uintptr_t(1023));
   unsigned char *staging = smem;
-  unsigned char *operands = smem + kStgStages * kBBytes;
-  uint64_t *stg_full = reinterpret_cast<uint64_t *>(operands + kStages * kStageAt);
+  unsigned char *operands = smem + kStgStages * Cfg::kStg;
+  uint64_t *stg_full = reinterpret_cast<uint64_t *>(operands + kStages * Cfg::kStage);
   uint64_t *stg_empty = stg_full + kStgStages;
   uint64_t *full = stg_empty + kStgStages;
   uint64_t *empty = full + kStages;
@@ -588,11 +655,11 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t n0 = (int64_t)blockIdx.x * kN;
+  const int64_t n0 = (int64_t)blockIdx.x * NC;
   const int64_t k_begin = (int64_t)blockIdx.z * rows_per_split;
   const int64_t k_end = min(m, k_begin + rows_per_split);
   const int num_it = k_end > k_begin ? (int)((k_end - k_begin + kKStage - 1) / kKStage) : 0;
-  constexpr uint32_t kCols = MT * kN;
+  constexpr uint32_t kCols = MT * NC;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStgStages; ++i) {
@@ -610,6 +677,7 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
   if (warp == 0 && lane == 0) {
     tc::prefetch_tmap(&tmap_a);
     tc::prefetch_tmap(&tmap_xt);
+    if (X3) tc::prefetch_tmap(&tmap_xl);
   }
   if (warp == 1) tc::tmem_alloc(tmem_slot, kCols);
   tc::tc_fence_before();
@@ -629,15 +697,18 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
           break;
         }
         const int32_t y = (int32_t)(k_begin + (int64_t)it * kKStage);
-        unsigned char *dst = staging + sst * kBBytes;
-        tc::mbar_arrive_expect_tx(&stg_full[sst], kBBytes);
+        unsigned char *dst = staging + sst * Cfg::kStg;
+        tc::mbar_arrive_expect_tx(&stg_full[sst], Cfg::kStg);
 #pragma unroll
-        for (int atom = 0; atom < kN / 32; ++atom)
+        for (int atom = 0; atom < NC / 32; ++atom)
           tc::tma_load_2d(dst + atom * kAtomBytes, &tmap_a, (int32_t)(n0 + atom * 32), y, &stg_full[sst]);
-        unsigned char *xt = operands + st * kStageAt;
-        tc::mbar_arrive_expect_tx(&full[st], kXtBytes);
+        unsigned char *xt = operands + st * Cfg::kStage;
+        tc::mbar_arrive_expect_tx(&full[st], (X3 ? 2 : 1) * Cfg::kXt);
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt) tc::tma_load_2d(xt + mt * kOmegaBytes, &tmap_xt, y, mt * 128, &full[st]);
+        for (int mt = 0; mt < MT; ++mt) {
+          tc::tma_load_2d(xt + mt * kOmegaBytes, &tmap_xt, y, mt * 128, &full[st]);
+          if (X3) tc::tma_load_2d(xt + Cfg::kHalf + mt * kOmegaBytes, &tmap_xl, y, mt * 128, &full[st]);
+        }
         ++issued;
       }
       for (int it = issued > kStgStages ? issued - kStgStages : 0; it < issued; ++it)
@@ -645,7 +716,7 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::instr_desc(2, 2, 0, 0, kN, kM);
+      constexpr uint32_t idesc = tc::instr_desc(2, 2, 0, 0, NC, kM);
       for (int it = 0; it < num_it; ++it) {
         const int st = it % kStages;
         if (*abort_flag || !tc::mbar_wait(&full[st], (it / kStages) & 1)) {
@@ -654,43 +725,60 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
           break;
         }
         tc::tc_fence_after();
-        const uint32_t base = tc::smem_u32(operands + st * kStageAt);
-        const uint32_t b_addr = base + kXtBytes;
+        const uint32_t base = tc::smem_u32(operands + st * Cfg::kStage);
+        const uint32_t b_addr = base + Cfg::kXt;
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
           for (int kk = 0; kk < kKStage / 8; ++kk) {
-            const uint64_t adesc = tc::smem_desc(base + mt * kOmegaBytes + kk * 32, 16, 1024, tc::kSwizzle128B);
-            const uint64_t bdesc = tc::smem_desc(b_addr + kk * 32, 16, 1024, tc::kSwizzle128B);
-            tc::mma_tf32(tmem + mt * kN, adesc, bdesc, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+            const uint64_t xh = tc::smem_desc(base + mt * kOmegaBytes + kk * 32, 16, 1024, tc::kSwizzle128B);
+            const uint64_t ah = tc::smem_desc(b_addr + kk * 32, 16, 1024, tc::kSwizzle128B);
+            tc::mma_tf32(tmem + mt * NC, xh, ah, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+            if (X3) {
+              const uint64_t xl =
+                  tc::smem_desc(base + Cfg::kHalf + mt * kOmegaBytes + kk * 32, 16, 1024, tc::kSwizzle128B);
+              const uint64_t al = tc::smem_desc(b_addr + Cfg::kHalf + kk * 32, 16, 1024, tc::kSwizzle128B);
+              tc::mma_tf32(tmem + mt * NC, xh, al, idesc, 1u);
+              tc::mma_tf32(tmem + mt * NC, xl, ah, idesc, 1u);
+            }
           }
         tc::mma_commit(&empty[st]);
       }
       tc::mma_commit(done);
     }
   } else if (warp < 4) {
-    // transposers: staging (row-major, swizzled) -> K-major B tile (see the Gaussian kernel)
+    // transposers: staging (row-major, swizzled) -> K-major B tile (see the Gaussian kernel); X3 also writes the
+    // remainder tile.  Unit (kq, cq): rows 4kq..4kq+3 x columns 4cq..4cq+3, cq < NC/4.
     const int tl = (warp - kTransWarp0) * 32 + lane;
     const int lq = tl & 7, grp = tl >> 3;
     for (int it = 0; it < num_it; ++it) {
       const int st = it % kStages, sst = it % kStgStages;
       if (!warp_wait(&stg_full[sst], (it / kStgStages) & 1, abort_flag, status)) break;
       if (!warp_wait(&empty[st], ((it / kStages) & 1) ^ 1, abort_flag, status)) break;
-      const unsigned char *src = staging + sst * kBBytes;
-      unsigned char *btile = operands + st * kStageAt + kXtBytes;
+      const unsigned char *src = staging + sst * Cfg::kStg;
+      unsigned char *btile = operands + st * Cfg::kStage + Cfg::kXt;
 #pragma unroll 2
-      for (int d = grp; d < 64; d += 8) {
-        const int kq = lq, cq = (d + lq) & 63;
+      for (int d = grp; d < NC / 4; d += 8) {
+        const int kq = lq, cq = (d + lq) & (NC / 4 - 1);
         const int atom = cq >> 3, cc = cq & 7;
         float4 v[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t)
           v[t] = *reinterpret_cast<const float4 *>(src + atom * kAtomBytes + swz_off(4 * kq + t, cc));
         const int c4 = 4 * cq;
-        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 0, kq)) = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
-        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 1, kq)) = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
-        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 2, kq)) = make_float4(v[0].z, v[1].z, v[2].z, v[3].z);
-        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 3, kq)) = make_float4(v[0].w, v[1].w, v[2].w, v[3].w);
+        float4 o[4] = {make_float4(v[0].x, v[1].x, v[2].x, v[3].x), make_float4(v[0].y, v[1].y, v[2].y, v[3].y),
+                       make_float4(v[0].z, v[1].z, v[2].z, v[3].z), make_float4(v[0].w, v[1].w, v[2].w, v[3].w)};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (X3) {
+            float4 h, lo;
+            split4(o[j], h, lo);
+            *reinterpret_cast<float4 *>(btile + swz_off(c4 + j, kq)) = h;
+            *reinterpret_cast<float4 *>(btile + Cfg::kHalf + swz_off(c4 + j, kq)) = lo;
+          } else {
+            *reinterpret_cast<float4 *>(btile + swz_off(c4 + j, kq)) = o[j];
+          }
+        }
       }
       tc::fence_proxy_async_smem();
       __syncwarp();
@@ -705,14 +793,14 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
     const bool ok = warp_wait(done, 0, abort_flag, status);
     tc::tc_fence_after();
     const int64_t row = (int64_t)et * kM + q * 32 + lane;    // row of W (index into l)
-    const int64_t ncols = min((int64_t)kN, n - n0);
+    const int64_t ncols = min((int64_t)NC, n - n0);
     if (ok) {
       float *prow = part + ((int64_t)blockIdx.z * l + row) * n + n0;
 #pragma unroll 1
-      for (int c0 = 0; c0 < kN; c0 += 32) {
+      for (int c0 = 0; c0 < NC; c0 += 32) {
         float v[32];
         if (num_it > 0) {
-          tc::tmem_ld32(tmem + (uint32_t)(et * kN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+          tc::tmem_ld32(tmem + (uint32_t)(et * NC) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
         } else {
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = 0.f;
@@ -758,62 +846,98 @@ __global__ void transpose32_kernel(const float *__restrict__ in, int64_t rows, i
   }
 }
 
-int at_splits(int64_t m, int64_t n, int num_sms) { return tc_splits(m, (n + kN - 1) / kN, num_sms); }
+// Column tile of W = X^T A: 128 columns in the 3xTF32 form (both operand halves must fit), 256 otherwise.
+int at_cols(bool x3) { return x3 ? 128 : 256; }
+
+int at_splits(int64_t m, int64_t n, bool x3, int num_sms) {
+  return tc_splits(m, (n + at_cols(x3) - 1) / at_cols(x3), num_sms);
+}
 
 int64_t xt_ld(int64_t rows) { return (rows + 3) / 4 * 4; }   // 16-byte row pitch for TMA
 
-// Launch Y = A X with X^T (l x n) given; l <= 256.
-int launch_an_t(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *Xt, int64_t l,
-                int64_t ldxt, float *Y, int64_t ldy) {
-  CUtensorMap ma, mx;
+// In place: Xt (rows x cols, ld) <- its TF32 head; Xl <- the remainder (3xTF32 operand split).
+__global__ void split_tf32_kernel(float *Xt, int64_t rows, int64_t cols, int64_t ld, float *Xl) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e - r * cols;
+    const float v = Xt[r * ld + c], h = tf32_head(v);
+    Xt[r * ld + c] = h;
+    Xl[r * ld + c] = v - h;
+  }
+}
+
+template <int NP, bool X3>
+int an_launch(rmc_ctx *ctx, const CUtensorMap &ma, const CUtensorMap &mx, const CUtensorMap &ml, int64_t m,
+              int64_t n, int64_t l, float *Y, int64_t ldy) {
+  const size_t smem = AnCfg<NP, X3>::kSmem;
+  RMC_TRY_CUDA(cudaFuncSetAttribute(tc_an_kernel<NP, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  tc_an_kernel<NP, X3><<<(unsigned)((m + 127) / 128), kAnThreads, smem, ctx->stream>>>(ma, mx, ml, m, n, l, Y, ldy,
+                                                                                      ctx->d_status);
+  return RMC_OK;
+}
+
+// Launch Y = A X with X^T (l x n) given (X3: Xt holds the heads, Xl the remainders); l <= 256.
+int launch_an_t(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *Xt, const float *Xl,
+                int64_t l, int64_t ldxt, float *Y, int64_t ldy, bool x3) {
+  CUtensorMap ma, mx, ml;
   const int npad = l <= 32 ? 32 : l <= 64 ? 64 : l <= 128 ? 128 : 256;
   RMC_TRY(make_tmap(&ma, A, m, n, lda, 128));
   RMC_TRY(make_tmap(&mx, Xt, l, n, ldxt, npad));
-  const size_t smem = 1024 + (size_t)kAnStages * (128 * 128 + npad * 128) + 256;
-  cudaStream_t st = ctx->stream;
-  const unsigned grid = (unsigned)((m + 127) / 128);
-  RmcProf prof(ctx, RMC_K_MATMUL_AN);
-#define RMC_AN_CASE(NP)                                                                                     \
-  case NP:                                                                                                  \
-    RMC_TRY_CUDA(cudaFuncSetAttribute(tc_an_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    tc_an_kernel<NP><<<grid, kAnThreads, smem, st>>>(ma, mx, m, n, l, Y, ldy, ctx->d_status);                \
-    break;
-  switch (npad) {
-    RMC_AN_CASE(32)
-    RMC_AN_CASE(64)
-    RMC_AN_CASE(128)
-    RMC_AN_CASE(256)
+  if (x3) RMC_TRY(make_tmap(&ml, Xl, l, n, ldxt, npad));
+  else ml = mx;
+  {
+    RmcProf prof(ctx, RMC_K_MATMUL_AN);
+    int rc = RMC_OK;
+    switch (npad * 2 + (x3 ? 1 : 0)) {
+      case 64: rc = an_launch<32, false>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
+      case 65: rc = an_launch<32, true>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
+      case 128: rc = an_launch<64, false>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
+      case 129: rc = an_launch<64, true>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
+      case 256: rc = an_launch<128, false>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
+      case 257: rc = an_launch<128, true>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
+      case 512: rc = an_launch<256, false>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
+      default: rc = an_launch<256, true>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
+    }
+    RMC_TRY(rc);
   }
-#undef RMC_AN_CASE
   rmc_note_launch();
   RMC_LAUNCH_CHECK();
   return RMC_OK;
 }
 
-// Launch W = X^T A with X^T (l x m) given; l <= 256; part: workspace for the row-range partial sums.
-int launch_at_t(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *Xt, int64_t l,
-                int64_t ldxt, float *W, int64_t ldw, float *part) {
-  CUtensorMap ma, mx;
+template <int MT, bool X3>
+int at_launch(rmc_ctx *ctx, const CUtensorMap &ma, const CUtensorMap &mx, const CUtensorMap &ml, int64_t m,
+              int64_t n, int64_t l, int64_t rows, int splits, float *part) {
+  const size_t smem = AtCfg<MT, X3>::kSmem;
+  RMC_TRY_CUDA(cudaFuncSetAttribute(tc_at_kernel<MT, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)((n + AtCfg<MT, X3>::NC - 1) / AtCfg<MT, X3>::NC), 1, (unsigned)splits);
+  tc_at_kernel<MT, X3><<<grid, 32 * (4 + 4 * MT), smem, ctx->stream>>>(ma, mx, ml, m, n, l, rows, part,
+                                                                       ctx->d_status);
+  return RMC_OK;
+}
+
+// Launch W = X^T A with X^T (l x m) given (X3: Xt heads, Xl remainders); l <= 256; part: workspace for the
+// row-range partial sums.
+int launch_at_t(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *Xt, const float *Xl,
+                int64_t l, int64_t ldxt, float *W, int64_t ldw, float *part, bool x3) {
+  CUtensorMap ma, mx, ml;
   RMC_TRY(make_tmap(&ma, A, m, n, lda, kKStage));
   RMC_TRY(make_tmap(&mx, Xt, l, m, ldxt, 128));
-  const int splits = at_splits(m, n, ctx->num_sms);
+  if (x3) RMC_TRY(make_tmap(&ml, Xl, l, m, ldxt, 128));
+  else ml = mx;
+  const int splits = at_splits(m, n, x3, ctx->num_sms);
   int64_t rows = (m + splits - 1) / splits;
   rows = (rows + kKStage - 1) / kKStage * kKStage;
-  cudaStream_t st = ctx->stream;
-  dim3 grid((unsigned)((n + kN - 1) / kN), 1, (unsigned)splits);
   {
     RmcProf prof(ctx, RMC_K_MATMUL_AT);
-    if (l <= 128) {
-      const size_t smem = 1024 + (size_t)kStgStages * kBBytes + (size_t)kStages * (kOmegaBytes + kBBytes) + 256;
-      RMC_TRY_CUDA(cudaFuncSetAttribute(tc_at_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      tc_at_kernel<1><<<grid, 32 * 8, smem, st>>>(ma, mx, m, n, l, rows, part, ctx->d_status);
-    } else {
-      const size_t smem = 1024 + (size_t)kStgStages * kBBytes + (size_t)kStages * (2 * kOmegaBytes + kBBytes) + 256;
-      RMC_TRY_CUDA(cudaFuncSetAttribute(tc_at_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      tc_at_kernel<2><<<grid, 32 * 12, smem, st>>>(ma, mx, m, n, l, rows, part, ctx->d_status);
-    }
+    int rc;
+    if (l <= 128) rc = x3 ? at_launch<1, true>(ctx, ma, mx, ml, m, n, l, rows, splits, part)
+                          : at_launch<1, false>(ctx, ma, mx, ml, m, n, l, rows, splits, part);
+    else rc = x3 ? at_launch<2, true>(ctx, ma, mx, ml, m, n, l, rows, splits, part)
+                 : at_launch<2, false>(ctx, ma, mx, ml, m, n, l, rows, splits, part);
+    RMC_TRY(rc);
   }
-  sum_parts_kernel<<<rmc_blocks(l * n, 256, 8192), 256, 0, st>>>(part, splits, l, n, W, ldw);
+  sum_parts_kernel<<<rmc_blocks(l * n, 256, 8192), 256, 0, ctx->stream>>>(part, splits, l, n, W, ldw);
   rmc_note_launch(2);
   RMC_LAUNCH_CHECK();
   return RMC_OK;
@@ -821,39 +945,48 @@ int launch_at_t(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda,
 
 }  // namespace
 
-// Workspace of the public TF32 products: X^T (padded pitch) plus the split partials of W = X^T A.
-size_t rmc_tc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, int num_sms) {
+// Workspace of the public tensor-core products: X^T (padded pitch; 3xTF32 also its remainder) plus the split
+// partials of W = X^T A.
+size_t rmc_tc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, bool x3, int num_sms) {
   WsCarve w;
-  if (which == 0) {
-    w.take<float>((size_t)l * xt_ld(n));
-  } else {
-    w.take<float>((size_t)l * xt_ld(m));
-    w.take<float>((size_t)at_splits(m, n, num_sms) * l * n);
-  }
+  const int64_t ld = xt_ld(which == 0 ? n : m);
+  w.take<float>((size_t)l * ld);
+  if (x3) w.take<float>((size_t)l * ld);
+  if (which == 1) w.take<float>((size_t)at_splits(m, n, x3, num_sms) * l * n);
   return w.off;
 }
 
 int rmc_tc_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
-                     int64_t ldx, float *Y, int64_t ldy, void *ws) {
+                     int64_t ldx, float *Y, int64_t ldy, bool x3, void *ws) {
   WsCarve w;
   w.base = static_cast<char *>(ws);
   const int64_t ld = xt_ld(n);
   float *Xt = w.take<float>((size_t)l * ld);
+  float *Xl = x3 ? w.take<float>((size_t)l * ld) : nullptr;
   dim3 grid((unsigned)((l + 31) / 32), (unsigned)((n + 31) / 32));
   transpose32_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(X, n, l, ldx, Xt, ld);
   rmc_note_launch();
-  return launch_an_t(ctx, A, m, n, lda, Xt, l, ld, Y, ldy);
+  if (x3) {
+    split_tf32_kernel<<<rmc_blocks(l * n, 256, 4096), 256, 0, ctx->stream>>>(Xt, l, n, ld, Xl);
+    rmc_note_launch();
+  }
+  return launch_an_t(ctx, A, m, n, lda, Xt, Xl, l, ld, Y, ldy, x3);
 }
 
 int rmc_tc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
-                     int64_t ldx, float *W, int64_t ldw, void *ws) {
+                     int64_t ldx, float *W, int64_t ldw, bool x3, void *ws) {
   WsCarve w;
   w.base = static_cast<char *>(ws);
   const int64_t ld = xt_ld(m);
   float *Xt = w.take<float>((size_t)l * ld);
-  float *part = w.take<float>((size_t)at_splits(m, n, ctx->num_sms) * l * n);
+  float *Xl = x3 ? w.take<float>((size_t)l * ld) : nullptr;
+  float *part = w.take<float>((size_t)at_splits(m, n, x3, ctx->num_sms) * l * n);
   dim3 grid((unsigned)((l + 31) / 32), (unsigned)((m + 31) / 32));
   transpose32_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(X, m, l, ldx, Xt, ld);
   rmc_note_launch();
-  return launch_at_t(ctx, A, m, n, lda, Xt, l, ld, W, ldw, part);
+  if (x3) {
+    split_tf32_kernel<<<rmc_blocks(l * m, 256, 4096), 256, 0, ctx->stream>>>(Xt, l, m, ld, Xl);
+    rmc_note_launch();
+  }
+  return launch_at_t(ctx, A, m, n, lda, Xt, Xl, l, ld, W, ldw, part, x3);
 }

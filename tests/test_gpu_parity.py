@@ -292,20 +292,24 @@ def test_cholqr2_ill_conditioned_falls_back_to_fp64(R):
 
 # ------------------------------------------------------------------ a5-a7 on the tensor cores (TF32)
 
-@pytest.mark.parametrize("m,n,l", [(2048, 512, 20), (1000, 300, 33), (70000, 200, 120), (4096, 1000, 200)])
-def test_matmuls_tf32(R, m, n, l):
+@pytest.mark.parametrize("prec,tol", [("tf32", 2e-3), ("tf32x3", 1e-5)])
+@pytest.mark.parametrize("m,n,l", [(2048, 512, 20), (1000, 300, 33), (70000, 200, 120), (4096, 1000, 200),
+                                   (333, 4100, 64), (5000, 260, 256)])
+def test_matmuls_tf32(R, m, n, l, prec, tol):
+    """TF32 keeps 10 mantissa bits (2e-3); 3xTF32 splits every operand into a TF32 head and remainder and is
+    compared at the FP32 tolerance (1e-5)."""
     A = workloads.gaussian(m, n, 1)
     X1 = workloads.gaussian(n, l, 2)
     X2 = workloads.gaussian(m, l, 3)
-    Y = R.rmc_matmul_an(dev(A), dev(X1), prec="tf32")
-    W = R.rmc_matmul_at(dev(A), dev(X2), prec="tf32")
+    Y = R.rmc_matmul_an(dev(A), dev(X1), prec=prec)
+    W = R.rmc_matmul_at(dev(A), dev(X2), prec=prec)
     R.rmc_sync()
     A64 = A.astype(np.float64)
-    assert relfro(Y.cpu().numpy(), A64 @ X1) < 2e-3
-    assert relfro(W.cpu().numpy(), X2.astype(np.float64).T @ A64) < 2e-3
+    assert relfro(Y.cpu().numpy(), A64 @ X1) < tol
+    assert relfro(W.cpu().numpy(), X2.astype(np.float64).T @ A64) < tol
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "tf32x3"])
 def test_rsvd_factor_rank_workload(R, prec):
     """A = G1 diag(1/i) G2^T (Gaussian factors), the large-rSVD recipe at a size the oracle runs."""
     A = workloads.factor_rank_numpy(4096, 2048, 256, seed=3)
@@ -313,7 +317,7 @@ def test_rsvd_factor_rank_workload(R, prec):
     U, s, V = R.rmc_rsvd(dev(A), k, p, q, seed=7, prec=prec)
     R.rmc_sync()
     _, so, _, _ = rsvd.rsvd(A, k, p, q, 7)
-    tol = 1e-4 if prec == "fp32" else 2e-3
+    tol = 2e-3 if prec == "tf32" else 1e-4
     np.testing.assert_allclose(s.cpu().numpy(), so, rtol=tol)
     A64 = A.astype(np.float64)
     err = np.linalg.norm(A64 - (U.cpu().numpy() * s.cpu().numpy()) @ V.cpu().numpy().T)
