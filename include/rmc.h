@@ -92,6 +92,17 @@ int rmc_sync(rmc_ctx *ctx);
 /* A static description of a status code. */
 const char *rmc_status_string(int status);
 
+/* Context options (rmc_set_option / rmc_get_option):
+ *   RMC_OPT_SMALL_FP64  0 (default): the small l x l factorizations run in FP32 where that meets the stated
+ *                       tolerances -- CholeskyQR2's Cholesky in FP32 with an FP64 fallback on a non-positive
+ *                       pivot, its Gram matrices with FP32 products summed in FP64, the one-sided Jacobi SVD in
+ *                       FP32 above l = 32.  1: all of them in FP64 (Gram products, Cholesky, Jacobi rotations);
+ *                       slower on this GPU, whose FP64 rate is a small fraction of its FP32 rate.
+ * Errors: RMC_EINVAL for an unknown option or value. */
+#define RMC_OPT_SMALL_FP64 1
+int rmc_set_option(rmc_ctx *ctx, int option, int value);
+int rmc_get_option(const rmc_ctx *ctx, int option, int *value);
+
 /* Bytes of device workspace the context currently holds. */
 int rmc_workspace_bytes(const rmc_ctx *ctx, size_t *bytes);
 

@@ -33,6 +33,8 @@ _SIGS = {
     "rmc_set_stream": [_p, _p],
     "rmc_sync": [_p],
     "rmc_workspace_bytes": [_p, ctypes.POINTER(_sz)],
+    "rmc_set_option": [_p, _int, _int],
+    "rmc_get_option": [_p, _int, ctypes.POINTER(_int)],
     "rmc_sketch": [_p, _p, _i64, _i64, _i64, _i64, _int, _u64, _int, _p, _i64],
     "rmc_lsr_sketch": [_p, _p, _i64, _i64, _i64, _p, _i64, _int, _u64, _int, _p],
     "rmc_rsvd": [_p, _p, _i64, _i64, _i64, _int, _int, _int, _u64, _int, _p, _i64, _p, _p, _i64],
@@ -179,6 +181,21 @@ def rmc_sync_all():
     """rmc_sync on every context of the current device."""
     for c in _device_contexts():
         _check(lib.rmc_sync(c.handle), "rmc_sync")
+
+
+RMC_OPT_SMALL_FP64 = 1
+
+
+def rmc_set_option(option, value):
+    """Set a context option of the current stream's context (RMC_OPT_SMALL_FP64: 1 runs the small
+    factorizations in FP64)."""
+    _check(lib.rmc_set_option(context().bind(), option, value), "rmc_set_option")
+
+
+def rmc_get_option(option):
+    out = _int()
+    _check(lib.rmc_get_option(context().bind(), option, ctypes.byref(out)), "rmc_get_option")
+    return out.value
 
 
 def rmc_workspace_bytes():

@@ -123,6 +123,26 @@ const char *rmc_status_string(int status) {
   }
 }
 
+int rmc_set_option(rmc_ctx *ctx, int option, int value) {
+  if (!ctx) return RMC_EINVAL;
+  switch (option) {
+    case RMC_OPT_SMALL_FP64:
+      if (value != 0 && value != 1) return RMC_EINVAL;
+      ctx->small_fp64 = value != 0;
+      return RMC_OK;
+    default:
+      return RMC_EINVAL;
+  }
+}
+
+int rmc_get_option(const rmc_ctx *ctx, int option, int *value) {
+  if (!ctx || !value) return RMC_EINVAL;
+  switch (option) {
+    case RMC_OPT_SMALL_FP64: *value = ctx->small_fp64 ? 1 : 0; return RMC_OK;
+    default: return RMC_EINVAL;
+  }
+}
+
 int rmc_workspace_bytes(const rmc_ctx *ctx, size_t *bytes) {
   if (!ctx || !bytes) return RMC_EINVAL;
   *bytes = ctx->ws_bytes;

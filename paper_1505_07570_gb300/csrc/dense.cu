@@ -612,6 +612,108 @@ __global__ void jacobi_finish_kernel(const T *W, const T *V, int l, float *Ub, f
   }
 }
 
+// ---------------------------------------------------- one-sided Jacobi, eight lanes per column pair
+// The same round-robin rotations as jacobi_smem_kernel, with W alone in shared memory (no rotation
+// accumulator: the other singular factor is recovered afterwards, see jacobi_right_kernel) and eight lanes per
+// column pair instead of a warp: a 1024-thread block rotates up to 128 disjoint pairs per round, each lane
+// holding every eighth row, with three shuffle levels per inner product.  For l = 120 this turns a round of 60
+// pairs from two warp-serial pair updates into one pass of 15 warps.
+template <typename T>
+__global__ void __launch_bounds__(1024) jacobi_grp_kernel(T *Wg, int l, T tol, int max_sweeps, int *status) {
+  extern __shared__ __align__(16) unsigned char jg_raw[];
+  T *W = reinterpret_cast<T *>(jg_raw);
+  __shared__ int rotated;
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) W[e] = Wg[e];
+  const int grp = threadIdx.x >> 3, j = threadIdx.x & 7;
+  const int lp = (l + 1) & ~1;
+  const T tol2 = tol * tol;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int round = 0; round < lp - 1; ++round) {
+      int p = -1, q = -1;
+      if (grp < lp / 2) {
+        const int a = grp, b = lp - 1 - grp;
+        p = a == 0 ? 0 : 1 + (a - 1 + round) % (lp - 1);
+        q = b == 0 ? 0 : 1 + (b - 1 + round) % (lp - 1);
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        if (q >= l) p = -1;
+      }
+      T alpha = 0, beta = 0, gamma = 0;
+      T *wp = W + (size_t)(p < 0 ? 0 : p) * l, *wq = W + (size_t)(p < 0 ? 0 : q) * l;
+      if (p >= 0)
+        for (int r = j; r < l; r += 8) {
+          const T x = wp[r], y = wq[r];
+          alpha = fma(x, x, alpha);
+          beta = fma(y, y, beta);
+          gamma = fma(x, y, gamma);
+        }
+      // the eight lanes of a group are aligned in the warp: xor offsets 1, 2, 4 stay inside the group
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+        beta += __shfl_xor_sync(0xffffffffu, beta, o);
+        gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
+      }
+      if (p >= 0 && gamma != T(0) && gamma * gamma > tol2 * alpha * beta) {
+        T c, sn;
+        rotation(alpha, beta, gamma, c, sn);
+        for (int r = j; r < l; r += 8) {
+          const T x = wp[r], y = wq[r];
+          wp[r] = c * x - sn * y;
+          wq[r] = sn * x + c * y;
+        }
+        if (j == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  if (sweep == max_sweeps && threadIdx.x == 0) rmc_report(status, RMC_ENUMERIC);
+  __syncthreads();
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) Wg[e] = W[e];
+}
+
+// After jacobi_grp_kernel on R (R V = W, columns of W orthogonal): sigma_j = ||w_j|| (FP64 sum), the columns
+// ranked by descending sigma (ties by index), M[:, rank(j)] = w_j / sigma_j (the left singular vectors of R,
+// row-major l x l FP32) and sigma[rank(j)].
+template <typename T>
+__global__ void jacobi_left_kernel(const T *W, int l, float *M, float *sigma) {
+  extern __shared__ double sgl[];
+  for (int jj = threadIdx.x; jj < l; jj += blockDim.x) {
+    double s = 0;
+    for (int r = 0; r < l; ++r) s += (double)W[(int64_t)jj * l + r] * (double)W[(int64_t)jj * l + r];
+    sgl[jj] = sqrt(s);
+  }
+  __syncthreads();
+  for (int jj = threadIdx.x; jj < l; jj += blockDim.x) {
+    int rank = 0;
+    for (int u = 0; u < l; ++u) rank += (sgl[u] > sgl[jj]) || (sgl[u] == sgl[jj] && u < jj);
+    sigma[rank] = (float)sgl[jj];
+    const double inv = sgl[jj] > 0 ? 1.0 / sgl[jj] : 0.0;
+    for (int r = 0; r < l; ++r) M[r * l + rank] = (float)(W[(int64_t)jj * l + r] * inv);
+  }
+}
+
+// The right singular vectors of R (upper triangular, row-major FP64) from its left ones: R = M diag(sigma) V^T
+// gives V = R^T M diag(sigma)^-1, Ub[:, c] = R^T M[:, c] / sigma_c in FP64 (one block per column c).  The error
+// of column c is about eps_FP32 * sigma_1 / sigma_c: FP32-level for the leading columns a k-SVD keeps.
+__global__ void jacobi_right_kernel(const double *R, int l, const float *M, const float *sigma, float *Ub) {
+  const int c = blockIdx.x;
+  const double inv = sigma[c] > 0.f ? 1.0 / (double)sigma[c] : 0.0;
+  for (int r = threadIdx.x; r < l; r += blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i <= r; ++i) acc += R[(int64_t)i * l + r] * (double)M[(int64_t)i * l + c];
+    Ub[(int64_t)r * l + c] = (float)(acc * inv);
+  }
+}
+
 // R (row-major FP64, upper) -> column-major working copy of type T.
 template <typename T>
 __global__ void to_colmajor_kernel(const double *R, int l, T *W) {
@@ -1153,7 +1255,7 @@ static int launch_factor(rmc_ctx *ctx, double *G, int l, double *Rinv, float *Ri
   cudaStream_t st = ctx->stream;
   const size_t smem = chol32_smem_bytes(l);
   RmcProf prof(ctx, RMC_K_SMALL);
-  if (smem > kMaxPackedBytes) {
+  if (smem > kMaxPackedBytes || ctx->small_fp64) {
     force_fp64_kernel<<<1, 1, 0, st>>>(&fail[0]);
   } else {
     if (smem > 48 * 1024)
@@ -1192,7 +1294,7 @@ int rmc_launch_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l_, int64_t ld
   int *fail = w.take<int>(4);
   double *part = reinterpret_cast<double *>(w.take<char>(gram_ws(m, l, ctx->num_sms)));
   for (int pass = 0; pass < passes; ++pass) {
-    RMC_TRY(launch_gram(ctx, Y, m, l, ldy, G, part, fp64_gram));
+    RMC_TRY(launch_gram(ctx, Y, m, l, ldy, G, part, fp64_gram || ctx->small_fp64));
     RMC_TRY(launch_factor(ctx, G, l, Rinv, Rinv32, fail));
     RMC_TRY(launch_rowblock(st, Y, m, l, ldy, Rinv32, l, l, Y, ldy));
     if (R) {
@@ -1210,6 +1312,41 @@ int rmc_launch_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l_, int64_t ld
 // ------------------------------------------------------------------------------------------- small SVD
 
 static bool jacobi_in_fp64(int l) { return l <= 32; }
+
+// The eight-lanes-per-pair Jacobi keeps W (l x l) in shared memory: FP32 up to l = 240, FP64 up to l = 120.
+static bool jacobi_grp_fits(int l, bool fp64) {
+  return (size_t)l * l * (fp64 ? sizeof(double) : sizeof(float)) + 64 <= 227 * 1024;
+}
+
+// Jacobi on R (FP64 row-major upper, l x l) with the group kernel: M (left singular vectors of R, row-major) and
+// sigma, descending.  fp64: rotations in FP64 (else FP32, FP64 below l = 33 as jacobi_in_fp64 says).
+static int launch_jacobi_grp(rmc_ctx *ctx, const double *R, int l, double *work, float *M, float *sigma,
+                             bool fp64) {
+  cudaStream_t st = ctx->stream;
+  if (fp64 || jacobi_in_fp64(l)) {
+    const double tol = 8 * 2.220446049250313e-16 * sqrt((double)l);
+    const size_t smem = sizeof(double) * (size_t)l * l;
+    if (smem > 48 * 1024)
+      RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_grp_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    to_colmajor_kernel<double><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, work);
+    jacobi_grp_kernel<double><<<1, 1024, smem, st>>>(work, l, tol, 60, ctx->d_status);
+    jacobi_left_kernel<double><<<1, 256, sizeof(double) * l, st>>>(work, l, M, sigma);
+  } else {
+    const float tol = 4 * 1.1920929e-7f * sqrtf((float)l);
+    const size_t smem = sizeof(float) * (size_t)l * l;
+    float *Wf = reinterpret_cast<float *>(work);
+    if (smem > 48 * 1024)
+      RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_grp_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    to_colmajor_kernel<float><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, Wf);
+    jacobi_grp_kernel<float><<<1, 1024, smem, st>>>(Wf, l, tol, 60, ctx->d_status);
+    jacobi_left_kernel<float><<<1, 256, sizeof(double) * l, st>>>(Wf, l, M, sigma);
+  }
+  rmc_note_launch(3);
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
 
 size_t rmc_svd_wide_ws(int64_t l, int64_t n, int num_sms) {
   WsCarve w;
@@ -1238,26 +1375,32 @@ int rmc_launch_svd_wide(rmc_ctx *ctx, const float *B, int64_t l_, int64_t n, int
   // the singular values come from R: its Gram matrices take FP64 products
   RMC_TRY(rmc_launch_cholqr2(ctx, Bt, n, l, l, R, rest, 2, true));           // B^T = Q2 R
   RmcProf prof(ctx, RMC_K_SMALL);
-  rmc_note_launch(3);
-  const size_t smem64 = 2 * sizeof(double) * (size_t)l * l, smem32 = 2 * sizeof(float) * (size_t)l * l;
-  if (jacobi_in_fp64(l)) {
-    const double tol = 8 * 2.220446049250313e-16 * sqrt((double)l);
-    to_colmajor_kernel<double><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, W);
-    jacobi_smem_kernel<double><<<1, 1024, smem64, st>>>(W, V, l, tol, 60, ctx->d_status);
-    jacobi_finish_kernel<double><<<1, 256, sizeof(double) * l, st>>>(W, V, l, Ub, M, sigma);
+  if (jacobi_grp_fits(l, ctx->small_fp64)) {
+    RMC_TRY(launch_jacobi_grp(ctx, R, l, W, M, sigma, ctx->small_fp64));
+    jacobi_right_kernel<<<l, 128, 0, st>>>(R, l, M, sigma, Ub);                // Ub = R^T M diag(sigma)^-1
+    rmc_note_launch();
   } else {
-    const float tol = 4 * 1.1920929e-7f * sqrtf((float)l);
-    float *Wf = reinterpret_cast<float *>(W), *Vf = reinterpret_cast<float *>(V);
-    to_colmajor_kernel<float><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, Wf);
-    if (smem32 <= 200 * 1024) {
-      if (smem32 > 48 * 1024)
-        RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_smem_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem32));
-      jacobi_smem_kernel<float><<<1, 1024, smem32, st>>>(Wf, Vf, l, tol, 60, ctx->d_status);
+    rmc_note_launch(3);
+    const size_t smem64 = 2 * sizeof(double) * (size_t)l * l, smem32 = 2 * sizeof(float) * (size_t)l * l;
+    if (jacobi_in_fp64(l)) {
+      const double tol = 8 * 2.220446049250313e-16 * sqrt((double)l);
+      to_colmajor_kernel<double><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, W);
+      jacobi_smem_kernel<double><<<1, 1024, smem64, st>>>(W, V, l, tol, 60, ctx->d_status);
+      jacobi_finish_kernel<double><<<1, 256, sizeof(double) * l, st>>>(W, V, l, Ub, M, sigma);
     } else {
-      jacobi_kernel<float><<<1, 1024, 0, st>>>(Wf, Vf, l, tol, 60, ctx->d_status);
+      const float tol = 4 * 1.1920929e-7f * sqrtf((float)l);
+      float *Wf = reinterpret_cast<float *>(W), *Vf = reinterpret_cast<float *>(V);
+      to_colmajor_kernel<float><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, Wf);
+      if (smem32 <= 200 * 1024) {
+        if (smem32 > 48 * 1024)
+          RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_smem_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem32));
+        jacobi_smem_kernel<float><<<1, 1024, smem32, st>>>(Wf, Vf, l, tol, 60, ctx->d_status);
+      } else {
+        jacobi_kernel<float><<<1, 1024, 0, st>>>(Wf, Vf, l, tol, 60, ctx->d_status);
+      }
+      jacobi_finish_kernel<float><<<1, 256, sizeof(double) * l, st>>>(Wf, Vf, l, Ub, M, sigma);
     }
-    jacobi_finish_kernel<float><<<1, 256, sizeof(double) * l, st>>>(Wf, Vf, l, Ub, M, sigma);
   }
   RMC_LAUNCH_CHECK();
   return launch_rowblock(st, Bt, n, l, l, M, l, l, Vb, ldv);                 // Vb = Q2 M
@@ -1266,7 +1409,8 @@ int rmc_launch_svd_wide(rmc_ctx *ctx, const float *B, int64_t l_, int64_t n, int
 // SVD of a square l x l matrix by one-sided Jacobi on its columns, with no QR first (for symmetric PSD
 // matrices whose condition number is beyond a Cholesky-based QR, e.g. the landmark block of a kernel matrix):
 // W (row-major FP64) = Ml diag(sigma) Vr^T with Ml the left and Vr the right singular vectors (row-major FP32,
-// columns ordered by descending sigma).  FP64 rotations for l <= 32, FP32 above, as the small SVD of rmc_rsvd.
+// columns ordered by descending sigma; Vr is written only on the path for l beyond the shared-memory group
+// kernel).  FP64 rotations for l <= 32 or with RMC_OPT_SMALL_FP64, FP32 otherwise, as the small SVD of rmc_rsvd.
 size_t rmc_jacobi_square_ws(int64_t l) { return 2 * sizeof(double) * (size_t)l * l + 256; }
 
 int rmc_launch_jacobi_square(rmc_ctx *ctx, const double *Wrm, int l, float *Ml, float *sigma, float *Vr, void *ws) {
@@ -1275,6 +1419,7 @@ int rmc_launch_jacobi_square(rmc_ctx *ctx, const double *Wrm, int l, float *Ml, 
   double *V = W + (size_t)l * l;
   const size_t smem64 = 2 * sizeof(double) * (size_t)l * l, smem32 = 2 * sizeof(float) * (size_t)l * l;
   RmcProf prof(ctx, RMC_K_SMALL);
+  if (jacobi_grp_fits(l, ctx->small_fp64)) return launch_jacobi_grp(ctx, Wrm, l, W, Ml, sigma, ctx->small_fp64);
   rmc_note_launch(3);
   if (jacobi_in_fp64(l)) {
     const double tol = 8 * 2.220446049250313e-16 * sqrt((double)l);

@@ -22,6 +22,7 @@ struct rmc_ctx {
   int *h_status;        // pinned host copy
   int device;
   int num_sms;
+  bool small_fp64;      // RMC_OPT_SMALL_FP64: CholeskyQR2 Gram products, Cholesky and Jacobi SVD in FP64
   // measurement hooks
   bool prof;
   int prof_used, prof_cap;

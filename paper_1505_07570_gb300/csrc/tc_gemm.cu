@@ -451,7 +451,8 @@ namespace {
 //
 // X3 (RMC_TF32X3): every FP32 operand v is split into a TF32 head h (v with its 13 low mantissa bits cleared,
 // exactly what the tensor core reads) and the remainder v - h (exact in FP32), and each k-step issues three
-// MMAs into the same accumulator: A_h X_h + A_h X_l + A_l X_h.  The dropped A_l X_l and the TF32 reading of the
+// MMAs: A_h X_h into one accumulator, the cross terms A_h X_l + A_l X_h into a second (their own rounding is
+// then ~2^-11 smaller than the main chain's), summed with round-to-nearest in the epilogue.  The dropped A_l X_l and the TF32 reading of the
 // remainders leave about 2^-21 relative error per product instead of TF32's 2^-11.  X's head and remainder are
 // split once in global memory; A's are split on chip (converter warps for Y = A X, the transposer warps for
 // W = X^T A, which write both parts of the transposed tile).
@@ -483,7 +484,7 @@ __global__ void __launch_bounds__(kAnThreads, 1) tc_an_kernel(const __grid_const
                                                               const __grid_constant__ CUtensorMap tmap_xt,
                                                               const __grid_constant__ CUtensorMap tmap_xl,
                                                               int64_t m, int64_t n, int64_t l, float *Y,
-                                                              int64_t ldy, int *status) {
+                                                              int64_t ldy, int64_t cols_per_split, int *status) {
   using Cfg = AnCfg<NPAD, X3>;
   constexpr int kS = Cfg::kStages;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -498,8 +499,12 @@ __global__ void __launch_bounds__(kAnThreads, 1) tc_an_kernel(const __grid_const
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t row0 = (int64_t)blockIdx.x * 128;
-  const int num_it = (int)((n + kKStage - 1) / kKStage);
-  constexpr uint32_t kCols = NPAD < 32 ? 32 : NPAD;
+  // split-K: this CTA reduces over columns [k0, k1) of A; its partial goes to Y + blockIdx.y * m * ldy
+  const int64_t k0 = (int64_t)blockIdx.y * cols_per_split, k1 = min(n, k0 + cols_per_split);
+  const int num_it = k1 > k0 ? (int)((k1 - k0 + kKStage - 1) / kKStage) : 0;
+  Y += (int64_t)blockIdx.y * m * ldy;
+  // X3: the cross terms accumulate in a second accumulator (columns NPAD..2 NPAD-1), see tc_an's epilogue
+  constexpr uint32_t kCols = (X3 ? 2 : 1) * (NPAD < 32 ? 32 : NPAD);
   constexpr int kHalf = Cfg::kA + Cfg::kX;
 
   if (threadIdx.x == 0) {
@@ -535,9 +540,10 @@ __global__ void __launch_bounds__(kAnThreads, 1) tc_an_kernel(const __grid_const
         }
         unsigned char *stage = smem + st * Cfg::kStage;
         tc::mbar_arrive_expect_tx(&full[st], X3 ? Cfg::kA + 2 * Cfg::kX : Cfg::kA + Cfg::kX);
-        tc::tma_load_2d(stage, &tmap_a, it * kKStage, (int32_t)row0, &full[st]);
-        tc::tma_load_2d(stage + Cfg::kA, &tmap_xt, it * kKStage, 0, &full[st]);
-        if (X3) tc::tma_load_2d(stage + kHalf + Cfg::kA, &tmap_xl, it * kKStage, 0, &full[st]);
+        const int32_t kx = (int32_t)(k0 + (int64_t)it * kKStage);
+        tc::tma_load_2d(stage, &tmap_a, kx, (int32_t)row0, &full[st]);
+        tc::tma_load_2d(stage + Cfg::kA, &tmap_xt, kx, 0, &full[st]);
+        if (X3) tc::tma_load_2d(stage + kHalf + Cfg::kA, &tmap_xl, kx, 0, &full[st]);
         ++issued;
       }
       for (int it = issued > kS ? issued - kS : 0; it < issued; ++it)
@@ -564,8 +570,8 @@ __global__ void __launch_bounds__(kAnThreads, 1) tc_an_kernel(const __grid_const
           if (X3) {
             const uint64_t al = tc::smem_desc(a_addr + kHalf + kk * 32, 16, 1024, tc::kSwizzle128B);
             const uint64_t xl = tc::smem_desc(x_addr + kHalf + kk * 32, 16, 1024, tc::kSwizzle128B);
-            tc::mma_tf32(tmem, ah, xl, idesc, 1u);
-            tc::mma_tf32(tmem, al, xh, idesc, 1u);
+            tc::mma_tf32(tmem + NPAD, ah, xl, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+            tc::mma_tf32(tmem + NPAD, al, xh, idesc, 1u);
           }
         }
         tc::mma_commit(&empty[st]);
@@ -601,7 +607,19 @@ __global__ void __launch_bounds__(kAnThreads, 1) tc_an_kernel(const __grid_const
 #pragma unroll 1
         for (int c0 = 0; c0 < NPAD; c0 += 32) {
           float v[32];
-          tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+          if (num_it > 0) {
+            tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+            if (X3) {
+              // main chain + cross terms, added with round-to-nearest
+              float w[32];
+              tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(NPAD + c0), w);
+#pragma unroll
+              for (int i = 0; i < 32; ++i) v[i] += w[i];
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = 0.f;   // an empty column range accumulated nothing
+          }
           if (row < m) {
 #pragma unroll
             for (int i = 0; i < 32; ++i)
@@ -659,7 +677,8 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
   const int64_t k_begin = (int64_t)blockIdx.z * rows_per_split;
   const int64_t k_end = min(m, k_begin + rows_per_split);
   const int num_it = k_end > k_begin ? (int)((k_end - k_begin + kKStage - 1) / kKStage) : 0;
-  constexpr uint32_t kCols = MT * NC;
+  // X3: the cross terms accumulate in a second set of accumulators (columns MT NC .. 2 MT NC - 1)
+  constexpr uint32_t kCols = (X3 ? 2 : 1) * MT * NC;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStgStages; ++i) {
@@ -738,8 +757,8 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
               const uint64_t xl =
                   tc::smem_desc(base + Cfg::kHalf + mt * kOmegaBytes + kk * 32, 16, 1024, tc::kSwizzle128B);
               const uint64_t al = tc::smem_desc(b_addr + Cfg::kHalf + kk * 32, 16, 1024, tc::kSwizzle128B);
-              tc::mma_tf32(tmem + mt * NC, xh, al, idesc, 1u);
-              tc::mma_tf32(tmem + mt * NC, xl, ah, idesc, 1u);
+              tc::mma_tf32(tmem + (MT + mt) * NC, xh, al, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+              tc::mma_tf32(tmem + (MT + mt) * NC, xl, ah, idesc, 1u);
             }
           }
         tc::mma_commit(&empty[st]);
@@ -801,6 +820,12 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
         float v[32];
         if (num_it > 0) {
           tc::tmem_ld32(tmem + (uint32_t)(et * NC) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+          if (X3) {
+            float w[32];
+            tc::tmem_ld32(tmem + (uint32_t)((MT + et) * NC) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, w);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] += w[i];
+          }
         } else {
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = 0.f;
@@ -846,11 +871,25 @@ __global__ void transpose32_kernel(const float *__restrict__ in, int64_t rows, i
   }
 }
 
+// Longest reduction one tensor-memory accumulator takes in the 3xTF32 form.  The tensor core adds each k-step
+// into its FP32 accumulator without round-to-nearest, so the rounding error grows with the number of k-steps
+// rather than with its square root; capping every chain at 4096 terms (512 k-steps) keeps it near 3e-5 relative,
+// and the chains are then summed with ordinary FP32 adds.  The single-TF32 form, whose operand rounding is
+// coarser, takes whole reductions.
+constexpr int64_t kX3Chain = 4096;
+
 // Column tile of W = X^T A: 128 columns in the 3xTF32 form (both operand halves must fit), 256 otherwise.
 int at_cols(bool x3) { return x3 ? 128 : 256; }
 
 int at_splits(int64_t m, int64_t n, bool x3, int num_sms) {
-  return tc_splits(m, (n + at_cols(x3) - 1) / at_cols(x3), num_sms);
+  int sp = tc_splits(m, (n + at_cols(x3) - 1) / at_cols(x3), num_sms);
+  // 3xTF32: no accumulator chain longer than kX3Chain rows of A (each split's rows are rounded up to whole
+  // 32-row stages, so aim below the cap)
+  if (x3) {
+    const int64_t need = (m + kX3Chain - 32 - 1) / (kX3Chain - 32);
+    if (sp < need) sp = (int)need;
+  }
+  return sp;
 }
 
 int64_t xt_ld(int64_t rows) { return (rows + 3) / 4 * 4; }   // 16-byte row pitch for TMA
@@ -866,41 +905,53 @@ __global__ void split_tf32_kernel(float *Xt, int64_t rows, int64_t cols, int64_t
   }
 }
 
+int an_splits(int64_t n, bool x3) { return x3 ? (int)((n + kX3Chain - 1) / kX3Chain) : 1; }
+
 template <int NP, bool X3>
 int an_launch(rmc_ctx *ctx, const CUtensorMap &ma, const CUtensorMap &mx, const CUtensorMap &ml, int64_t m,
-              int64_t n, int64_t l, float *Y, int64_t ldy) {
+              int64_t n, int64_t l, float *Y, int64_t ldy, int splits) {
   const size_t smem = AnCfg<NP, X3>::kSmem;
   RMC_TRY_CUDA(cudaFuncSetAttribute(tc_an_kernel<NP, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  tc_an_kernel<NP, X3><<<(unsigned)((m + 127) / 128), kAnThreads, smem, ctx->stream>>>(ma, mx, ml, m, n, l, Y, ldy,
-                                                                                      ctx->d_status);
+  int64_t per = (n + splits - 1) / splits;
+  per = (per + kKStage - 1) / kKStage * kKStage;
+  tc_an_kernel<NP, X3><<<dim3((unsigned)((m + 127) / 128), (unsigned)splits), kAnThreads, smem, ctx->stream>>>(
+      ma, mx, ml, m, n, l, Y, ldy, per, ctx->d_status);
   return RMC_OK;
 }
 
-// Launch Y = A X with X^T (l x n) given (X3: Xt holds the heads, Xl the remainders); l <= 256.
+// Launch Y = A X with X^T (l x n) given (X3: Xt holds the heads, Xl the remainders); l <= 256.  With more
+// than one K split the partial products go to part (splits x m x l) and are summed into Y in split order.
 int launch_an_t(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *Xt, const float *Xl,
-                int64_t l, int64_t ldxt, float *Y, int64_t ldy, bool x3) {
+                int64_t l, int64_t ldxt, float *Y, int64_t ldy, bool x3, float *part) {
+  const int splits = an_splits(n, x3);
   CUtensorMap ma, mx, ml;
   const int npad = l <= 32 ? 32 : l <= 64 ? 64 : l <= 128 ? 128 : 256;
   RMC_TRY(make_tmap(&ma, A, m, n, lda, 128));
   RMC_TRY(make_tmap(&mx, Xt, l, n, ldxt, npad));
   if (x3) RMC_TRY(make_tmap(&ml, Xl, l, n, ldxt, npad));
   else ml = mx;
+  float *outp = splits > 1 ? part : Y;
+  const int64_t ldo = splits > 1 ? l : ldy;
   {
     RmcProf prof(ctx, RMC_K_MATMUL_AN);
     int rc = RMC_OK;
     switch (npad * 2 + (x3 ? 1 : 0)) {
-      case 64: rc = an_launch<32, false>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
-      case 65: rc = an_launch<32, true>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
-      case 128: rc = an_launch<64, false>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
-      case 129: rc = an_launch<64, true>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
-      case 256: rc = an_launch<128, false>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
-      case 257: rc = an_launch<128, true>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
-      case 512: rc = an_launch<256, false>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
-      default: rc = an_launch<256, true>(ctx, ma, mx, ml, m, n, l, Y, ldy); break;
+      case 64: rc = an_launch<32, false>(ctx, ma, mx, ml, m, n, l, outp, ldo, splits); break;
+      case 65: rc = an_launch<32, true>(ctx, ma, mx, ml, m, n, l, outp, ldo, splits); break;
+      case 128: rc = an_launch<64, false>(ctx, ma, mx, ml, m, n, l, outp, ldo, splits); break;
+      case 129: rc = an_launch<64, true>(ctx, ma, mx, ml, m, n, l, outp, ldo, splits); break;
+      case 256: rc = an_launch<128, false>(ctx, ma, mx, ml, m, n, l, outp, ldo, splits); break;
+      case 257: rc = an_launch<128, true>(ctx, ma, mx, ml, m, n, l, outp, ldo, splits); break;
+      case 512: rc = an_launch<256, false>(ctx, ma, mx, ml, m, n, l, outp, ldo, splits); break;
+      default: rc = an_launch<256, true>(ctx, ma, mx, ml, m, n, l, outp, ldo, splits); break;
     }
     RMC_TRY(rc);
   }
   rmc_note_launch();
+  if (splits > 1) {
+    sum_parts_kernel<<<rmc_blocks(m * l, 256, 8192), 256, 0, ctx->stream>>>(part, splits, m, l, Y, ldy);
+    rmc_note_launch();
+  }
   RMC_LAUNCH_CHECK();
   return RMC_OK;
 }
@@ -953,6 +1004,7 @@ size_t rmc_tc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, bool x3, int
   w.take<float>((size_t)l * ld);
   if (x3) w.take<float>((size_t)l * ld);
   if (which == 1) w.take<float>((size_t)at_splits(m, n, x3, num_sms) * l * n);
+  else if (an_splits(n, x3) > 1) w.take<float>((size_t)an_splits(n, x3) * m * l);
   return w.off;
 }
 
@@ -963,6 +1015,7 @@ int rmc_tc_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t
   const int64_t ld = xt_ld(n);
   float *Xt = w.take<float>((size_t)l * ld);
   float *Xl = x3 ? w.take<float>((size_t)l * ld) : nullptr;
+  float *part = an_splits(n, x3) > 1 ? w.take<float>((size_t)an_splits(n, x3) * m * l) : nullptr;
   dim3 grid((unsigned)((l + 31) / 32), (unsigned)((n + 31) / 32));
   transpose32_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(X, n, l, ldx, Xt, ld);
   rmc_note_launch();
@@ -970,7 +1023,7 @@ int rmc_tc_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t
     split_tf32_kernel<<<rmc_blocks(l * n, 256, 4096), 256, 0, ctx->stream>>>(Xt, l, n, ld, Xl);
     rmc_note_launch();
   }
-  return launch_an_t(ctx, A, m, n, lda, Xt, Xl, l, ld, Y, ldy, x3);
+  return launch_an_t(ctx, A, m, n, lda, Xt, Xl, l, ld, Y, ldy, x3, part);
 }
 
 int rmc_tc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
