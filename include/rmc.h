@@ -23,13 +23,19 @@
  * ------------------------------------------------------------------------------------------
  *  Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  key = (seed mod 2^32, seed div 2^32);
  *  counter = (index mod 2^32, index div 2^32, stream, instance).  u(w) = ((w >> 9) + 1/2) * 2^-23.
- *   stream 0  Gaussian entries.  Entry (i, j) of a rows x cols matrix uses block index
+ *   stream 0  Gaussian entries of the range finder's test matrices (rmc_rsvd, rmc_block_lanczos,
+ *             rmc_gaussian_matrix).  Entry (i, j) of a rows x cols matrix uses block index
  *             i * ceil(cols/4) + j/4; words (0,1) -> columns 4t, 4t+1 and words (2,3) -> 4t+2, 4t+3 by
  *             Box-Muller: r = sqrt(-2 ln u(w_a)), (r cos 2 pi u(w_b), r sin 2 pi u(w_b)).
  *   stream 1  SRHT row sign of row i: -1 if bit 31 of word 0 of block i is set, else +1.
  *   stream 2  count-sketch row i: bucket h(i) = (word0 * s) >> 32, sign g(i) = -1 if bit 31 of word 1.
  *   stream 3  SRHT sample key of index j: (word0 << 32) | word1 of block j; the sample is the s indices
  *             with the smallest keys (ties to the smaller index), in ascending order.
+ *   stream 4  Gaussian SKETCHING matrix G (m x s) of RMC_GAUSSIAN.  Entry (i, j) uses block index
+ *             i * ceil(s/8) + j/8; the 16-bit halves of word w (low, high) are the pair of columns 8b + 2w,
+ *             8b + 2w + 1: with u16(h) = (h + 1/2) * 2^-16, r = sqrt(-2 ln u16(low)),
+ *             (r cos 2 pi u16(high), r sin 2 pi u16(high)).  Eight normals per block: half the Philox work of
+ *             stream 0 per entry; the uniforms' 2^-16 steps are finer than TF32 operand rounding (2^-11).
  *  Hashes, signs and sample indices are bit-identical to the oracle's; Gaussian entries agree to FP32
  *  rounding of log/sqrt/sin/cos.
  */
@@ -349,6 +355,13 @@ int rmc_profile_end(rmc_ctx *ctx);
  * argument), RMC_ECUDA. */
 int rmc_profile_reference(rmc_ctx *ctx);
 int rmc_profile_spans(rmc_ctx *ctx, int tag, double *start_ms, double *stop_ms, int max, int *count);
+
+/* Test hook for the delivery of device-side timeouts: enqueue one kernel whose bounded wait on a flag that
+ * nothing sets runs out after limit_ns (at most 1 s), reports RMC_ETIMEOUT to the context's status word and
+ * returns -- the same path every bounded wait of the library takes (mbarrier waits of the tensor-core kernels,
+ * the batch ring).  The next rmc_sync returns RMC_ETIMEOUT and clears it; the context stays usable.
+ * Errors: RMC_EINVAL (NULL context, limit above 1 s), RMC_ENOMEM, RMC_ECUDA. */
+int rmc_debug_wait_timeout(rmc_ctx *ctx, uint64_t limit_ns);
 
 /* Number of kernels this library has launched in the process so far (all contexts). */
 int rmc_launch_counter(uint64_t *launches);

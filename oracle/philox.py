@@ -18,8 +18,9 @@ Philox4x32-10, as published:
 
 Stream layout (one definition shared with the CUDA side through the library's public header):
   counter = (index mod 2^32, index div 2^32, stream, instance), key = (seed mod 2^32, seed div 2^32).
-  stream 0: Gaussian entries, stream 1: SRHT row signs, stream 2: count-sketch bucket and sign,
-  stream 3: SRHT sample keys.  Streams 8 and up are free for test data.
+  stream 0: Gaussian entries (test matrices of the range finder), stream 1: SRHT row signs, stream 2:
+  count-sketch bucket and sign, stream 3: SRHT sample keys, stream 4: entries of the Gaussian sketching matrix
+  (eight per block, from 16-bit uniforms).  Streams 8 and up are free for test data.
 """
 import numpy as np
 
@@ -33,6 +34,7 @@ STREAM_GAUSSIAN = 0
 STREAM_SRHT_SIGN = 1
 STREAM_COUNTSKETCH = 2
 STREAM_SRHT_KEY = 3
+STREAM_GAUSS_SKETCH = 4
 
 
 def philox4x32_10(counters, seed):
@@ -140,3 +142,39 @@ def srht_sample(seed, N, s, instance=0):
     keys = srht_keys(seed, N, instance)
     order = np.lexsort((np.arange(N), keys))      # primary: key, secondary: index
     return np.sort(order[:s])
+
+
+def unit_interval16(half):
+    """Map a 16-bit value to (0, 1): (half + 1/2) * 2^-16 (exact in FP32 and FP64)."""
+    return (np.asarray(half, dtype=np.float64) + 0.5) * 2.0 ** -16
+
+
+def sketch_gaussian_matrix(seed, rows, cols, instance=0, col_subset=None):
+    """The entries of the Gaussian sketching matrix G (rows x cols) of Sec. 3.2.1, from stream 4, in FP64.
+
+    Entry (i, j) comes from the Philox block at index i * ceil(cols / 8) + j // 8.  Its four words give eight
+    16-bit halves, h[2w] = low half and h[2w + 1] = high half of word w; pair t = 0..3 of halves gives columns
+    8b + 2t and 8b + 2t + 1 by Box-Muller on u = (h + 1/2) 2^-16: r = sqrt(-2 ln u(h[2t])),
+    (r cos 2 pi u(h[2t+1]), r sin 2 pi u(h[2t+1])).  Eight normals per block instead of four (half the Philox
+    work per entry); the uniforms' 2^-16 resolution is finer than the 2^-11 of the TF32 operands the sketch
+    feeds, and |G_ij| <= sqrt(-2 ln 2^-17) ~ 4.85.
+    ``col_subset`` restricts the returned columns (every row is still drawn).
+    """
+    groups = (cols + 7) // 8
+    if col_subset is None:
+        col_subset = np.arange(cols)
+    col_subset = np.asarray(col_subset, dtype=np.int64)
+    need = np.unique(col_subset // 8)
+    idx = (np.arange(rows, dtype=np.uint64)[:, None] * np.uint64(groups) + need.astype(np.uint64)[None, :]).ravel()
+    w = draw(idx, STREAM_GAUSS_SKETCH, seed, instance).astype(np.uint64).reshape(rows, need.size, 4)
+    halves = np.empty((rows, need.size, 8), dtype=np.uint64)
+    halves[..., 0::2] = w & np.uint64(0xFFFF)
+    halves[..., 1::2] = w >> np.uint64(16)
+    out = np.empty((rows, need.size, 8))
+    for t in range(4):
+        r = np.sqrt(-2.0 * np.log(unit_interval16(halves[..., 2 * t])))
+        ang = 2.0 * np.pi * unit_interval16(halves[..., 2 * t + 1])
+        out[..., 2 * t] = r * np.cos(ang)
+        out[..., 2 * t + 1] = r * np.sin(ang)
+    pos = np.searchsorted(need, col_subset // 8)
+    return out[:, pos, col_subset % 8]

@@ -23,22 +23,23 @@ def next_pow2(m):
 # ---------------------------------------------------------------- Gaussian projection (Sec. 3.2.1)
 
 def gaussian_sketch(A, s, seed, instance=0):
-    """C = S^T A with S = G / sqrt(s), G an m x s matrix of iid N(0, 1) entries (Sec. 3.2.1)."""
+    """C = S^T A with S = G / sqrt(s), G an m x s matrix of iid N(0, 1) entries (Sec. 3.2.1), drawn from the
+    sketch stream (philox.sketch_gaussian_matrix)."""
     A = np.asarray(A, dtype=np.float64)
-    G = philox.gaussian_matrix(seed, A.shape[0], s, instance)
+    G = philox.sketch_gaussian_matrix(seed, A.shape[0], s, instance)
     return (G.T @ A) / np.sqrt(s)
 
 
 def gaussian_sketch_rows(A, s, seed, rows, instance=0):
     """Selected rows of the Gaussian sketch, for matrices too large to sketch whole on the CPU."""
     A = np.asarray(A, dtype=np.float64)
-    G = philox.gaussian_matrix(seed, A.shape[0], s, instance, col_subset=np.asarray(rows))
+    G = philox.sketch_gaussian_matrix(seed, A.shape[0], s, instance, col_subset=np.asarray(rows))
     return (G.T @ A) / np.sqrt(s)
 
 
 def gaussian_S(m, s, seed, instance=0):
     """The explicit m x s Gaussian sketching matrix S = G / sqrt(s)."""
-    return philox.gaussian_matrix(seed, m, s, instance) / np.sqrt(s)
+    return philox.sketch_gaussian_matrix(seed, m, s, instance) / np.sqrt(s)
 
 
 # ---------------------------------------------------------------- SRHT (Sec. 3.2.2)

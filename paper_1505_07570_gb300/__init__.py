@@ -55,6 +55,7 @@ _SIGS.update({
     "rmc_profile_spans": [_p, _int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _int,
                           ctypes.POINTER(_int)],
     "rmc_launch_counter": [ctypes.POINTER(_u64)],
+    "rmc_debug_wait_timeout": [_p, _u64],
     "rmc_countsketch_noalloc": [_p, _p, _i64, _i64, _i64, _i64, _u64, _p, _i64],
     "rmc_lsr_precise": [_p, _p, _i64, _i64, _i64, _p, _i64, _int, _u64, _int, ctypes.c_double, _int,
                         ctypes.c_double, _p, _p],

@@ -365,6 +365,40 @@ int rmc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t ld
 
 }  // extern "C"
 
+// ------------------------------------------------------------------------------------ timeout delivery
+
+namespace {
+
+// One thread polls a flag that nothing sets, with the same kind of bound as every wait in the library (the
+// global nanosecond timer), then reports RMC_ETIMEOUT and returns: no trap, the context stays usable.
+__global__ void wait_never_set_kernel(const volatile int *flag, uint64_t limit_ns, int *status) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (uint32_t i = 0;; ++i) {
+    if (*flag) return;
+    if ((i & 63) == 0) {
+      uint64_t t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > limit_ns) {
+        rmc_report(status, RMC_ETIMEOUT);
+        return;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" int rmc_debug_wait_timeout(rmc_ctx *ctx, uint64_t limit_ns) {
+  if (!ctx || limit_ns > 1000000000ull) return RMC_EINVAL;
+  RMC_TRY(rmc_ws_reserve(ctx, 256));
+  RMC_TRY_CUDA(cudaMemsetAsync(ctx->ws, 0, sizeof(int), ctx->stream));
+  wait_never_set_kernel<<<1, 1, 0, ctx->stream>>>(static_cast<const int *>(ctx->ws), limit_ns, ctx->d_status);
+  rmc_note_launch();
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
 // ------------------------------------------------------------------------------------ measurement hooks
 
 #include <atomic>

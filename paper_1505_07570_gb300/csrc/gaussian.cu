@@ -1,7 +1,7 @@
 // Gaussian projection (Sec. 3.2.1, row orientation): C = S^T A with S = G / sqrt(s), G (m x s) iid N(0, 1).
 //
-// G is never stored: every tile of G is drawn from Philox where the product needs it (stream 0 layout of
-// rmc.h).  The reduction runs over the m rows of A, so the work is split over row ranges (split-K) and the
+// G is never stored: every tile of G is drawn from Philox where the product needs it (the sketch stream, 4, of
+// rmc.h: eight normals per Philox block from 16-bit uniforms).  The reduction runs over the m rows of A, so the work is split over row ranges (split-K) and the
 // partial products are summed in a fixed order afterwards.
 //   RMC_FP32: CUDA-core FMAs (the plain form), this file.
 //   RMC_TF32: tcgen05 tensor-core kernel (tc_gemm.cu).
@@ -27,15 +27,16 @@ __global__ void __launch_bounds__(256) gauss_simt_kernel(const float *__restrict
   const int64_t s0 = (int64_t)blockIdx.y * TS, c0 = (int64_t)blockIdx.x * TN;
   const int64_t r_begin = (int64_t)blockIdx.z * rows_per_split;
   const int64_t r_end = min(m, r_begin + rows_per_split);
-  const int64_t groups = (s + 3) / 4;
+  const int64_t groups = (s + 7) / 8;
   float acc[4][8] = {};
   for (int64_t k0 = r_begin; k0 < r_end; k0 += TK) {
-    {  // G tile: one Philox block (4 normals) per thread
-      const int kk = tid >> 4, g = tid & 15;
+    if (tid < TK * TS / 8) {  // G tile: one Philox block (8 normals) per thread of the first 128
+      const int kk = tid >> 3, g = tid & 7;
       const int64_t row = k0 + kk;
-      float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (row < r_end) z = gaussian4(seed, instance, (uint64_t)(row * groups + s0 / 4 + g));
-      *reinterpret_cast<float4 *>(&Os[kk][4 * g]) = z;
+      float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (row < r_end) gaussian8(seed, instance, (uint64_t)(row * groups + s0 / 8 + g), z);
+      *reinterpret_cast<float4 *>(&Os[kk][8 * g]) = make_float4(z[0], z[1], z[2], z[3]);
+      *reinterpret_cast<float4 *>(&Os[kk][8 * g + 4]) = make_float4(z[4], z[5], z[6], z[7]);
     }
     for (int e = tid; e < TK * TN; e += 256) {
       const int kk = e / TN, c = e % TN;

@@ -10,7 +10,13 @@ constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;  // Weyl key increments
 constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 
-enum : uint32_t { kStreamGaussian = 0, kStreamSrhtSign = 1, kStreamCountSketch = 2, kStreamSrhtKey = 3 };
+enum : uint32_t {
+  kStreamGaussian = 0,       // range-finder test matrices (four normals per block, 32-bit uniforms)
+  kStreamSrhtSign = 1,
+  kStreamCountSketch = 2,
+  kStreamSrhtKey = 3,
+  kStreamGaussSketch = 4     // Gaussian sketching matrix (eight normals per block, 16-bit uniforms)
+};
 
 // Ten rounds of the Philox S-P network on one 128-bit counter block.
 __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
@@ -43,6 +49,26 @@ __device__ __forceinline__ float2 box_muller(uint32_t wa, uint32_t wb) {
   float sn, cs;
   sincospif(2.0f * unit_f32(wb), &sn, &cs);  // 2 u_b is exact, so the angle carries no extra rounding
   return make_float2(r * cs, r * sn);
+}
+
+// (h + 1/2) * 2^-16 for a 16-bit h: the bit pattern of 1 + h 2^-16 minus (1 - 2^-17), exact in FP32.
+__device__ __forceinline__ float unit16_f32(uint32_t h) {
+  return __fsub_rn(__uint_as_float(0x3F800000u | (h << 7)), 0.9999923706054688f);
+}
+
+// The eight normals of sketch block `index` (columns 8b .. 8b+7 of one row of the Gaussian sketching matrix):
+// halves (lo, hi) of word w form the Box-Muller pair of columns 8b + 2w, 8b + 2w + 1.
+__device__ __forceinline__ void gaussian8(uint64_t seed, uint32_t instance, uint64_t index, float (&z)[8]) {
+  const uint4 w = philox_block(seed, kStreamGaussSketch, instance, index);
+  const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const float r = sqrtf(-2.0f * logf(unit16_f32(ws[t] & 0xFFFFu)));
+    float sn, cs;
+    sincospif(2.0f * unit16_f32(ws[t] >> 16), &sn, &cs);   // 2 u is exact: the angle carries no extra rounding
+    z[2 * t] = r * cs;
+    z[2 * t + 1] = r * sn;
+  }
 }
 
 // The four normals of Gaussian block `index` (columns 4t .. 4t+3 of one row).

@@ -6,9 +6,9 @@
 // range of rows of A):
 //   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators) and issues tcgen05.mma
 //               (M=128, N=256, K=8) from one lane
-//   warps 4-11  per stage of 32 rows: draw G^T (32 x 256) from Philox straight into the K-major, 128-byte-
-//               swizzled operand layout, transpose the 32 x 256 tile of A (read one stage ahead with 16-byte
-//               loads) into the same K-major layout, and fold the b column in with FP32 FMAs
+//   warps 2-3   transpose the 32 x 256 tile of A (staged by TMA) into the K-major, 128-byte-swizzled layout
+//   warps 4-19  per stage of 32 rows: draw G^T (32 x 256) from Philox (the sketch stream: eight normals per
+//               block) straight into the same K-major layout, and fold the b column in with FP32 FMAs
 //   warps 4-7   epilogue: tcgen05.ld of the accumulators, written as this row range's partial sum
 // Both sketch tiles share each transposed A tile.  Three stages of 64 KB are in flight; every wait is bounded
 // (RMC_ETIMEOUT after one second).
@@ -64,10 +64,11 @@ __device__ __forceinline__ float cos_ftz(float x) {
 // Box-Muller with the hardware approximations: the operands are rounded to TF32 (10-bit mantissa) before they
 // reach the tensor cores, far coarser than these approximations' ~2^-21 error.  -2 ln u = (-2 ln 2) log2 u; the
 // angle is shifted by -pi into (-pi, pi) and both outputs negated to compensate.
-__device__ __forceinline__ float2 box_muller_fast(uint32_t wa, uint32_t wb) {
-  const float t = -1.3862943611198906f * lg2_ftz(unit_f32(wa));
+// The Box-Muller pair of one word of the sketch stream (its low and high 16-bit halves).
+__device__ __forceinline__ float2 box_muller16_fast(uint32_t w) {
+  const float t = -1.3862943611198906f * lg2_ftz(unit16_f32(w & 0xFFFFu));
   const float r = t * rsqrt_ftz(t);
-  const float a = 6.283185307179586f * (unit_f32(wb) - 0.5f);
+  const float a = 6.283185307179586f * (unit16_f32(w >> 16) - 0.5f);
   return make_float2(-r * cos_ftz(a), -r * sin_ftz(a));
 }
 
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
   const int64_t k_begin = (int64_t)blockIdx.z * args.rows_per_split;
   const int64_t k_end = min(args.m, k_begin + args.rows_per_split);
   const int num_it = k_end > k_begin ? (int)((k_end - k_begin + kKStage - 1) / kKStage) : 0;
-  const int64_t groups = (args.s + 3) / 4;
+  const int64_t groups = (args.s + 7) / 8;     // Philox blocks per row of the sketch stream
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStgStages; ++i) {
@@ -233,59 +234,68 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
     }
   } else {
     // ---------------------------------------------------------------- G^T producers (+ b column)
+    // Thread = (K-row pair kp: rows 2 kp, 2 kp + 1 of the stage; group of 8 sketch rows g8 of tile mt).  Each
+    // K-row takes one Philox block of the sketch stream (8 normals = the 8 sketch rows of the group), and each
+    // sketch row's two values fill one 8-byte half of a 16-byte K-chunk of the K-major tile.
     const int rw = warp - kRngWarp0;                        // 0..15
     const int mt = rw >> 3;                                 // sketch tile of this warp
-    const int kq = lane & 7;                                // 16-byte chunk along K: rows 4kq .. 4kq+3
-    const int g = 4 * (rw & 7) + (lane >> 3);               // group of 4 sketch rows: 4g .. 4g+3
+    const int kp = lane & 15;                               // K-row pair: 16-byte chunk kp / 2, half kp % 2
+    const int g8 = 2 * (rw & 7) + (lane >> 4);              // sketch rows 8 g8 .. 8 g8 + 7 of the tile
     const bool with_b = args.b != nullptr && blockIdx.y == 0;
-    const uint64_t gidx = (uint64_t)((s0 + mt * kM) / 4 + g);
-    float bacc[4] = {0.f, 0.f, 0.f, 0.f};
+    const uint64_t gidx = (uint64_t)((s0 + mt * kM) / 8 + g8);
+    float bacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int it = 0; it < num_it; ++it) {
       const int st = it % kStages;
-      const int64_t row0 = k_begin + (int64_t)it * kKStage + 4 * kq;
-      float z[4][4];
+      const int64_t row0 = k_begin + (int64_t)it * kKStage + 2 * kp;
+      float z[2][8];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
+      for (int t = 0; t < 2; ++t) {
         const int64_t row = row0 + t;
         if (row < k_end) {
-          const uint4 w = philox_block(args.seed, kStreamGaussian, args.instance, (uint64_t)row * groups + gidx);
-          const float2 a = box_muller_fast(w.x, w.y), c = box_muller_fast(w.z, w.w);
-          z[t][0] = a.x; z[t][1] = a.y; z[t][2] = c.x; z[t][3] = c.y;
+          const uint4 w = philox_block(args.seed, kStreamGaussSketch, args.instance, (uint64_t)row * groups + gidx);
+          const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 p = box_muller16_fast(ws[q]);
+            z[t][2 * q] = p.x;
+            z[t][2 * q + 1] = p.y;
+          }
         } else {
-          z[t][0] = z[t][1] = z[t][2] = z[t][3] = 0.f;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) z[t][q] = 0.f;
         }
       }
       if (with_b) {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < 2; ++t) {
           const float bv = (row0 + t < k_end) ? __ldg(args.b + row0 + t) : 0.f;
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj) bacc[jj] = fmaf(z[t][jj], bv, bacc[jj]);
+          for (int jj = 0; jj < 8; ++jj) bacc[jj] = fmaf(z[t][jj], bv, bacc[jj]);
         }
       }
       if (!warp_wait(&empty[st], ((it / kStages) & 1) ^ 1, abort_flag, args.status)) break;
       unsigned char *otile = operands + st * kStageBytes + mt * kOmegaBytes;
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        const int r = 4 * g + jj;
-        *reinterpret_cast<float4 *>(otile + swz_off(r, kq)) =
-            make_float4(to_tf32(z[0][jj]), to_tf32(z[1][jj]), to_tf32(z[2][jj]), to_tf32(z[3][jj]));
+      for (int jj = 0; jj < 8; ++jj) {
+        const int r = 8 * g8 + jj;
+        *reinterpret_cast<float2 *>(otile + swz_off(r, kp >> 1) + 8 * (kp & 1)) =
+            make_float2(to_tf32(z[0][jj]), to_tf32(z[1][jj]));
       }
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&full[st]);
     }
     if (with_b) {
-      // sum over the 8 lanes (kq) that share a group, then write the b column of the partial
+      // sum over the 16 lanes (K-row pairs) that share a group, then write the b column of the partial
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj)
+      for (int jj = 0; jj < 8; ++jj)
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1) bacc[jj] += __shfl_xor_sync(0xffffffffu, bacc[jj], o);
-      if (kq == 0) {
+        for (int o = 1; o < 16; o <<= 1) bacc[jj] += __shfl_xor_sync(0xffffffffu, bacc[jj], o);
+      if (kp == 0) {
         float *pb = args.part + ((int64_t)blockIdx.z * args.s) * args.ntot;
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int64_t srow = s0 + mt * kM + 4 * g + jj;
+        for (int jj = 0; jj < 8; ++jj) {
+          const int64_t srow = s0 + mt * kM + 8 * g8 + jj;
           if (srow < args.s) pb[srow * args.ntot + args.n] = bacc[jj];
         }
       }
@@ -640,6 +650,8 @@ __global__ void __launch_bounds__(kAnThreads, 1) tc_an_kernel(const __grid_const
 // W = X^T A over a row range of A: A_op = X^T tiles (MT x 128 rows of l, K-major via TMA), B_op = A tile
 // (NC columns) staged by TMA and transposed to K-major by warps 2-3.  Partial sums per row range.  X3: the
 // X^T remainder arrives by a second TMA, the transposers write the A tile's head and remainder.
+constexpr int kAtTrans = 4;       // transposer warps of tc_at_kernel (warps 2-5; 4 and 5 join the epilogue)
+
 template <int MT, bool X3>
 struct AtCfg {
   static constexpr int NC = X3 ? 128 : 256;            // columns of A per CTA (the MMA's N)
@@ -683,10 +695,10 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStgStages; ++i) {
       tc::mbar_init(&stg_full[i], 1);
-      tc::mbar_init(&stg_empty[i], kTransWarps);
+      tc::mbar_init(&stg_empty[i], kAtTrans);
     }
     for (int i = 0; i < kStages; ++i) {
-      tc::mbar_init(&full[i], kTransWarps + 1);      // two transposer warps + the X^T TMA arrival
+      tc::mbar_init(&full[i], kAtTrans + 1);         // the transposer warps + the X^T TMA arrival
       tc::mbar_init(&empty[i], 1);
     }
     tc::mbar_init(done, 1);
@@ -765,10 +777,13 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
       }
       tc::mma_commit(done);
     }
-  } else if (warp < 4) {
+  } else {
+   if (warp < 2 + kAtTrans) {
     // transposers: staging (row-major, swizzled) -> K-major B tile (see the Gaussian kernel); X3 also writes the
-    // remainder tile.  Unit (kq, cq): rows 4kq..4kq+3 x columns 4cq..4cq+3, cq < NC/4.
-    const int tl = (warp - kTransWarp0) * 32 + lane;
+    // remainder tile.  Unit (kq, cq): rows 4kq..4kq+3 x columns 4cq..4cq+3, cq < NC/4; lane lq of a group of
+    // eight takes kq = lq and cq = (d + lq) mod NC/4, so each group's reads and writes hit 8 distinct 16-byte
+    // bank groups.
+    const int tl = (warp - 2) * 32 + lane;
     const int lq = tl & 7, grp = tl >> 3;
     for (int it = 0; it < num_it; ++it) {
       const int st = it % kStages, sst = it % kStgStages;
@@ -777,7 +792,7 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
       const unsigned char *src = staging + sst * Cfg::kStg;
       unsigned char *btile = operands + st * Cfg::kStage + Cfg::kXt;
 #pragma unroll 2
-      for (int d = grp; d < NC / 4; d += 8) {
+      for (int d = grp; d < NC / 4; d += 4 * kAtTrans) {
         const int kq = lq, cq = (d + lq) & (NC / 4 - 1);
         const int atom = cq >> 3, cc = cq & 7;
         float4 v[4];
@@ -806,7 +821,8 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
         tc::mbar_arrive(&full[st]);
       }
     }
-  } else {
+   }
+   if (warp >= 4) {
     // epilogue: warps 4.. (MT x 4 warps), accumulator et, lane quarter q
     const int ew = warp - 4, et = ew >> 2, q = warp & 3;
     const bool ok = warp_wait(done, 0, abort_flag, status);
@@ -837,6 +853,7 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
         }
       }
     }
+  }
   }
   tc::tc_fence_before();
   __syncthreads();

