@@ -429,7 +429,7 @@ def run_probe(kind):
         if kind == "lsr_precise":
             return rmc.rmc_lsr_precise(A, b, 1024, "countsketch", SEED, max_iters=4, tol=0.0)
         if kind == "rsvd":
-            return rmc.rmc_rsvd(A, 100, 20, 1, SEED, prec="tf32")[1]
+            return rmc.rmc_rsvd(A, 100, 20, 1, SEED, prec=GAUSS_PREC)[1]
         if kind == "rsvd_full":
             return rmc.rmc_rsvd(A, 100, 20, int(os.environ.get("RMC_PROBE_Q", "0")), SEED, prec=GAUSS_PREC)[1]
         if kind == "lanczos_full":

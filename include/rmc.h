@@ -237,13 +237,19 @@ int rmc_srht_sample(rmc_ctx *ctx, uint64_t seed, uint32_t instance, int64_t N, i
 
 /* CholeskyQR2 in place (the qr(., 0) of Algorithm 5.2 and of the Sec. 5.1 listing): Y (m x l, ldy, FP32) is
  * overwritten by Q with orthonormal columns; R (l x l row-major FP64, upper triangular, optional: NULL) gets
- * the factor with Y_in = Q R.  The Gram matrices are accumulated in FP64 and factored in FP64.
- * Requires 1 <= l <= 256, m >= l.  RMC_ENUMERIC at rmc_sync on a non-positive pivot. */
+ * the factor with Y_in = Q R.  Each pass forms the Gram matrix with FP32 products summed in FP64 across 32-row
+ * slices and factors it in FP32, falling back to an FP64 Cholesky on a non-positive pivot; with
+ * RMC_OPT_SMALL_FP64 the products and the Cholesky are FP64.  Requires 1 <= l <= 256, m >= l.  RMC_ENUMERIC at
+ * rmc_sync when the FP64 factorization meets a non-positive pivot too. */
 int rmc_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l, int64_t ldy, double *R);
 
 /* SVD of a short, wide matrix B (l x n, ldb, l <= n, l <= 256) -- the svd(Q^T A, 'econ') step of Algorithm
  * 5.2: B = Ub diag(sigma) Vb^T with Ub l x l (row-major, FP32), sigma[l] descending (FP32) and Vb n x l
- * (ldv, FP32).  Computed as CholeskyQR2 of B^T followed by FP64 one-sided Jacobi on the l x l factor. */
+ * (ldv, FP32).  Computed as CholeskyQR2 of B^T (B^T = Q2 R, the last pass with FP64 Gram products) and a
+ * one-sided Jacobi SVD of R = M diag(sigma) V^T (FP32 rotations, FP64 for l <= 32 or with RMC_OPT_SMALL_FP64):
+ * Vb = Q2 M; Ub = V = R^T M diag(sigma)^-1 (FP64 products) for l up to 240 (120 in FP64), so column j of Ub is
+ * accurate to about eps * sigma_1 / sigma_j (the leading columns, those a k-SVD keeps, to FP32 level); larger l
+ * accumulates the rotations instead. */
 int rmc_svd_wide(rmc_ctx *ctx, const float *B, int64_t l, int64_t n, int64_t ldb, float *Ub,
                  float *sigma, float *Vb, int64_t ldv);
 

@@ -291,33 +291,40 @@ __device__ void load_packed(const double *G, int l, int ldg, float *P, int *base
 
 // CholeskyQR step: factor G (l x l FP64) in FP32, write R (FP64, upper) into G and R^-1 in FP32 (Rinv32).
 // fail[0] = 1 when the FP32 factorization broke down (the FP64 kernels below then take over).
+// X_SMEM: R^-1 is built in shared memory (l x l more floats) and copied out; otherwise in Rinv32 directly.
+template <bool X_SMEM>
 __global__ void __launch_bounds__(512) chol32_inv_kernel(double *G, int l, float *Rinv32, int *fail) {
   extern __shared__ float smem32[];
   int *base = reinterpret_cast<int *>(smem32);
   float *dinv = smem32 + l;
   float *P = smem32 + 2 * l;
+  float *X = X_SMEM ? P + (size_t)l * (l + 1) / 2 : Rinv32;   // X[i * l + c]: thread c's column
   load_packed(G, l, l, P, base);
   const bool ok = chol32_smem(P, base, dinv, l);
   if (threadIdx.x == 0) fail[0] = ok ? 0 : 1;
   if (!ok) return;
   __syncthreads();
   // R^-1, one thread per column c, rows from the bottom: X[i][c] = (delta_ic - sum_{k>i} U[i][k] X[k][c]) / U[i][i].
-  // A column depends only on itself, so no synchronisation; X lives in Rinv32 (the thread's own column).
+  // A column depends only on itself, so no synchronisation (consecutive threads, consecutive banks).
   for (int c = threadIdx.x; c < l; c += blockDim.x) {
-    for (int i = l - 1; i > c; --i) Rinv32[(int64_t)i * l + c] = 0.f;
+    for (int i = l - 1; i > c; --i) X[(int64_t)i * l + c] = 0.f;
     for (int i = c; i >= 0; --i) {
       const int bi = base[i];
       float a0 = (i == c) ? 1.f : 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
       int k = i + 1;
       for (; k + 4 <= c + 1; k += 4) {
-        a0 = fmaf(-P[bi + k], Rinv32[(int64_t)k * l + c], a0);
-        a1 = fmaf(-P[bi + k + 1], Rinv32[(int64_t)(k + 1) * l + c], a1);
-        a2 = fmaf(-P[bi + k + 2], Rinv32[(int64_t)(k + 2) * l + c], a2);
-        a3 = fmaf(-P[bi + k + 3], Rinv32[(int64_t)(k + 3) * l + c], a3);
+        a0 = fmaf(-P[bi + k], X[(int64_t)k * l + c], a0);
+        a1 = fmaf(-P[bi + k + 1], X[(int64_t)(k + 1) * l + c], a1);
+        a2 = fmaf(-P[bi + k + 2], X[(int64_t)(k + 2) * l + c], a2);
+        a3 = fmaf(-P[bi + k + 3], X[(int64_t)(k + 3) * l + c], a3);
       }
-      for (; k <= c; ++k) a0 = fmaf(-P[bi + k], Rinv32[(int64_t)k * l + c], a0);
-      Rinv32[(int64_t)i * l + c] = ((a0 + a1) + (a2 + a3)) * dinv[i];
+      for (; k <= c; ++k) a0 = fmaf(-P[bi + k], X[(int64_t)k * l + c], a0);
+      X[(int64_t)i * l + c] = ((a0 + a1) + (a2 + a3)) * dinv[i];
     }
+  }
+  if (X_SMEM) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < l * l; e += blockDim.x) Rinv32[e] = X[e];
   }
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int i = e / l, j = e % l;
@@ -1258,9 +1265,18 @@ static int launch_factor(rmc_ctx *ctx, double *G, int l, double *Rinv, float *Ri
   if (smem > kMaxPackedBytes || ctx->small_fp64) {
     force_fp64_kernel<<<1, 1, 0, st>>>(&fail[0]);
   } else {
-    if (smem > 48 * 1024)
-      RMC_TRY_CUDA(cudaFuncSetAttribute(chol32_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    chol32_inv_kernel<<<1, 512, smem, st>>>(G, l, Rinv32, fail);
+    const size_t smem_x = smem + sizeof(float) * (size_t)l * l;
+    if (smem_x <= kMaxPackedBytes) {
+      if (smem_x > 48 * 1024)
+        RMC_TRY_CUDA(cudaFuncSetAttribute(chol32_inv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem_x));
+      chol32_inv_kernel<true><<<1, 512, smem_x, st>>>(G, l, Rinv32, fail);
+    } else {
+      if (smem > 48 * 1024)
+        RMC_TRY_CUDA(cudaFuncSetAttribute(chol32_inv_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+      chol32_inv_kernel<false><<<1, 512, smem, st>>>(G, l, Rinv32, fail);
+    }
   }
   RMC_TRY_CUDA(cudaMemsetAsync(&fail[1], 0, sizeof(int), st));
   chol64_fallback_kernel<<<1, 1024, 0, st>>>(G, l, &fail[0], ctx->d_status, &fail[1]);
@@ -1294,7 +1310,11 @@ int rmc_launch_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l_, int64_t ld
   int *fail = w.take<int>(4);
   double *part = reinterpret_cast<double *>(w.take<char>(gram_ws(m, l, ctx->num_sms)));
   for (int pass = 0; pass < passes; ++pass) {
-    RMC_TRY(launch_gram(ctx, Y, m, l, ldy, G, part, fp64_gram || ctx->small_fp64));
+    // FP64 products (fp64_gram) only where they decide the result: the last pass.  An earlier pass only needs a
+    // well-conditioned basis, which the FP32 products (summed in FP64) give; R = R2 R1 is exact up to the FP32
+    // storage of the intermediate basis either way.
+    const bool fp64_products = (fp64_gram && pass == passes - 1) || ctx->small_fp64;
+    RMC_TRY(launch_gram(ctx, Y, m, l, ldy, G, part, fp64_products));
     RMC_TRY(launch_factor(ctx, G, l, Rinv, Rinv32, fail));
     RMC_TRY(launch_rowblock(st, Y, m, l, ldy, Rinv32, l, l, Y, ldy));
     if (R) {

@@ -28,7 +28,10 @@ __global__ void __launch_bounds__(256) gauss_simt_kernel(const float *__restrict
   const int64_t r_begin = (int64_t)blockIdx.z * rows_per_split;
   const int64_t r_end = min(m, r_begin + rows_per_split);
   const int64_t groups = (s + 7) / 8;
-  float acc[4][8] = {};
+  // Blocked summation: acc collects 16 steps (256 rows), then folds into tot, so no FP32 chain is longer than
+  // 256 + rows / 256 terms (a split may span 2^18 rows of a 2^20-row matrix).
+  float acc[4][8] = {}, tot[4][8] = {};
+  int step = 0;
   for (int64_t k0 = r_begin; k0 < r_end; k0 += TK) {
     if (tid < TK * TS / 8) {  // G tile: one Philox block (8 normals) per thread of the first 128
       const int kk = tid >> 3, g = tid & 7;
@@ -62,14 +65,28 @@ __global__ void __launch_bounds__(256) gauss_simt_kernel(const float *__restrict
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(g[i], x[j], acc[i][j]);
     }
     __syncthreads();
+    if (++step == 16) {
+      step = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          tot[i][j] += acc[i][j];
+          acc[i][j] = 0.f;
+        }
+    }
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) tot[i][j] += acc[i][j];
   float *o = part + (int64_t)blockIdx.z * s * ntot;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int64_t r = s0 + 4 * ty + i, c = c0 + tx + 16 * j;
-      if (r < s && c < ntot) o[r * ntot + c] = acc[i][j];
+      if (r < s && c < ntot) o[r * ntot + c] = tot[i][j];
     }
 }
 

@@ -130,7 +130,8 @@ int rmc_launch_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int
                          int64_t l, int64_t ldx, int prec, float *W, int64_t ldw, void *ws);
 size_t rmc_cholqr2_ws(int64_t m, int64_t l, int num_sms);
 // passes = 2: CholeskyQR2; passes = 1: one CholeskyQR pass (a well-conditioned, not orthonormal, basis).
-// fp64_gram: FP64 products in the Gram matrices (else FP32 products, FP64 sums across 32-row slices).
+// fp64_gram: FP64 products in the last pass's Gram matrix (else, and in earlier passes, FP32 products with FP64
+// sums across 32-row slices); RMC_OPT_SMALL_FP64 makes every pass FP64.
 int rmc_launch_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l, int64_t ldy, double *R, void *ws,
                        int passes = 2, bool fp64_gram = false);
 size_t rmc_svd_wide_ws(int64_t l, int64_t n, int num_sms);
