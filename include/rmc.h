@@ -187,8 +187,9 @@ int rmc_block_lanczos(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_
  *   D = Q_D R_D;  Q_D^T L = U_bar diag(sigma_bar) V_bar^T (top k);  C R_D^-1 U_bar diag(sigma_bar) =
  *   U diag(sigma) V_hat^T;  V = V_bar V_hat.
  * Outputs as rmc_rsvd (U m x k, sigma[k] descending, V n x k, the same sign rule).  Requires
- * 1 <= k <= s <= 256, s <= p <= p_cs, s <= n, k <= m.  Errors as rmc_rsvd (RMC_ENUMERIC at rmc_sync when R_D
- * is singular). */
+ * 1 <= k <= s <= 256, s <= p <= p_cs, s <= n, k <= m.  R_D is inverted (the listing's pinv(R_D) for a D of full
+ * column rank, which needs rank(A) >= s); errors as rmc_rsvd, with RMC_ENUMERIC at rmc_sync when D is rank
+ * deficient. */
 int rmc_rsvd_fast(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, int k, int s, int p_cs, int p,
                   uint64_t seed, int prec, float *U, int64_t ldu, float *sigma, float *V, int64_t ldv);
 
@@ -292,6 +293,21 @@ typedef struct rmc_request {
  * Errors: RMC_EINVAL (a request breaks the limits; nothing is enqueued), RMC_ENOMEM, RMC_ECUDA; RMC_ENUMERIC
  * at rmc_sync when a problem's factorization broke down (its outputs are then NaN). */
 int rmc_batch_run(rmc_ctx *ctx, const rmc_request *reqs, int nreq);
+
+/* Autotuned schedule of rmc_batch_run.  The k-SVD problems of a batch fall into 16 tuning classes (n in 1-64,
+ * 65-128, 129-192, 193-256, times l = k + p rounded up to 8, 16, 24, 32); each class has a row-tile height for
+ * the passes over A (0 = as many rows as a ring stage holds, else 32, 64 or 128).  rmc_batch_autotune times
+ * every candidate on up to 256 of the caller's own problems per class (reps timed launches each, after one
+ * warm-up) and keeps the fastest in the context's table, which later rmc_batch_run calls on this context use.
+ * It runs the problems (their outputs are overwritten) and synchronises the stream.  rmc_batch_get_tiles /
+ * rmc_batch_set_tiles read and write the table (count >= 16 entries; entries multiples of 16 in [0, 256]) so it
+ * can be kept between processes.  Different tables change the summation order, not the results beyond FP32
+ * rounding; for a fixed table a problem's result is the same alone or in any mix.
+ * Errors: RMC_EINVAL (bad arguments or requests), RMC_ENOMEM, RMC_ECUDA, and the status of the runs. */
+#define RMC_BATCH_TILE_CLASSES 16
+int rmc_batch_autotune(rmc_ctx *ctx, const rmc_request *reqs, int nreq, int reps);
+int rmc_batch_get_tiles(const rmc_ctx *ctx, int *table, int count);
+int rmc_batch_set_tiles(rmc_ctx *ctx, const int *table, int count);
 
 /* ------------------------------------------------------------------ continuous-batching request server */
 

@@ -520,6 +520,33 @@ def rmc_batch_run(requests):
     _check(lib.rmc_batch_run(context().bind(), arr, len(requests)), "rmc_batch_run")
 
 
+RMC_BATCH_TILE_CLASSES = 16
+lib.rmc_batch_autotune.argtypes = [_p, ctypes.POINTER(rmc_request), _int, _int]
+lib.rmc_batch_autotune.restype = ctypes.c_int
+lib.rmc_batch_get_tiles.argtypes = [_p, ctypes.POINTER(_int), _int]
+lib.rmc_batch_get_tiles.restype = ctypes.c_int
+lib.rmc_batch_set_tiles.argtypes = [_p, ctypes.POINTER(_int), _int]
+lib.rmc_batch_set_tiles.restype = ctypes.c_int
+
+
+def rmc_batch_autotune(requests, reps=3):
+    """Tune the batched kernel's row tiles on these problems (they are run); returns the 16-entry table."""
+    arr = (rmc_request * len(requests))(*requests)
+    _check(lib.rmc_batch_autotune(context().bind(), arr, len(requests), reps), "rmc_batch_autotune")
+    return rmc_batch_get_tiles()
+
+
+def rmc_batch_get_tiles():
+    t = (_int * RMC_BATCH_TILE_CLASSES)()
+    _check(lib.rmc_batch_get_tiles(context().bind(), t, RMC_BATCH_TILE_CLASSES), "rmc_batch_get_tiles")
+    return list(t)
+
+
+def rmc_batch_set_tiles(table):
+    t = (_int * RMC_BATCH_TILE_CLASSES)(*table)
+    _check(lib.rmc_batch_set_tiles(context().bind(), t, RMC_BATCH_TILE_CLASSES), "rmc_batch_set_tiles")
+
+
 class rmc_serve_request(ctypes.Structure):
     """Mirror of the C struct rmc_serve_request."""
     _fields_ = [("req", rmc_request), ("sketch", _int), ("prec", _int)]

@@ -44,6 +44,7 @@ constexpr int64_t kMaxM = int64_t(1) << 24;
 struct BatchItem {
   int kind, k, p, q;
   int m, n, s, vec;   // vec: rows of A start on 16-byte boundaries (16-byte cp.async)
+  int rtile;          // rsvd: cap on the row-tile height (multiple of 16; 0 = as many rows as a stage holds)
   int64_t lda;
   uint64_t seed;
   const float *A, *b;
@@ -546,6 +547,7 @@ __device__ void rsvd_problem(const BatchItem &it, float *sm, Ring &rg, int *flag
   g.dense = it.lda == it.n && (reinterpret_cast<uintptr_t>(it.A) & 15) == 0;
   g.S = g.dense ? g.n : g.nz + 4;
   g.R = min(256, (kStageFloats - 32) / (g.S + LP)) & ~15;  // A span + Y span, each with a 16-float tail
+  if (it.rtile >= 16 && it.rtile < g.R) g.R = it.rtile & ~15;  // the tuned row tile of this problem's class
   g.yoff = g.R * g.S + (g.dense ? 16 : 0);  // where the W pass puts the Y tile in a stage
   g.MB = g.R >> 4;
   g.KB = g.nz >> 3;
@@ -1197,6 +1199,14 @@ static double cost_us(const rmc_request &r) {
   return std::max(bytes / 4.0e4, fma / 1.5e5) + 40.0;
 }
 
+// Tuning class of a k-SVD problem: n class (n in 1-64, 65-128, 129-192, 193-256) x l class (l rounded up to
+// 8, 16, 24 or 32: the kernel's column tile).
+static int tile_class(const rmc_request &r) {
+  const int nc = (int)std::min<int64_t>(3, (r.n - 1) / 64);
+  const int lc = std::min(3, lp_of(r.k + r.p) / 8 - 1);
+  return nc * 4 + lc;
+}
+
 static bool bad_request(const rmc_request &r) {
   if (!r.A || r.m < 1 || r.m > kMaxM || r.n < 1 || r.n > kMaxN || r.lda < r.n) return true;
   if (r.kind == RMC_REQ_LSR) return !r.b || !r.x || r.s < r.n || r.s > kMaxS;
@@ -1280,6 +1290,7 @@ extern "C" int rmc_batch_run(rmc_ctx *ctx, const rmc_request *reqs, int nreq) {
     b.n = (int)r.n;
     b.s = (int)r.s;
     b.vec = ((reinterpret_cast<uintptr_t>(r.A) & 15) == 0 && (r.lda & 3) == 0) ? 1 : 0;
+    b.rtile = (r.kind == RMC_REQ_RSVD) ? ctx->batch_rtile[tile_class(r)] : 0;
     b.lda = r.lda;
     b.seed = r.seed;
     b.A = r.A;
@@ -1317,5 +1328,75 @@ extern "C" int rmc_batch_run(rmc_ctx *ctx, const rmc_request *reqs, int nreq) {
   }
   rmc_note_launch();
   RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
+// ------------------------------------------------------------------------------------------- autotuner
+// The row-tile height of the k-SVD passes trades barrier count (tall tiles) against parallel k-splits and
+// load balance inside a tile (short tiles); the best height depends on n and l.  The tuner times each
+// candidate on the caller's own problems, class by class, and keeps the fastest in the context's table.
+
+extern "C" int rmc_batch_autotune(rmc_ctx *ctx, const rmc_request *reqs, int nreq, int reps) {
+  if (!ctx || nreq < 0 || (nreq > 0 && !reqs) || reps < 1 || reps > 100) return RMC_EINVAL;
+  for (int i = 0; i < nreq; ++i)
+    if (bad_request(reqs[i])) return RMC_EINVAL;
+  constexpr int kCand[] = {0, 32, 64, 128};   // 0: as many rows as a stage holds
+  constexpr int kSample = 256;                // problems per class that are timed
+  std::vector<std::vector<rmc_request>> byclass(kBatchTileClasses);
+  for (int i = 0; i < nreq; ++i)
+    if (reqs[i].kind == RMC_REQ_RSVD && (int)byclass[tile_class(reqs[i])].size() < kSample)
+      byclass[tile_class(reqs[i])].push_back(reqs[i]);
+  cudaEvent_t e0, e1;
+  RMC_TRY_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    (void)cudaGetLastError();
+    return RMC_ECUDA;
+  }
+  int rc = RMC_OK;
+  for (int c = 0; c < kBatchTileClasses && rc == RMC_OK; ++c) {
+    if (byclass[c].empty()) continue;
+    float best = 0.f;
+    int best_tile = 0;
+    bool have = false;
+    for (int cand : kCand) {
+      ctx->batch_rtile[c] = cand;
+      rc = rmc_batch_run(ctx, byclass[c].data(), (int)byclass[c].size());     // warm-up (and workspace)
+      if (rc != RMC_OK) break;
+      if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { rc = RMC_ECUDA; break; }
+      for (int r = 0; r < reps && rc == RMC_OK; ++r) rc = rmc_batch_run(ctx, byclass[c].data(), (int)byclass[c].size());
+      if (rc != RMC_OK) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = RMC_ECUDA;
+        break;
+      }
+      if (!have || ms < best) {
+        have = true;
+        best = ms;
+        best_tile = cand;
+      }
+    }
+    ctx->batch_rtile[c] = best_tile;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  (void)cudaGetLastError();
+  if (rc == RMC_OK) rc = rmc_sync(ctx);
+  return rc;
+}
+
+extern "C" int rmc_batch_get_tiles(const rmc_ctx *ctx, int *table, int count) {
+  if (!ctx || !table || count < kBatchTileClasses) return RMC_EINVAL;
+  for (int c = 0; c < kBatchTileClasses; ++c) table[c] = ctx->batch_rtile[c];
+  return RMC_OK;
+}
+
+extern "C" int rmc_batch_set_tiles(rmc_ctx *ctx, const int *table, int count) {
+  if (!ctx || !table || count < kBatchTileClasses) return RMC_EINVAL;
+  for (int c = 0; c < kBatchTileClasses; ++c)
+    if (table[c] < 0 || table[c] > 256 || (table[c] % 16) != 0) return RMC_EINVAL;
+  for (int c = 0; c < kBatchTileClasses; ++c) ctx->batch_rtile[c] = table[c];
   return RMC_OK;
 }

@@ -8,6 +8,8 @@
 
 #include "../../include/rmc.h"
 
+constexpr int kBatchTileClasses = 16;   // k-SVD tuning classes of the batched kernel: 4 n classes x 4 l classes
+
 struct RmcProfRec {
   int tag;
   cudaEvent_t start, stop;
@@ -23,6 +25,7 @@ struct rmc_ctx {
   int device;
   int num_sms;
   bool small_fp64;      // RMC_OPT_SMALL_FP64: CholeskyQR2 Gram products, Cholesky and Jacobi SVD in FP64
+  int batch_rtile[kBatchTileClasses];  // tuned row-tile height per k-SVD class of rmc_batch_run (0 = default)
   // measurement hooks
   bool prof;
   int prof_used, prof_cap;

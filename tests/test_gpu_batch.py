@@ -195,3 +195,51 @@ def test_batch_empty_and_invalid(R):
     good.kind = 7
     with pytest.raises(R.RmcError):
         R.rmc_batch_run([good])
+
+
+# ------------------------------------------------------------------------------------------ autotuner
+
+def test_autotune_fills_the_table_and_keeps_parity(R):
+    """rmc_batch_autotune picks a row tile per k-SVD class from the candidates; with the tuned table every
+    problem still matches the oracle, and a problem is bit-identical alone and in the mix."""
+    cases = [make_case(i, c) for i, c in enumerate(CASES)]
+    reqs, outs = [], []
+    for spec, A, b, Ad, bd in cases:
+        r, o = request(R, spec, Ad, bd)
+        reqs.append(r)
+        outs.append(o)
+    default = R.rmc_batch_get_tiles()
+    try:
+        table = R.rmc_batch_autotune(reqs, reps=2)
+        assert len(table) == R.RMC_BATCH_TILE_CLASSES
+        assert all(t in (0, 32, 64, 128) for t in table)
+        R.rmc_batch_run(reqs)
+        R.rmc_sync()
+        for (spec, A, b, Ad, bd), o in zip(cases, outs):
+            if spec["kind"] == "rsvd":
+                check_rsvd(spec, A, o)
+            else:
+                check_lsr(spec, A, b, o)
+        # alone vs in the mix under the tuned table
+        i = 3
+        spec, A, b, Ad, bd = cases[i]
+        r, o = request(R, spec, Ad, bd)
+        R.rmc_batch_run([r])
+        R.rmc_sync()
+        for g, e in zip(o, outs[i]):
+            assert torch.equal(g, e)
+    finally:
+        R.rmc_batch_set_tiles(default)
+
+
+def test_tile_table_round_trip_and_validation(R):
+    old = R.rmc_batch_get_tiles()
+    try:
+        t = [16 * (i % 9) for i in range(R.RMC_BATCH_TILE_CLASSES)]
+        R.rmc_batch_set_tiles(t)
+        assert R.rmc_batch_get_tiles() == t
+        with pytest.raises(R.RmcError):
+            R.rmc_batch_set_tiles([17] * R.RMC_BATCH_TILE_CLASSES)
+        assert R.rmc_batch_get_tiles() == t
+    finally:
+        R.rmc_batch_set_tiles(old)
