@@ -36,6 +36,7 @@ GAUSS_PREC = os.environ.get("RMC_BENCH_GAUSS_PREC", "tf32")
 # DRAM bytes per row of A per launch from ncu captures of `python bench.py --probe <kind>` (A 262,144 x 256 + b):
 # dram__bytes_read.sum + dram__bytes_write.sum divided by 262,144.  Re-capture when a kernel changes.
 PROFILED_DRAM_BYTES_PER_ROW = {
+    "gaussian_sketch": (270.093056e6 + 4.715008e6) / 262144,
     "srht_stage1": (268.572928e6 + 42.968832e6) / 262144,
     "countsketch_gather": (271.633408e6 + 4.247552e6) / 262144,
 }
@@ -379,7 +380,7 @@ def run_ours(args, world, rank, local):
     serve_info = None
     if world == 1 and not args.no_serve:
         serve_info = serve_measure(torch, rmc, rates=tuple(int(r) for r in args.serve_rates.split(",")),
-                                   window_s=args.serve_window)
+                                   window_s=args.serve_window, nstreams=args.serve_streams)
 
     cpu = None
     if world == 1:
@@ -638,13 +639,16 @@ def batch_measure(torch, rmc, count=4096, m_range=(512, 32768), reps=3):
     return out
 
 
-def serve_measure(torch, rmc, rates=(100, 1000, 2500, 5000), window_s=2.0, pool=48, budget=64 << 30, nstreams=4):
+def serve_measure(torch, rmc, rates=(100, 1000, 2500, 5000), window_s=2.0, pool=48, budget=64 << 30, nstreams=4,
+                  max_outstanding=4096):
     """The served stream: Poisson arrivals at each rate for window_s seconds over a pool of resident problems
     (m log-uniform [1e3, 2e5], n log-uniform [32, 1024]; 60% count-sketch least squares with s = 4n, 40%
-    randomized k-SVD with k in {8, 32, 64}, p = 8, q = 1), admitted under a 64 GB budget on 4 streams.  The
+    randomized k-SVD with k in {8, 32, 64}, p = 8, q = 1), admitted under a 64 GB budget on nstreams streams.  The
     stream is replayed in real time, once with FP32 products and once with 3xTF32 products for the k-SVDs (the
     same 1e-4 singular-value tolerance against the oracle: equal stated error).  Reports completed requests/s
-    and p50/p99 latency (submit to completion)."""
+    and p50/p99 latency (submit to completion).  Load shedding: an arrival that finds max_outstanding requests
+    queued or in flight is rejected and counted (their outputs hold device memory, so an overloaded stream would
+    otherwise grow without bound)."""
     import time
     import workloads
     ms_, ns_ = workloads.serve_pool(pool, seed=SEED)
@@ -664,34 +668,46 @@ def serve_measure(torch, rmc, rates=(100, 1000, 2500, 5000), window_s=2.0, pool=
             arr = workloads.serve_arrivals(rate, window_s, pool, seed=SEED + rate)
             srv = rmc.Server(budget, nstreams=nstreams, max_batch=256)
             live, lat = {}, []
+            rejected, failed, spec_of = 0, [], {}
             i, t0 = 0, time.perf_counter()
             while True:
                 now = time.perf_counter() - t0
                 while i < len(arr) and arr[i]["t"] <= now:
                     a = arr[i]
+                    if len(live) >= max_outstanding:
+                        rejected += 1
+                        i += 1
+                        continue
                     A, b = mats[a["pool"]]
                     n = A.shape[1]
                     if a["kind"] == "lsr":
                         r, o = rmc.lsr_request(A, b, a["s_factor"] * n, a["seed"])
                         tk = srv.submit(r, sketch="countsketch", prec="fp32")
+                        spec_of[tk] = ("lsr", int(A.shape[0]), int(n), a["s_factor"] * n, a["seed"], a["pool"])
                     else:
                         k = max(1, min(a["k"], n - a["p"]))
                         r, o = rmc.rsvd_request(A, k, a["p"], a["q"], a["seed"])
                         tk = srv.submit(r, prec=prec)
+                        spec_of[tk] = ("rsvd", int(A.shape[0]), int(n), k, a["p"], a["q"], a["seed"], a["pool"])
                     live[tk] = o
                     i += 1
                 srv.progress()
                 for tk, st, l in srv.poll():
-                    assert st == rmc.RMC_OK, st
-                    lat.append(l)
+                    if st != rmc.RMC_OK:
+                        failed.append((st,) + spec_of[tk])
+                    else:
+                        lat.append(l)
                     del live[tk]
+                    del spec_of[tk]
                 if i == len(arr) and not live:
                     break
             t_end = time.perf_counter() - t0
             srv.close()
             lat_ms = np.sort(np.array(lat)) * 1e3
             out["runs"]["%s_rate%d" % (prec, rate)] = {
-                "offered_per_s": len(arr) / window_s, "completed": len(lat), "completed_per_s": len(lat) / t_end,
+                "offered_per_s": len(arr) / window_s, "completed": len(lat), "rejected": rejected,
+                "failed": len(failed), "failed_first": failed[:8],
+                "completed_per_s": len(lat) / t_end,
                 "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
                 "mean_ms": float(lat_ms.mean()), "drain_s": t_end}
     del mats
@@ -715,6 +731,7 @@ def main():
                     help="run only the served-stream measurement (with --serve-window / --serve-rates) and exit")
     ap.add_argument("--serve-window", type=float, default=2.0, help="seconds of Poisson arrivals per rate")
     ap.add_argument("--serve-rates", type=str, default="100,1000,2500,5000", help="offered rates, requests/s")
+    ap.add_argument("--serve-streams", type=int, default=4, help="streams of the request server")
     args = ap.parse_args()
     if args.probe:
         return run_probe(args.probe)
@@ -722,7 +739,8 @@ def main():
         import torch
         import paper_1505_07570_gb300 as rmc
         rates = tuple(int(r) for r in args.serve_rates.split(","))
-        print(json.dumps({"serve": serve_measure(torch, rmc, rates=rates, window_s=args.serve_window)}))
+        print(json.dumps({"serve": serve_measure(torch, rmc, rates=rates, window_s=args.serve_window,
+                                                 nstreams=args.serve_streams)}))
         return 0
     world, rank, local = dist_env()
     if args.impl == "reference":

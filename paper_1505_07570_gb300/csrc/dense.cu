@@ -619,19 +619,19 @@ __global__ void jacobi_finish_kernel(const T *W, const T *V, int l, float *Ub, f
   }
 }
 
-// ---------------------------------------------------- one-sided Jacobi, eight lanes per column pair
+// ---------------------------------------------------- one-sided Jacobi, a lane group per column pair
 // The same round-robin rotations as jacobi_smem_kernel, with W alone in shared memory (no rotation
-// accumulator: the other singular factor is recovered afterwards, see jacobi_right_kernel) and eight lanes per
-// column pair instead of a warp: a 1024-thread block rotates up to 128 disjoint pairs per round, each lane
-// holding every eighth row, with three shuffle levels per inner product.  For l = 120 this turns a round of 60
-// pairs from two warp-serial pair updates into one pass of 15 warps.
-template <typename T>
+// accumulator: the other singular factor is recovered afterwards, see jacobi_right_kernel) and a group of G lanes
+// per column pair instead of a warp: a 1024-thread block rotates up to 1024 / G disjoint pairs per round, each
+// lane holding every G-th row (G = 16 for l <= 128, 8 up to l = 256).
+// G lanes per pair (8 or 16; 1024 / G pairs per round at most).
+template <typename T, int G>
 __global__ void __launch_bounds__(1024) jacobi_grp_kernel(T *Wg, int l, T tol, int max_sweeps, int *status) {
   extern __shared__ __align__(16) unsigned char jg_raw[];
   T *W = reinterpret_cast<T *>(jg_raw);
   __shared__ int rotated;
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) W[e] = Wg[e];
-  const int grp = threadIdx.x >> 3, j = threadIdx.x & 7;
+  const int grp = threadIdx.x / G, j = threadIdx.x % G;
   const int lp = (l + 1) & ~1;
   const T tol2 = tol * tol;
   int sweep = 0;
@@ -654,15 +654,15 @@ __global__ void __launch_bounds__(1024) jacobi_grp_kernel(T *Wg, int l, T tol, i
       T alpha = 0, beta = 0, gamma = 0;
       T *wp = W + (size_t)(p < 0 ? 0 : p) * l, *wq = W + (size_t)(p < 0 ? 0 : q) * l;
       if (p >= 0)
-        for (int r = j; r < l; r += 8) {
+        for (int r = j; r < l; r += G) {
           const T x = wp[r], y = wq[r];
           alpha = fma(x, x, alpha);
           beta = fma(y, y, beta);
           gamma = fma(x, y, gamma);
         }
-      // the eight lanes of a group are aligned in the warp: xor offsets 1, 2, 4 stay inside the group
+      // the G lanes of a group are aligned in the warp: xor offsets below G stay inside the group
 #pragma unroll
-      for (int o = 1; o < 8; o <<= 1) {
+      for (int o = 1; o < G; o <<= 1) {
         alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
         beta += __shfl_xor_sync(0xffffffffu, beta, o);
         gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(1024) jacobi_grp_kernel(T *Wg, int l, T tol, i
       if (p >= 0 && gamma != T(0) && gamma * gamma > tol2 * alpha * beta) {
         T c, sn;
         rotation(alpha, beta, gamma, c, sn);
-        for (int r = j; r < l; r += 8) {
+        for (int r = j; r < l; r += G) {
           const T x = wp[r], y = wq[r];
           wp[r] = c * x - sn * y;
           wq[r] = sn * x + c * y;
@@ -1258,7 +1258,19 @@ int rmc_launch_transpose(cudaStream_t st, const float *in, int64_t rows, int64_t
 // shared memory first; only if it meets a non-positive pivot (or the matrix is too large for shared memory)
 // does the FP64 factorization run (its kernels return at once otherwise), with no host round trip.
 // fail[0]: the FP32 path failed; fail[1]: the FP64 path failed.
-static int launch_factor(rmc_ctx *ctx, double *G, int l, double *Rinv, float *Rinv32, int *fail) {
+// refresh (optional): the basis whose Gram matrix G is, with the partials buffer; when G was formed with FP32
+// products and the FP32 factorization fails, G is formed again with FP64 products (exact for FP32 data) before
+// the FP64 factorization, so that a basis whose condition number squared is beyond FP32 but within FP64 (e.g.
+// A Omega with a square, ill-conditioned Gaussian Omega) still factors.  The refresh runs only when the FP32
+// path failed (decided on the device).
+struct GramRefresh {
+  const float *Y;
+  int64_t m, ldy;
+  double *part;
+};
+
+static int launch_factor(rmc_ctx *ctx, double *G, int l, double *Rinv, float *Rinv32, int *fail,
+                         const GramRefresh *refresh = nullptr) {
   cudaStream_t st = ctx->stream;
   const size_t smem = chol32_smem_bytes(l);
   RmcProf prof(ctx, RMC_K_SMALL);
@@ -1279,6 +1291,7 @@ static int launch_factor(rmc_ctx *ctx, double *G, int l, double *Rinv, float *Ri
     }
   }
   RMC_TRY_CUDA(cudaMemsetAsync(&fail[1], 0, sizeof(int), st));
+  if (refresh) RMC_TRY(launch_gram(ctx, refresh->Y, refresh->m, l, refresh->ldy, G, refresh->part, true, &fail[0]));
   chol64_fallback_kernel<<<1, 1024, 0, st>>>(G, l, &fail[0], ctx->d_status, &fail[1]);
   tri_inverse_cols_kernel<<<l, 32, sizeof(double) * l, st>>>(G, l, Rinv, Rinv32, &fail[0], &fail[1]);
   rmc_note_launch(3);
@@ -1315,7 +1328,8 @@ int rmc_launch_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l_, int64_t ld
     // storage of the intermediate basis either way.
     const bool fp64_products = (fp64_gram && pass == passes - 1) || ctx->small_fp64;
     RMC_TRY(launch_gram(ctx, Y, m, l, ldy, G, part, fp64_products));
-    RMC_TRY(launch_factor(ctx, G, l, Rinv, Rinv32, fail));
+    const GramRefresh refresh{Y, m, ldy, part};
+    RMC_TRY(launch_factor(ctx, G, l, Rinv, Rinv32, fail, fp64_products ? nullptr : &refresh));
     RMC_TRY(launch_rowblock(st, Y, m, l, ldy, Rinv32, l, l, Y, ldy));
     if (R) {
       if (pass == 0) RMC_TRY_CUDA(cudaMemcpyAsync(R1, G, sizeof(double) * l * l, cudaMemcpyDeviceToDevice, st));
@@ -1346,21 +1360,35 @@ static int launch_jacobi_grp(rmc_ctx *ctx, const double *R, int l, double *work,
   if (fp64 || jacobi_in_fp64(l)) {
     const double tol = 8 * 2.220446049250313e-16 * sqrt((double)l);
     const size_t smem = sizeof(double) * (size_t)l * l;
-    if (smem > 48 * 1024)
-      RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_grp_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
     to_colmajor_kernel<double><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, work);
-    jacobi_grp_kernel<double><<<1, 1024, smem, st>>>(work, l, tol, 60, ctx->d_status);
+    if (l <= 128) {
+      if (smem > 48 * 1024)
+        RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_grp_kernel<double, 16>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      jacobi_grp_kernel<double, 16><<<1, 1024, smem, st>>>(work, l, tol, 60, ctx->d_status);
+    } else {
+      if (smem > 48 * 1024)
+        RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_grp_kernel<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+      jacobi_grp_kernel<double, 8><<<1, 1024, smem, st>>>(work, l, tol, 60, ctx->d_status);
+    }
     jacobi_left_kernel<double><<<1, 256, sizeof(double) * l, st>>>(work, l, M, sigma);
   } else {
     const float tol = 4 * 1.1920929e-7f * sqrtf((float)l);
     const size_t smem = sizeof(float) * (size_t)l * l;
     float *Wf = reinterpret_cast<float *>(work);
-    if (smem > 48 * 1024)
-      RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_grp_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
     to_colmajor_kernel<float><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, Wf);
-    jacobi_grp_kernel<float><<<1, 1024, smem, st>>>(Wf, l, tol, 60, ctx->d_status);
+    if (l <= 128) {
+      if (smem > 48 * 1024)
+        RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_grp_kernel<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+      jacobi_grp_kernel<float, 16><<<1, 1024, smem, st>>>(Wf, l, tol, 60, ctx->d_status);
+    } else {
+      if (smem > 48 * 1024)
+        RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_grp_kernel<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+      jacobi_grp_kernel<float, 8><<<1, 1024, smem, st>>>(Wf, l, tol, 60, ctx->d_status);
+    }
     jacobi_left_kernel<float><<<1, 256, sizeof(double) * l, st>>>(Wf, l, M, sigma);
   }
   rmc_note_launch(3);

@@ -52,13 +52,33 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity to complete.  Returns false on timeout.
+// try_wait with a suspend-time hint: the thread is parked (issuing nothing) until the phase completes or about
+// hint_ns nanoseconds pass, instead of spinning on the barrier and taking issue slots from the working warps.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
+// Suspend hint of the bounded waits: long enough that a waiting thread wakes on the phase, not on the hint.
+constexpr uint32_t kSuspendHintNs = 100000;
+
+// Bounded wait for the phase with the given parity to complete.  Returns false on timeout (kWaitLimitNs, checked
+// after every suspended try).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
-  for (uint32_t i = 1;; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+  for (;;) {
+    if (mbar_try_wait_sleep(bar, parity, kSuspendHintNs)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
   }
 }
 

@@ -247,6 +247,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
     for (int it = 0; it < num_it; ++it) {
       const int st = it % kStages;
       const int64_t row0 = k_begin + (int64_t)it * kKStage + 2 * kp;
+      // b for this stage's two rows, loaded first so its latency hides behind the draws
+      float bv[2] = {0.f, 0.f};
+      if (with_b) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+          if (row0 + t < k_end) bv[t] = __ldg(args.b + row0 + t);
+      }
       float z[2][8];
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
@@ -267,11 +274,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
       }
       if (with_b) {
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          const float bv = (row0 + t < k_end) ? __ldg(args.b + row0 + t) : 0.f;
+        for (int t = 0; t < 2; ++t)
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj) bacc[jj] = fmaf(z[t][jj], bv, bacc[jj]);
-        }
+          for (int jj = 0; jj < 8; ++jj) bacc[jj] = fmaf(z[t][jj], bv[t], bacc[jj]);
       }
       if (!warp_wait(&empty[st], ((it / kStages) & 1) ^ 1, abort_flag, args.status)) break;
       unsigned char *otile = operands + st * kStageBytes + mt * kOmegaBytes;

@@ -392,3 +392,17 @@ def test_set_option_rejects_unknown(R):
         R.rmc_set_option(99, 1)
     with pytest.raises(R.RmcError):
         R.rmc_set_option(R.RMC_OPT_SMALL_FP64, 2)
+
+
+@pytest.mark.parametrize("q", [0, 1])
+def test_rsvd_square_ill_conditioned_omega(R, q):
+    """l = n = 33 makes Omega a square Gaussian; with this seed it is ill-conditioned enough that the Gram matrix
+    of A Omega with FP32 products is indefinite.  The FP32 Cholesky fails, the Gram matrix is formed again with
+    FP64 products and factored in FP64 (a served request once returned RMC_ENUMERIC here).  Q spans range(A), so
+    the singular values are A's own."""
+    A = workloads.gaussian(20000, 33, seed=77)
+    U, s, V = R.rmc_rsvd(dev(A), 25, 8, q, seed=4317)
+    R.rmc_sync()
+    _, so, _, _ = rsvd.rsvd(A, 25, 8, q, 4317)
+    np.testing.assert_allclose(s.cpu().numpy(), so, rtol=1e-4)
+    np.testing.assert_allclose(so, np.linalg.svd(A.astype(np.float64), compute_uv=False)[:25], rtol=1e-10)
