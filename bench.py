@@ -367,6 +367,9 @@ def run_ours(args, world, rank, local):
             isolated[name] = roofline_of(name, {"launches": cnt, "ms_total": ms})
     rmc.rmc_profile_end()
 
+    forms_info = None
+    if world == 1:
+        forms_info = gaussian_forms_measure(torch, rmc, A, b)
     precise_info = None
     if world == 1 and not args.no_rsvd:
         precise_info = precise_measure(torch, rmc, A, b)
@@ -397,7 +400,8 @@ def run_ours(args, world, rank, local):
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernels, "kernels_isolated": isolated,
-        "lsr_precise": precise_info, "rsvd": rsvd_info, "batch": batch_info, "serve": serve_info,
+        "gaussian_forms": forms_info, "lsr_precise": precise_info, "rsvd": rsvd_info, "batch": batch_info,
+        "serve": serve_info,
     }
     print(json.dumps(line))
     if world > 1:
@@ -515,16 +519,80 @@ def lanczos_measure(torch, rmc, A, k=100, s=120, q=2):
     return out
 
 
+def gaussian_forms_measure(torch, rmc, A, b):
+    """Whole SRHT and count-sketch calls on [A, b] (device time of every kernel of the call, algorithmic bytes
+    against the HBM peak), then the Gaussian sketch of [A, b] in each operand precision (FP32 CUDA cores;
+    TF32 and BF16 tensor cores) at s = 1024 and 4096: device time per call (three calls, CUDA events), TFLOP/s of
+    the product 2 m (n + 1) s, and the relative Frobenius difference from the FP32 form's sketch (the FP32 form
+    is pinned to the oracle at 1e-5 by the tests; TF32 and BF16 differ from it by their operand rounding)."""
+    m, n = A.shape
+    Ab = torch.cat([A, b[:, None]], dim=1).contiguous()
+    pk = peaks()
+    out = {"workload": "tall-lsr %dx%d + b, Gaussian sketch of [A, b]" % (m, n), "calls": {}}
+    # whole calls of the HBM-bound kinds (every kernel of the call, e.g. both SRHT stages), one call at a time
+    for kind in ("srht", "countsketch"):
+        for s in (1024, 4096):
+            rmc.rmc_sketch(Ab, s, kind, SEED)
+            rmc.rmc_sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                rmc.rmc_sketch(Ab, s, kind, SEED)
+            e1.record()
+            rmc.rmc_sync()
+            ms = e0.elapsed_time(e1) / 3
+            gbs = call_bytes(m, n, s) / ms / 1e6
+            out["calls"]["%s_call_s%d" % (kind, s)] = {"ms": ms, "gbs": gbs, "frac_hbm": gbs / pk["hbm_gbs"]}
+    for s in (1024, 4096):
+        # the drawing bound: the same normals with no product (one CTA of 16 drawing warps per SM)
+        rmc.rmc_gaussian_draw_floor(m, s, SEED)
+        rmc.rmc_sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            rmc.rmc_gaussian_draw_floor(m, s, SEED)
+        e1.record()
+        rmc.rmc_sync()
+        floor_ms = e0.elapsed_time(e1) / 3
+        out["calls"]["draw_floor_s%d" % s] = {"ms": floor_ms, "normals_per_s": m * s / floor_ms * 1e3}
+        ref = None
+        for prec in ("fp32", "tf32", "bf16"):
+            C = rmc.rmc_sketch(Ab, s, "gaussian", SEED, prec=prec)
+            rmc.rmc_sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                C = rmc.rmc_sketch(Ab, s, "gaussian", SEED, prec=prec)
+            e1.record()
+            rmc.rmc_sync()
+            ms = e0.elapsed_time(e1) / 3
+            tflops = 2.0 * m * (n + 1) * s / ms / 1e9
+            rec = {"ms": ms, "tflops": tflops}
+            if prec == "fp32":
+                ref = C.double()
+                rec["frac_fp32_alu_peak"] = tflops / (152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12)
+            else:
+                ratio = 1.1 / 2.25 if prec == "tf32" else 1.0
+                rec["frac_tensor_peak"] = tflops / (pk["bf16_tflops"] * ratio)
+                rec["relfro_vs_fp32"] = float(torch.linalg.matrix_norm(C.double() - ref) /
+                                              torch.linalg.matrix_norm(ref))
+                rec["draw_floor_over_ms"] = floor_ms / ms   # 1.0: the sketch costs no more than drawing its normals
+            out["calls"]["%s_s%d" % (prec, s)] = rec
+    del Ab
+    torch.cuda.empty_cache()
+    return out
+
+
 def rsvd_measure(torch, rmc):
     """The large randomized-SVD workload (A = G1 diag(1/i) G2^T, 65,536 x 16,384, rank 2048; k = 100, p = 20)
-    at q = 0, 1, 2 in FP32 and TF32 operands: device time per call and useful TFLOP/s of the products with A
-    (2q + 2 passes of 2 m n l flops)."""
+    at q = 0, 1, 2 in FP32, 3xTF32, TF32 and BF16 operands: device time per call and useful TFLOP/s of the
+    products with A (2q + 2 passes of 2 m n l flops)."""
     import workloads
     m, n, k, p = 65536, 16384, 100, 20
     A = workloads.factor_rank_torch(m, n, 2048, seed=SEED)
     out = {"workload": "rsvd 65536x16384 rank-2048 sigma_i=1/i, k=100 p=20", "calls": {}}
     ref = {}
-    for prec in ["fp32", "tf32x3", "tf32"]:
+    for prec in ["fp32", "tf32x3", "tf32", "bf16"]:
         for q in [0, 1, 2]:
             rmc.rmc_rsvd(A, k, p, q, SEED, prec=prec)
             rmc.rmc_sync()

@@ -69,7 +69,9 @@ extern "C" {
 /* ------------------------------------------------------------- GEMM operand precision (accumulate FP32) */
 #define RMC_FP32  0   /* FP32 operands on the CUDA cores (the plain form)                                 */
 #define RMC_TF32  1   /* TF32 operands on the tensor cores (tcgen05.mma kind::tf32), FP32 accumulation    */
-#define RMC_BF16  2   /* reserved for BF16 operands (tcgen05.mma kind::f16): not built, rejected with RMC_EINVAL */
+#define RMC_BF16  2   /* BF16 operands on the tensor cores (tcgen05.mma kind::f16), FP32 accumulation: A is read
+                         in FP32 and rounded on chip, the other operand (Omega drawn, or X) rounded to BF16; about
+                         2^-9 relative error per product (the Gaussian sketch: ~2e-3 relative Frobenius) */
 #define RMC_TF32X3 3  /* 3xTF32 on the tensor cores: each FP32 operand split into a TF32 head and remainder,
                          three kind::tf32 MMAs per step (head*head + head*rest + rest*head), FP32 accumulation:
                          about 2^-21 relative error per product (FP32-level), for the products with A of
@@ -121,7 +123,7 @@ int rmc_workspace_bytes(const rmc_ctx *ctx, size_t *bytes);
  *                   unnormalised Hadamard matrix H_N (Sylvester order), s sampled rows without replacement
  *                   kept in ascending index order, scaled by 1/sqrt(s) (Sec. 3.2.2); 1 <= s <= N.
  *         RMC_COUNTSKETCH: C[h(i), :] += g(i) A[i, :] for every row i (Algorithm 3.1); any s >= 1.
- *   prec  GEMM operand precision of the Gaussian kind (RMC_FP32 or RMC_TF32); ignored otherwise, but
+ *   prec  GEMM operand precision of the Gaussian kind (RMC_FP32, RMC_TF32 or RMC_BF16); ignored otherwise, but
  *         always checked (any other value is RMC_EINVAL).
  *         The tensor-core forms stream A with TMA and need 16-byte aligned rows (A and lda * 4 multiples of
  *         16 bytes); other layouts run the FP32 CUDA-core kernel.
@@ -145,7 +147,7 @@ int rmc_lsr_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t l
  *   B = Q^T A (l x n); B = U_B diag(sigma) V_B^T (FP64 one-sided Jacobi on the R factor of B^T);
  *   U = Q U_B[:, :k] (m x k, ldu), sigma[k] descending, V = V_B[:, :k] (n x k, ldv).
  * Each column pair (u_i, v_i) is signed so the largest-magnitude entry of v_i is positive.
- * prec selects the operand precision of the products with A (RMC_FP32, RMC_TF32 or RMC_TF32X3).
+ * prec selects the operand precision of the products with A (RMC_FP32, RMC_TF32, RMC_TF32X3 or RMC_BF16).
  * Requires 1 <= k, l <= min(m, n), l <= 256,
  * q >= 0.  Errors: RMC_EINVAL, RMC_ENOMEM, RMC_ECUDA; RMC_ENUMERIC at rmc_sync (breakdown of CholeskyQR2
  * or no Jacobi convergence). */
@@ -172,8 +174,8 @@ int rmc_lsr_precise(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t 
  * stream of rmc_rsvd), K = [C, (A A^T) C, ..., (A A^T)^(q-1) C] (m x s q), Q = orth(K), B = Q^T A,
  * B = U_B diag(sigma) V_B^T; U = Q U_B[:, :k] (m x k, ldu), sigma[k] descending, V = V_B[:, :k] (n x k, ldv),
  * signed as rmc_rsvd signs them.  Each Krylov block is orthonormalised and projected off the earlier blocks
- * as it is formed (same span, stable basis).  2q passes over A.  prec: RMC_FP32 or RMC_TF32 for the products
- * with A.  Requires 1 <= k <= s q, s q <= min(m, n), s q <= 256, q >= 1.  With q = 1 the result is rmc_rsvd's
+ * as it is formed (same span, stable basis).  2q passes over A.  prec: the operand precision of the products
+ * with A, as for rmc_rsvd.  Requires 1 <= k <= s q, s q <= min(m, n), s q <= 256, q >= 1.  With q = 1 the result is rmc_rsvd's
  * with p = s - k and no power iteration.  Errors as rmc_rsvd. */
 int rmc_block_lanczos(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, int k, int s, int q,
                       uint64_t seed, int prec, float *U, int64_t ldu, float *sigma, float *V, int64_t ldv);
@@ -182,7 +184,7 @@ int rmc_block_lanczos(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_
  * composite of Sec. 3.2.4, two passes over A:
  *   C = A S (S an n x s count sketch over the columns, Philox instance 1);
  *   L = P^T A, D = P^T C with P = P_cs P_gp (a count sketch of the rows to p_cs, instance 2, then a Gaussian
- *   projection to p rows, instance 3; prec RMC_TF32 runs it on the tensor cores, RMC_FP32 and
+ *   projection to p rows, instance 3; prec RMC_TF32 or RMC_BF16 runs it on the tensor cores, RMC_FP32 and
  *   RMC_TF32X3 in FP32);
  *   D = Q_D R_D;  Q_D^T L = U_bar diag(sigma_bar) V_bar^T (top k);  C R_D^-1 U_bar diag(sigma_bar) =
  *   U diag(sigma) V_hat^T;  V = V_bar V_hat.
@@ -258,7 +260,8 @@ int rmc_svd_wide(rmc_ctx *ctx, const float *B, int64_t l, int64_t n, int64_t ldb
  * and the C = A' * C; C = A * C power step of the Sec. 5.1 listing):
  *   rmc_matmul_an:  Y (m x l, ldy) = A (m x n) * X, with X n x l (ldx).
  *   rmc_matmul_at:  W (l x n, ldw) = X^T * A,       with X m x l (ldx).
- * prec: RMC_FP32 (CUDA cores), RMC_TF32 or RMC_TF32X3 (tensor cores); FP32 accumulation.  1 <= l <= 256. */
+ * prec: RMC_FP32 (CUDA cores), RMC_TF32, RMC_TF32X3 or RMC_BF16 (tensor cores); FP32 accumulation.
+ * 1 <= l <= 256. */
 int rmc_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X,
                   int64_t l, int64_t ldx, int prec, float *Y, int64_t ldy);
 int rmc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X,
@@ -318,7 +321,7 @@ int rmc_batch_set_tiles(rmc_ctx *ctx, const int *table, int count);
 typedef struct rmc_serve_request {
   rmc_request req;
   int sketch;   /* LSR: RMC_GAUSSIAN, RMC_SRHT or RMC_COUNTSKETCH (RSVD: ignored)                        */
-  int prec;     /* RMC_FP32 or RMC_TF32: operand precision of the products with A                            */
+  int prec;     /* operand precision of the products with A (RMC_FP32, RMC_TF32, RMC_TF32X3, RMC_BF16)       */
 } rmc_serve_request;
 
 typedef struct rmc_server rmc_server;
@@ -384,6 +387,14 @@ int rmc_profile_spans(rmc_ctx *ctx, int tag, double *start_ms, double *stop_ms, 
  * the batch ring).  The next rmc_sync returns RMC_ETIMEOUT and clears it; the context stays usable.
  * Errors: RMC_EINVAL (NULL context, limit above 1 s), RMC_ENOMEM, RMC_ECUDA. */
 int rmc_debug_wait_timeout(rmc_ctx *ctx, uint64_t limit_ns);
+
+/* Measurement hook for the drawing bound of the tensor-core Gaussian sketch: enqueue one kernel that draws the
+ * m x s normals of the sketch's operator (Philox stream 4, the Box-Muller pairs of rmc_sketch's RMC_GAUSSIAN
+ * tensor-core forms, rounded to TF32) with one CTA of 16 drawing warps per SM -- the sketch kernel's drawing
+ * warps, with no product, staging or barrier -- and write their FP64 sum to *sum (device memory).  Its device
+ * time is the time the sketch of an m-row matrix to s rows spends drawing at best.  Errors: RMC_EINVAL,
+ * RMC_ECUDA. */
+int rmc_gaussian_draw_floor(rmc_ctx *ctx, int64_t m, int64_t s, uint64_t seed, double *sum);
 
 /* Number of kernels this library has launched in the process so far (all contexts). */
 int rmc_launch_counter(uint64_t *launches);

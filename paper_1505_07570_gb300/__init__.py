@@ -56,6 +56,7 @@ _SIGS.update({
                           ctypes.POINTER(_int)],
     "rmc_launch_counter": [ctypes.POINTER(_u64)],
     "rmc_debug_wait_timeout": [_p, _u64],
+    "rmc_gaussian_draw_floor": [_p, _i64, _i64, _u64, _p],
     "rmc_countsketch_noalloc": [_p, _p, _i64, _i64, _i64, _i64, _u64, _p, _i64],
     "rmc_lsr_precise": [_p, _p, _i64, _i64, _i64, _p, _i64, _int, _u64, _int, ctypes.c_double, _int,
                         ctypes.c_double, _p, _p],
@@ -451,6 +452,16 @@ def rmc_profile_spans(tag):
 def rmc_profile_end():
     for c in _device_contexts():
         _check(lib.rmc_profile_end(c.handle), "rmc_profile_end")
+
+
+def rmc_gaussian_draw_floor(m, s, seed):
+    """Draw the m x s normals of the Gaussian sketch's operator without the product (the drawing bound of the
+    tensor-core sketch), on the current torch stream; returns a 1-element FP64 CUDA tensor with their sum."""
+    import torch
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    _check(lib.rmc_gaussian_draw_floor(context().bind(), int(m), int(s), int(seed), out.data_ptr()),
+           "rmc_gaussian_draw_floor")
+    return out
 
 
 def rmc_launch_counter():

@@ -164,7 +164,7 @@ int rmc_check_sketch_args(const float *A, int64_t m, int64_t n, int64_t lda, int
 size_t rmc_sketch_plan_bytes(rmc_ctx *ctx, int64_t m, int64_t ntot, int64_t s, int kind, int prec) {
   switch (kind) {
     case RMC_GAUSSIAN: return rmc_gauss_ws(m, ntot, s, prec, ctx->num_sms);
-    case RMC_SRHT: return rmc_srht_ws(m, ntot, s);
+    case RMC_SRHT: return rmc_srht_ws(m, ntot, s, ctx->num_sms);
     default: return rmc_countsketch_ws(m, s);
   }
 }

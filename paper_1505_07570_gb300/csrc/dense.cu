@@ -160,63 +160,114 @@ __global__ void __launch_bounds__(256) gram_f64_kernel(const float *__restrict__
   if (i1 < l && j1 < l) o[i1 * l + j1] = acc11;
 }
 
-// Gram matrix with FP32 products summed in FP32 over each 32-row slice and in FP64 across slices (for
-// CholeskyQR2, whose factorization runs in FP32: FP64 products would not be used).
-__global__ void __launch_bounds__(256) gram_f32_kernel(const float *__restrict__ Y, int64_t m, int l, int64_t ldy,
-                                                       int64_t rows_per_chunk, double *__restrict__ part) {
-  __shared__ float As[GRAM_T][GRAM_T + 1];
-  __shared__ float Bs[GRAM_T][GRAM_T + 1];
+// a + b as hi + lo exactly (TwoSum): the running double-FP32 sums of the Gram kernel below.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+  const float s = hi + x, bb = s - hi;
+  lo += (hi - (s - bb)) + (x - bb);
+  hi = s;
+}
+
+// Partial Gram matrix of one chunk of rows for one TILE x TILE tile pair (ti <= tj): 256 threads as 16 x 16, each
+// owning an R x R block (R = TILE / 16) of adjacent rows and columns; 32-row slices of both column tiles are
+// staged in shared memory while the next slice is loaded into registers.  Sums are double-FP32 (hi + lo), so the
+// FP64 pipe (a small fraction of the FP32 rate on this GPU) is not used:
+//   EXACT = false: FP32 products summed in FP32 over a slice, slices summed in double-FP32;
+//   EXACT = true:  every product split exactly as p + e (e = fma(a, b, -p)), both summed in double-FP32 — exact
+//                  products with ~48-bit sums, the FP32-data equivalent of FP64 products.
+template <int TILE, bool EXACT>
+__global__ void __launch_bounds__(256) gram_tile_kernel(const float *__restrict__ Y, int64_t m, int l, int64_t ldy,
+                                                        int64_t rows_per_chunk, double *__restrict__ part) {
+  constexpr int R = TILE / 16, SLICE = 32, LD = SLICE * TILE * 2 / 256;
+  __shared__ __align__(16) float As[SLICE][TILE];
+  __shared__ __align__(16) float Bs[SLICE][TILE];
   int p = blockIdx.x, ti = 0;
-  const int T = (l + GRAM_T - 1) / GRAM_T;
+  const int T = (l + TILE - 1) / TILE;
   while (p >= T - ti) { p -= T - ti; ++ti; }
   const int tj = ti + p;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t r_begin = (int64_t)blockIdx.y * rows_per_chunk;
   const int64_t r_end = min(m, r_begin + rows_per_chunk);
-  double acc00 = 0, acc01 = 0, acc10 = 0, acc11 = 0;
-  for (int64_t r0 = r_begin; r0 < r_end; r0 += GRAM_T) {
-    for (int e = tid; e < GRAM_T * GRAM_T; e += 256) {
-      const int rr = e / GRAM_T, cc = e % GRAM_T;
+  float hi[R][R], lo[R][R];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) hi[i][j] = lo[i][j] = 0.f;
+  float st[LD];
+  auto load = [&](int64_t r0) {
+#pragma unroll
+    for (int u = 0; u < LD; ++u) {
+      const int e = tid + 256 * u, which = e / (SLICE * TILE), ee = e % (SLICE * TILE);
+      const int rr = ee / TILE, cc = ee % TILE;
+      const int col = (which ? tj : ti) * TILE + cc;
       const int64_t r = r0 + rr;
-      const int ca = ti * GRAM_T + cc, cb = tj * GRAM_T + cc;
-      As[rr][cc] = (r < r_end && ca < l) ? Y[r * ldy + ca] : 0.f;
-      Bs[rr][cc] = (r < r_end && cb < l) ? Y[r * ldy + cb] : 0.f;
+      st[u] = (r < r_end && col < l) ? __ldg(Y + r * ldy + col) : 0.f;
+    }
+  };
+  if (r_begin < r_end) load(r_begin);
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += SLICE) {
+#pragma unroll
+    for (int u = 0; u < LD; ++u) {
+      const int e = tid + 256 * u, which = e / (SLICE * TILE), ee = e % (SLICE * TILE);
+      (which ? &Bs[0][0] : &As[0][0])[ee] = st[u];
     }
     __syncthreads();
-    float f00 = 0.f, f01 = 0.f, f10 = 0.f, f11 = 0.f;
-#pragma unroll 8
-    for (int rr = 0; rr < GRAM_T; ++rr) {
-      const float a0 = As[rr][ty], a1 = As[rr][ty + 16], b0 = Bs[rr][tx], b1 = Bs[rr][tx + 16];
-      f00 = fmaf(a0, b0, f00);
-      f01 = fmaf(a0, b1, f01);
-      f10 = fmaf(a1, b0, f10);
-      f11 = fmaf(a1, b1, f11);
+    if (r0 + SLICE < r_end) load(r0 + SLICE);
+    float f[R][R];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) f[i][j] = 0.f;
+#pragma unroll 4
+    for (int rr = 0; rr < SLICE; ++rr) {
+      float a[R], b[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        a[i] = As[rr][ty * R + i];
+        b[i] = Bs[rr][tx * R + i];
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          if (EXACT) {
+            const float pr = a[i] * b[j];
+            f[i][j] += fmaf(a[i], b[j], -pr);
+            two_sum_acc(hi[i][j], lo[i][j], pr);
+          } else {
+            f[i][j] = fmaf(a[i], b[j], f[i][j]);
+          }
+        }
     }
-    acc00 += f00;
-    acc01 += f01;
-    acc10 += f10;
-    acc11 += f11;
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        if (EXACT) lo[i][j] += f[i][j];          // the product errors of the slice
+        else two_sum_acc(hi[i][j], lo[i][j], f[i][j]);
+      }
     __syncthreads();
   }
   double *o = part + (int64_t)blockIdx.y * l * l;
-  const int i0 = ti * GRAM_T + ty, i1 = i0 + 16, j0 = tj * GRAM_T + tx, j1 = j0 + 16;
-  if (i0 < l && j0 < l) o[i0 * l + j0] = acc00;
-  if (i0 < l && j1 < l) o[i0 * l + j1] = acc01;
-  if (i1 < l && j0 < l) o[i1 * l + j0] = acc10;
-  if (i1 < l && j1 < l) o[i1 * l + j1] = acc11;
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int gi = ti * TILE + ty * R + i, gj = tj * TILE + tx * R + j;
+      if (gi < l && gj < l) o[gi * l + gj] = (double)hi[i][j] + (double)lo[i][j];
+    }
 }
 
-__global__ void gram_reduce_kernel(const double *__restrict__ part, int chunks, int l, double *__restrict__ G,
-                                   const int *gate) {
+__global__ void gram_reduce_kernel(const double *__restrict__ part, int chunks, int l, int tile,
+                                   double *__restrict__ G, const int *gate) {
   if (gate && !*gate) return;
   const int total = l * l;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const int i = e / l, j = e % l;
-    if (i / GRAM_T > j / GRAM_T) continue;      // lower tiles are mirrored below
+    if (i / tile > j / tile) continue;      // lower tiles are mirrored below
     double s = 0;
     for (int c = 0; c < chunks; ++c) s += part[(int64_t)c * total + e];
     G[i * l + j] = s;
-    if (i / GRAM_T < j / GRAM_T) G[j * l + i] = s;
+    if (i / tile < j / tile) G[j * l + i] = s;
   }
 }
 
@@ -332,6 +383,104 @@ __global__ void __launch_bounds__(512) chol32_inv_kernel(double *G, int l, float
   }
 }
 
+// The same factorization and inverse for l <= 128 with one barrier per pivot.  Right-looking without scaling the
+// pivot row: in step j every row below it is updated from row j alone,
+//   P[i][k] -= g_i P[j][k]   (k >= i),   B[i][c] -= g_i B[j][c]   (c <= j),   g_i = P[j][i] / P[j][j],  i > j,
+// with B = I at the start; finally P[j][k] = r_j U[j][k] and B[j][c] = r_j Y[j][c], r_j = sqrt(P[j][j]) and
+// Y = U^-T (forward substitution on U^T Y = I, row j of Y final in step j).  No thread writes row j in step j.
+// P is the packed upper triangle (row-major, (i, k) at i l - i(i+1)/2 + k), B the packed lower one ((i, c) at
+// i(i+1)/2 + c).  Warp w updates rows j + 1 + w + 16 r (r < 8), lanes along the row in 32-wide chunks; row j's
+// chunk is loaded once for all the warp's rows, and every load of a chunk is issued before its stores (the
+// compiler cannot see that the stores never touch row j), so a step costs a few shared-memory latencies.
+constexpr int kCholFusedMaxL = 128;
+constexpr int kCholFusedThreads = 512;
+
+__global__ void __launch_bounds__(kCholFusedThreads) chol32_fused_kernel(double *G, int l, float *Rinv32, int *fail) {
+  extern __shared__ float cfs[];
+  const int N = l * (l + 1) / 2;
+  float *P = cfs, *B = cfs + N, *invr = cfs + 2 * N;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  // the upper triangle of G, rounded to FP32 (a flat loop, so that the loads of one thread overlap)
+#pragma unroll 8
+  for (int e = t; e < l * l; e += kCholFusedThreads) {
+    const int i = e / l, k = e - i * l;
+    const double g = G[e];
+    if (k >= i) P[i * l - i * (i + 1) / 2 + k] = (float)g;
+  }
+  for (int e = t; e < N; e += kCholFusedThreads) B[e] = 0.f;
+  __syncthreads();
+  for (int i = t; i < l; i += kCholFusedThreads) B[i * (i + 1) / 2 + i] = 1.f;
+  __syncthreads();
+  for (int j = 0; j < l; ++j) {
+    const int pj = j * l - j * (j + 1) / 2, bj = j * (j + 1) / 2;   // P[pj + k] = (j, k), B[bj + c] = (j, c)
+    const float d = P[pj + j];
+    if (!(d > 0.f) || !isfinite(d)) {        // uniform: every thread read the same pivot
+      if (t == 0) fail[0] = 1;
+      return;
+    }
+    const float invd = 1.f / d;
+    if (t == 0) invr[j] = 1.f / sqrtf(d);
+    float pjk[4], bjc[4], g[8];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int k = 32 * c + lane;
+      pjk[c] = (k > j && k < l) ? P[pj + k] : 0.f;
+      bjc[c] = (k <= j) ? B[bj + k] : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = j + 1 + w + 16 * r;
+      g[r] = i < l ? P[pj + i] * invd : 0.f;
+    }
+    // upper: rows i, columns k >= i
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = j + 1 + w + 16 * r;
+      if (i >= l) break;                      // uniform across the warp
+      const int pi = i * l - i * (i + 1) / 2;
+      float v[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int k = 32 * c + lane;
+        v[c] = (k >= i && k < l) ? P[pi + k] : 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int k = 32 * c + lane;
+        if (k >= i && k < l) P[pi + k] = fmaf(-g[r], pjk[c], v[c]);
+      }
+    }
+    // lower: rows i, columns c <= j
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = j + 1 + w + 16 * r;
+      if (i >= l) break;
+      const int bi = i * (i + 1) / 2;
+      float v[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int cc = 32 * c + lane;
+        v[c] = (cc <= j) ? B[bi + cc] : 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int cc = 32 * c + lane;
+        if (cc <= j) B[bi + cc] = fmaf(-g[r], bjc[c], v[c]);
+      }
+    }
+    __syncthreads();
+  }
+  if (t == 0) fail[0] = 0;
+  // R (FP64, upper, zeros below) and R^-1 = Y^T (FP32, row-major): R[i][k] = P[i][k] / r_i, R^-1[c][j] = B[j][c] / r_j
+  for (int e = t; e < l * l; e += kCholFusedThreads) {
+    const int i = e / l, k = e % l;
+    G[e] = (k >= i) ? (double)(P[i * l - i * (i + 1) / 2 + k] * invr[i]) : 0.0;
+    Rinv32[e] = (k >= i) ? B[k * (k + 1) / 2 + i] * invr[k] : 0.f;
+  }
+}
+
+size_t chol32_fused_smem_bytes(int l) { return sizeof(float) * ((size_t)l * (l + 1) + (size_t)l); }
+
 // Least squares on the augmented FP64 Gram matrix G ((n+1) x (n+1), last column g = [S^T A]^T S^T b):
 // U = chol32(G11), then x0 = U^-1 U^-T g and x += U^-1 U^-T (g - G11 x) with FP64 residuals (iters times).
 // fail[0] = 1 when the FP32 factorization broke down (the FP64 kernels below then take over).
@@ -432,6 +581,69 @@ __global__ void __launch_bounds__(256) rowblock_mul_kernel(const float *in, int6
           if (SUB) out[r * ldo + c] -= acc[i][t];
           else out[r * ldo + c] = acc[i][t];
         }
+      }
+    }
+  }
+}
+
+// The same product for li, lo <= 128 with register tiles: 64 rows per block, both operands in shared memory
+// (the row block transposed, M padded to 128 columns with zeros), 256 threads as 16 x 16, thread (ty, tx)
+// owning rows 4 ty .. 4 ty + 3 and columns 4 tx .. 4 tx + 3 and 64 + 4 tx .. 64 + 4 tx + 3: three 16-byte
+// shared-memory loads per 32 FMAs.
+constexpr int RB2 = 64, RB2_LD = RB2 + 4;
+
+template <bool SUB>
+__global__ void __launch_bounds__(256) rowblock_tile_kernel(const float *in, int64_t m, int li, int64_t ldi,
+                                                            const float *__restrict__ M, int lo, int64_t ldm,
+                                                            float *out, int64_t ldo) {
+  extern __shared__ __align__(16) float rbs[];
+  float *Yt = rbs, *Ms = rbs + (size_t)li * RB2_LD;   // Yt[k][r] (li x RB2_LD), Ms[k][c] (li x 128)
+  const int64_t r0 = (int64_t)blockIdx.x * RB2;
+  // both operands by 4-byte cp.async, all in flight at once (a load-then-store loop would wait out the
+  // latency of every load in turn); out-of-range elements are zero-filled (source size 0)
+  for (int e = threadIdx.x; e < RB2 * li; e += blockDim.x) {
+    const int rr = e / li, k = e - rr * li;
+    const bool in_range = r0 + rr < m;
+    const float *src = in_range ? in + (r0 + rr) * ldi + k : in;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(
+                     Yt + k * RB2_LD + rr)),
+                 "l"(src), "r"(in_range ? 4 : 0)
+                 : "memory");
+  }
+  for (int e = threadIdx.x; e < li * 128; e += blockDim.x) {
+    const int k = e >> 7, c = e & 127;
+    const bool in_range = c < lo;
+    const float *src = in_range ? M + (int64_t)k * ldm + c : M;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(Ms + e)),
+                 "l"(src), "r"(in_range ? 4 : 0)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][8] = {};
+#pragma unroll 4
+  for (int k = 0; k < li; ++k) {
+    const float4 a = *reinterpret_cast<const float4 *>(Yt + k * RB2_LD + 4 * ty);
+    const float4 b0 = *reinterpret_cast<const float4 *>(Ms + k * 128 + 4 * tx);
+    const float4 b1 = *reinterpret_cast<const float4 *>(Ms + k * 128 + 64 + 4 * tx);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t r = r0 + 4 * ty + i;
+    if (r >= m) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = (j < 4 ? 4 * tx + j : 64 + 4 * tx + j - 4);
+      if (c < lo) {
+        if (SUB) out[r * ldo + c] -= acc[i][j];
+        else out[r * ldo + c] = acc[i][j];
       }
     }
   }
@@ -623,7 +835,8 @@ __global__ void jacobi_finish_kernel(const T *W, const T *V, int l, float *Ub, f
 // The same round-robin rotations as jacobi_smem_kernel, with W alone in shared memory (no rotation
 // accumulator: the other singular factor is recovered afterwards, see jacobi_right_kernel) and a group of G lanes
 // per column pair instead of a warp: a 1024-thread block rotates up to 1024 / G disjoint pairs per round, each
-// lane holding every G-th row (G = 16 for l <= 128, 8 up to l = 256).
+// lane holding every G-th row (G = 16 up to l = 128 and 8 above in FP64; FP32 uses it above l = 128 with G = 8,
+// and jacobi_vec_kernel below that).
 // G lanes per pair (8 or 16; 1024 / G pairs per round at most).
 template <typename T, int G>
 __global__ void __launch_bounds__(1024) jacobi_grp_kernel(T *Wg, int l, T tol, int max_sweeps, int *status) {
@@ -685,6 +898,92 @@ __global__ void __launch_bounds__(1024) jacobi_grp_kernel(T *Wg, int l, T tol, i
   if (sweep == max_sweeps && threadIdx.x == 0) rmc_report(status, RMC_ENUMERIC);
   __syncthreads();
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) Wg[e] = W[e];
+}
+
+// FP32 rotation for the vectorised kernel below.  The angle only steers convergence, so t is formed with fast
+// reciprocals and square roots; c = (1 + t^2)^-1/2 is correctly rounded and s = c t, so that c^2 + s^2 - 1 is an
+// unbiased rounding error and the column norms do not drift over the ~l x sweeps rotations of a column.
+__device__ __forceinline__ void rotation_fast(float alpha, float beta, float gamma, float &c, float &s) {
+  const float zeta = __fdividef(beta - alpha, 2.f * gamma);
+  const float x = fmaf(zeta, zeta, 1.f);
+  const float t = copysignf(__fdividef(1.f, fabsf(zeta) + x * rsqrtf(x)), zeta);
+  c = __frsqrt_rn(fmaf(t, t, 1.f));
+  s = c * t;
+}
+
+// One-sided Jacobi for l <= 128 (FP32), the rotations and ordering of jacobi_grp_kernel with 8 lanes per column
+// pair, columns padded with zero rows to ldw = 32 NV (zeros change neither inner products nor rotations): lane j
+// of a group holds rows 4 j + 32 v .. +3 (v < NV) of both columns as float4 registers, so a pair is loaded once,
+// reduced, rotated in registers and stored once.  The block has exactly (l' / 2) x 8 threads (l' = l rounded up
+// to even) and the round-robin indices advance without divisions.
+template <int NV>
+__global__ void __launch_bounds__(512) jacobi_vec_kernel(float *Wg, int l, float tol, int max_sweeps, int *status) {
+  extern __shared__ __align__(16) float jv[];
+  constexpr int ldw = 32 * NV;
+  __shared__ int rotated;
+#pragma unroll 8
+  for (int e = threadIdx.x; e < l * ldw; e += blockDim.x) {
+    const int col = e / ldw, r = e % ldw;
+    jv[e] = r < l ? Wg[(int64_t)col * l + r] : 0.f;
+  }
+  const int lp = (l + 1) & ~1;
+  const int grp = threadIdx.x >> 3, j = threadIdx.x & 7;
+  const int a = grp, b = lp - 1 - grp;
+  int ia = a - 1, ib = b - 1;   // (a - 1 + round) mod (lp - 1), (b - 1 + round) mod (lp - 1)
+  const float tol2 = tol * tol;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int round = 0; round < lp - 1; ++round) {
+      int p = a == 0 ? 0 : 1 + ia, q = b == 0 ? 0 : 1 + ib;
+      if (p > q) {
+        const int tt = p;
+        p = q;
+        q = tt;
+      }
+      ia = (ia + 1 == lp - 1) ? 0 : ia + 1;
+      ib = (ib + 1 == lp - 1) ? 0 : ib + 1;
+      // the padding column of an odd l sits out: its partner p (< l, touched by no other group in this round)
+      // stands in for it and nothing is stored
+      const bool live = q < l;
+      float4 x[NV], y[NV];
+      float alpha = 0.f, beta = 0.f, gamma = 0.f;
+      float4 *wp = reinterpret_cast<float4 *>(jv + (size_t)p * ldw) + j;
+      float4 *wq = reinterpret_cast<float4 *>(jv + (size_t)(live ? q : p) * ldw) + j;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        x[v] = wp[8 * v];
+        y[v] = wq[8 * v];
+        alpha = fmaf(x[v].x, x[v].x, fmaf(x[v].y, x[v].y, fmaf(x[v].z, x[v].z, fmaf(x[v].w, x[v].w, alpha))));
+        beta = fmaf(y[v].x, y[v].x, fmaf(y[v].y, y[v].y, fmaf(y[v].z, y[v].z, fmaf(y[v].w, y[v].w, beta))));
+        gamma = fmaf(x[v].x, y[v].x, fmaf(x[v].y, y[v].y, fmaf(x[v].z, y[v].z, fmaf(x[v].w, y[v].w, gamma))));
+      }
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {   // the 8 lanes of a group are aligned in the warp
+        alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+        beta += __shfl_xor_sync(0xffffffffu, beta, o);
+        gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
+      }
+      if (live && gamma != 0.f && gamma * gamma > tol2 * alpha * beta) {
+        float c, sn;
+        rotation_fast(alpha, beta, gamma, c, sn);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const float4 u = x[v], w = y[v];
+          wp[8 * v] = make_float4(c * u.x - sn * w.x, c * u.y - sn * w.y, c * u.z - sn * w.z, c * u.w - sn * w.w);
+          wq[8 * v] = make_float4(sn * u.x + c * w.x, sn * u.y + c * w.y, sn * u.z + c * w.z, sn * u.w + c * w.w);
+        }
+        if (j == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  if (sweep == max_sweeps && threadIdx.x == 0) rmc_report(status, RMC_ENUMERIC);
+  __syncthreads();
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) Wg[e] = jv[(e / l) * ldw + e % l];
 }
 
 // After jacobi_grp_kernel on R (R V = W, columns of W orthogonal): sigma_j = ||w_j|| (FP64 sum), the columns
@@ -1113,8 +1412,14 @@ __global__ void lsr_refine_finish_kernel(const double *xs, int n, int last, doub
 
 // ----------------------------------------------------------------------------------------- host helpers
 
-int gram_chunks(int64_t m, int l, int num_sms) {
-  const int T = (l + GRAM_T - 1) / GRAM_T;
+// Products and sums of the Gram matrix (launch_gram): FP32 products summed in FP32 over 32-row slices and in
+// double-FP32 across them; exact products in double-FP32; exact products in FP64 (least squares, refresh).
+enum GramMode { kGramF32, kGramExact, kGramF64 };
+
+static int gram_tile(int l, GramMode mode) { return (mode == kGramF64 || l <= 48) ? GRAM_T : 64; }
+
+int gram_chunks(int64_t m, int l, int num_sms, int tile) {
+  const int T = (l + tile - 1) / tile;
   const int pairs = T * (T + 1) / 2;
   int64_t chunks = (2 * (int64_t)num_sms + pairs - 1) / pairs;
   const int64_t max_chunks = (m + 255) / 256;
@@ -1124,32 +1429,55 @@ int gram_chunks(int64_t m, int l, int num_sms) {
 }
 
 size_t gram_ws(int64_t m, int l, int num_sms) {
-  return sizeof(double) * (size_t)gram_chunks(m, l, num_sms) * l * l;
+  const int c = std::max(gram_chunks(m, l, num_sms, GRAM_T), gram_chunks(m, l, num_sms, 64));
+  return sizeof(double) * (size_t)c * l * l;
 }
 
-// G (l x l FP64) = Y^T Y; fp64_products selects FP64 products (least squares) or FP32 products with FP64
-// sums across 32-row slices (CholeskyQR2).
-// With `gate`, the kernels run only if *gate is nonzero (decided on the device).
+// G (l x l FP64) = Y^T Y with the products and sums of `mode`.
+// With `gate` (kGramF64 only), the kernels run only if *gate is nonzero (decided on the device).
 int launch_gram(rmc_ctx *ctx, const float *Y, int64_t m, int l, int64_t ldy, double *G, double *part,
-                bool fp64_products = true, const int *gate = nullptr) {
-  const int T = (l + GRAM_T - 1) / GRAM_T;
+                GramMode mode, const int *gate = nullptr) {
+  if (gate && mode != kGramF64) return RMC_EINVAL;
+  const int tile = gram_tile(l, mode);
+  const int T = (l + tile - 1) / tile;
   const int pairs = T * (T + 1) / 2;
-  const int chunks = gram_chunks(m, l, ctx->num_sms);
+  const int chunks = gram_chunks(m, l, ctx->num_sms, tile);
   int64_t rows = (m + chunks - 1) / chunks;
   rows = (rows + GRAM_T - 1) / GRAM_T * GRAM_T;
+  const dim3 grid(pairs, chunks);
+  cudaStream_t st = ctx->stream;
   {
     RmcProf prof(ctx, RMC_K_GRAM);
-    if (fp64_products) gram_f64_kernel<<<dim3(pairs, chunks), 256, 0, ctx->stream>>>(Y, m, l, ldy, rows, part, gate);
-    else gram_f32_kernel<<<dim3(pairs, chunks), 256, 0, ctx->stream>>>(Y, m, l, ldy, rows, part);
+    if (mode == kGramF64) gram_f64_kernel<<<grid, 256, 0, st>>>(Y, m, l, ldy, rows, part, gate);
+    else if (mode == kGramExact && tile == 64) gram_tile_kernel<64, true><<<grid, 256, 0, st>>>(Y, m, l, ldy, rows, part);
+    else if (mode == kGramExact) gram_tile_kernel<32, true><<<grid, 256, 0, st>>>(Y, m, l, ldy, rows, part);
+    else if (tile == 64) gram_tile_kernel<64, false><<<grid, 256, 0, st>>>(Y, m, l, ldy, rows, part);
+    else gram_tile_kernel<32, false><<<grid, 256, 0, st>>>(Y, m, l, ldy, rows, part);
   }
   rmc_note_launch(2);
-  gram_reduce_kernel<<<rmc_blocks((int64_t)l * l, 256, 1024), 256, 0, ctx->stream>>>(part, chunks, l, G, gate);
+  gram_reduce_kernel<<<rmc_blocks((int64_t)l * l, 256, 1024), 256, 0, st>>>(part, chunks, l, tile, G, gate);
   RMC_LAUNCH_CHECK();
   return RMC_OK;
 }
 
 int launch_rowblock(cudaStream_t st, const float *in, int64_t m, int li, int64_t ldi, const float *M, int lo,
                     int64_t ldm, float *out, int64_t ldo, bool subtract = false) {
+  if (li >= 1 && li <= 128 && lo <= 128) {
+    const size_t smem2 = sizeof(float) * ((size_t)li * RB2_LD + (size_t)li * 128);
+    if (smem2 > 48 * 1024) {
+      RMC_TRY_CUDA(cudaFuncSetAttribute(rowblock_tile_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem2));
+      RMC_TRY_CUDA(cudaFuncSetAttribute(rowblock_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem2));
+    }
+    if (subtract)
+      rowblock_tile_kernel<true><<<rmc_blocks(m, RB2), 256, smem2, st>>>(in, m, li, ldi, M, lo, ldm, out, ldo);
+    else
+      rowblock_tile_kernel<false><<<rmc_blocks(m, RB2), 256, smem2, st>>>(in, m, li, ldi, M, lo, ldm, out, ldo);
+    rmc_note_launch();
+    RMC_LAUNCH_CHECK();
+    return RMC_OK;
+  }
   const size_t smem = sizeof(float) * RB * li;
   if (smem > 48 * 1024) {
     RMC_TRY_CUDA(cudaFuncSetAttribute(rowblock_mul_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1187,6 +1515,11 @@ int rmc_tc_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t
 int rmc_tc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
                      int64_t ldx, float *W, int64_t ldw, bool x3, void *ws);
 size_t rmc_tc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, bool x3, int num_sms);
+int rmc_tc_matmul_an_bf16(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
+                          int64_t ldx, float *Y, int64_t ldy, void *ws);
+int rmc_tc_matmul_at_bf16(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
+                          int64_t ldx, float *W, int64_t ldw, void *ws);
+size_t rmc_tc_matmul_bf16_ws(int64_t m, int64_t n, int64_t l, int which, int num_sms);
 
 size_t rmc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, int prec, int num_sms) {
   size_t simt = 0;
@@ -1194,8 +1527,9 @@ size_t rmc_matmul_ws(int64_t m, int64_t n, int64_t l, int which, int prec, int n
     const int splits = matmul_at_splits(m, n, l, num_sms);
     simt = splits > 1 ? sizeof(float) * (size_t)splits * l * n : 0;
   }
-  if (prec != RMC_TF32 && prec != RMC_TF32X3) return simt;
-  const size_t tc = rmc_tc_matmul_ws(m, n, l, which, prec == RMC_TF32X3, num_sms);
+  size_t tc = 0;
+  if (prec == RMC_TF32 || prec == RMC_TF32X3) tc = rmc_tc_matmul_ws(m, n, l, which, prec == RMC_TF32X3, num_sms);
+  else if (prec == RMC_BF16) tc = rmc_tc_matmul_bf16_ws(m, n, l, which, num_sms);
   return tc > simt ? tc : simt;
 }
 
@@ -1208,6 +1542,7 @@ int rmc_launch_matmul_an(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int
                          int64_t ldx, int prec, float *Y, int64_t ldy, void *ws) {
   if ((prec == RMC_TF32 || prec == RMC_TF32X3) && tma_rows_ok(A, lda))
     return rmc_tc_matmul_an(ctx, A, m, n, lda, X, l, ldx, Y, ldy, prec == RMC_TF32X3, ws);
+  if (prec == RMC_BF16 && tma_rows_ok(A, lda)) return rmc_tc_matmul_an_bf16(ctx, A, m, n, lda, X, l, ldx, Y, ldy, ws);
   dim3 grid((unsigned)((l + GT - 1) / GT), (unsigned)((m + GT - 1) / GT));
   {
     RmcProf prof(ctx, RMC_K_MATMUL_AN);
@@ -1222,6 +1557,7 @@ int rmc_launch_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int
                          int64_t ldx, int prec, float *W, int64_t ldw, void *ws) {
   if ((prec == RMC_TF32 || prec == RMC_TF32X3) && tma_rows_ok(A, lda))
     return rmc_tc_matmul_at(ctx, A, m, n, lda, X, l, ldx, W, ldw, prec == RMC_TF32X3, ws);
+  if (prec == RMC_BF16 && tma_rows_ok(A, lda)) return rmc_tc_matmul_at_bf16(ctx, A, m, n, lda, X, l, ldx, W, ldw, ws);
   const int splits = matmul_at_splits(m, n, l, ctx->num_sms);
   int64_t rows = (m + splits - 1) / splits;
   rows = (rows + GK - 1) / GK * GK;
@@ -1276,6 +1612,11 @@ static int launch_factor(rmc_ctx *ctx, double *G, int l, double *Rinv, float *Ri
   RmcProf prof(ctx, RMC_K_SMALL);
   if (smem > kMaxPackedBytes || ctx->small_fp64) {
     force_fp64_kernel<<<1, 1, 0, st>>>(&fail[0]);
+  } else if (l <= kCholFusedMaxL) {
+    const size_t smem_f = chol32_fused_smem_bytes(l);
+    if (smem_f > 48 * 1024)
+      RMC_TRY_CUDA(cudaFuncSetAttribute(chol32_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));
+    chol32_fused_kernel<<<1, kCholFusedThreads, smem_f, st>>>(G, l, Rinv32, fail);
   } else {
     const size_t smem_x = smem + sizeof(float) * (size_t)l * l;
     if (smem_x <= kMaxPackedBytes) {
@@ -1291,7 +1632,7 @@ static int launch_factor(rmc_ctx *ctx, double *G, int l, double *Rinv, float *Ri
     }
   }
   RMC_TRY_CUDA(cudaMemsetAsync(&fail[1], 0, sizeof(int), st));
-  if (refresh) RMC_TRY(launch_gram(ctx, refresh->Y, refresh->m, l, refresh->ldy, G, refresh->part, true, &fail[0]));
+  if (refresh) RMC_TRY(launch_gram(ctx, refresh->Y, refresh->m, l, refresh->ldy, G, refresh->part, kGramF64, &fail[0]));
   chol64_fallback_kernel<<<1, 1024, 0, st>>>(G, l, &fail[0], ctx->d_status, &fail[1]);
   tri_inverse_cols_kernel<<<l, 32, sizeof(double) * l, st>>>(G, l, Rinv, Rinv32, &fail[0], &fail[1]);
   rmc_note_launch(3);
@@ -1326,10 +1667,10 @@ int rmc_launch_cholqr2(rmc_ctx *ctx, float *Y, int64_t m, int64_t l_, int64_t ld
     // FP64 products (fp64_gram) only where they decide the result: the last pass.  An earlier pass only needs a
     // well-conditioned basis, which the FP32 products (summed in FP64) give; R = R2 R1 is exact up to the FP32
     // storage of the intermediate basis either way.
-    const bool fp64_products = (fp64_gram && pass == passes - 1) || ctx->small_fp64;
-    RMC_TRY(launch_gram(ctx, Y, m, l, ldy, G, part, fp64_products));
+    const GramMode mode = ctx->small_fp64 ? kGramF64 : (fp64_gram && pass == passes - 1) ? kGramExact : kGramF32;
+    RMC_TRY(launch_gram(ctx, Y, m, l, ldy, G, part, mode));
     const GramRefresh refresh{Y, m, ldy, part};
-    RMC_TRY(launch_factor(ctx, G, l, Rinv, Rinv32, fail, fp64_products ? nullptr : &refresh));
+    RMC_TRY(launch_factor(ctx, G, l, Rinv, Rinv32, fail, mode == kGramF64 ? nullptr : &refresh));
     RMC_TRY(launch_rowblock(st, Y, m, l, ldy, Rinv32, l, l, Y, ldy));
     if (R) {
       if (pass == 0) RMC_TRY_CUDA(cudaMemcpyAsync(R1, G, sizeof(double) * l * l, cudaMemcpyDeviceToDevice, st));
@@ -1350,6 +1691,30 @@ static bool jacobi_in_fp64(int l) { return l <= 32; }
 // The eight-lanes-per-pair Jacobi keeps W (l x l) in shared memory: FP32 up to l = 240, FP64 up to l = 120.
 static bool jacobi_grp_fits(int l, bool fp64) {
   return (size_t)l * l * (fp64 ? sizeof(double) : sizeof(float)) + 64 <= 227 * 1024;
+}
+
+// FP32 Jacobi of the column-major l x l W (l <= 128) with the vectorised kernel.
+static int launch_jacobi_vec(cudaStream_t st, float *W, int l, float tol, int *status) {
+  const int nv = (l + 31) / 32;
+  const size_t smem = sizeof(float) * 32 * nv * (size_t)l;
+  const unsigned threads = (unsigned)(((l + 1) & ~1) / 2 * 8);
+  switch (nv) {
+#define RMC_JV(NV)                                                                                            \
+  case NV:                                                                                                    \
+    if (smem > 48 * 1024)                                                                                     \
+      RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_vec_kernel<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                        (int)smem));                                                          \
+    jacobi_vec_kernel<NV><<<1, threads, smem, st>>>(W, l, tol, 60, status);                                   \
+    break;
+    RMC_JV(1)
+    RMC_JV(2)
+    RMC_JV(3)
+    RMC_JV(4)
+#undef RMC_JV
+    default:
+      return RMC_EINVAL;
+  }
+  return RMC_OK;
 }
 
 // Jacobi on R (FP64 row-major upper, l x l) with the group kernel: M (left singular vectors of R, row-major) and
@@ -1379,10 +1744,7 @@ static int launch_jacobi_grp(rmc_ctx *ctx, const double *R, int l, double *work,
     float *Wf = reinterpret_cast<float *>(work);
     to_colmajor_kernel<float><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, Wf);
     if (l <= 128) {
-      if (smem > 48 * 1024)
-        RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_grp_kernel<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-      jacobi_grp_kernel<float, 16><<<1, 1024, smem, st>>>(Wf, l, tol, 60, ctx->d_status);
+      RMC_TRY(launch_jacobi_vec(st, Wf, l, tol, ctx->d_status));
     } else {
       if (smem > 48 * 1024)
         RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_grp_kernel<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1548,7 +1910,7 @@ int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n_, i
   copy_column_kernel<<<rmc_blocks(s, 256, 1024), 256, 0, st>>>(Sb, s, const_cast<float *>(SA), ldsa, n);
   rmc_note_launch();
   // FP32 products summed in FP64 across 32-row slices: the factor only preconditions the refinement
-  RMC_TRY(launch_gram(ctx, SA, s, l, ldsa, b.G, b.gpart, false));
+  RMC_TRY(launch_gram(ctx, SA, s, l, ldsa, b.G, b.gpart, kGramF32));
   {
     RmcProf prof(ctx, RMC_K_SMALL);
     lsr_rf_init_kernel<<<rmc_blocks((int64_t)n * n, 256, 1024), 256, 0, st>>>(b.G, l, n, b.Rf, b.flags);
@@ -1588,7 +1950,7 @@ int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n_, i
   }
   // FP64 path (every kernel returns at once unless flags[0] is set): FP64 Gram, FP64 Cholesky of the augmented
   // matrix, back substitution
-  RMC_TRY(launch_gram(ctx, SA, s, l, ldsa, b.G, b.gpart, true, &b.flags[0]));
+  RMC_TRY(launch_gram(ctx, SA, s, l, ldsa, b.G, b.gpart, kGramF64, &b.flags[0]));
   {
     RmcProf prof(ctx, RMC_K_SMALL);
     chol64_fallback_kernel<<<1, 1024, 0, st>>>(b.G, l, &b.flags[0], ctx->d_status, &b.flags[1]);

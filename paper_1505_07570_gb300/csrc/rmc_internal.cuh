@@ -2,6 +2,7 @@
 // device status word, and the launchers each .cu file provides.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -52,8 +53,10 @@ struct RmcProf {
   ~RmcProf();
 };
 
-// Operand precisions that have a built path (RMC_BF16 is reserved in the header and rejected).
-static inline bool rmc_prec_ok(int prec) { return prec == RMC_FP32 || prec == RMC_TF32 || prec == RMC_TF32X3; }
+// Operand precisions of the products with A (FP32 CUDA cores; TF32, 3xTF32 and BF16 tensor cores).
+static inline bool rmc_prec_ok(int prec) {
+  return prec == RMC_FP32 || prec == RMC_TF32 || prec == RMC_TF32X3 || prec == RMC_BF16;
+}
 
 #define RMC_TRY_CUDA(expr)                                   \
   do {                                                       \
@@ -115,7 +118,10 @@ int rmc_launch_countsketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, i
                            void *ws);
 
 // srht.cu
-size_t rmc_srht_ws(int64_t m, int64_t n_total, int64_t s);
+size_t rmc_srht_ws(int64_t m, int64_t n_total, int64_t s, int num_sms);
+// tc_gemm.cu: a dense (unswizzled) 2-D TMA map of a row-major FP32 matrix
+int rmc_make_tmap_dense(CUtensorMap *map, const float *base, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                        int box_rows);
 int rmc_launch_srht(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b,
                     int64_t s, uint64_t seed, uint32_t instance, float *C, int64_t ldc, float *Cb, void *ws);
 

@@ -36,7 +36,19 @@ constexpr int kTransWarp0 = 2, kTransWarps = 2;   // warps 2-3 transpose staging
 constexpr int kRngWarp0 = 4, kRngWarps = 16;      // warps 4-19 draw G^T
 constexpr int kThreads = 32 * (kRngWarp0 + kRngWarps);
 constexpr int kTmemCols = kMT * kN;               // 512
-constexpr size_t kSmemBytes = 1024 + (size_t)kStgStages * kBBytes + (size_t)kStages * kStageBytes + 256;
+
+// TF32: an operand stage holds 32 rows of A (128 bytes of TF32 along K).  BF16: the same bytes hold 64 rows
+// (128 bytes of BF16), filled from two 32-row staging buffers.
+template <bool BF16>
+struct GaussCfg {
+  static constexpr int kKOp = BF16 ? 64 : 32;         // rows of A per operand stage
+  static constexpr int kStgPer = kKOp / kKStage;      // staging buffers per operand stage
+  static constexpr int kStg = BF16 ? 3 : kStgStages;  // staging ring
+  // barriers (256 bytes), then the b-column partials of the two producer groups (TF32)
+  static constexpr size_t kSmem = 1024 + (size_t)kStg * kBBytes + (size_t)kStages * kStageBytes + 256 +
+                                  sizeof(float) * kM * kMT;
+};
+static_assert(GaussCfg<true>::kSmem <= 227 * 1024, "shared memory");
 
 // Approximate special functions (PTX .approx with flush-to-zero).  Every argument here is a normal number (u in
 // [2^-24, 1), -2 ln u >= 2^-24, angles in (-pi, pi)), so the subnormal handling of the default forms is skipped.
@@ -79,6 +91,13 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
+// Two FP32 values as BF16 (round to nearest even), the first in the low half (the lower K index).
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
 // Byte offset of (row r, 16-byte chunk q) in a tile with 128-byte rows and 128-byte swizzle.
 __device__ __forceinline__ int swz_off(int r, int q) { return r * 128 + ((q ^ (r & 7)) << 4); }
 
@@ -104,36 +123,39 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
 }
 
 // grid: x = 256-row sketch range, y = 256-column tile of A, z = row range of A.
+template <bool BF16>
 __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_constant__ CUtensorMap tmap_a,
                                                                GaussArgs args) {
+  using C = GaussCfg<BF16>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~uintptr_t(1023));
-  unsigned char *staging = smem;                                   // kStgStages x 32 KB
-  unsigned char *operands = smem + kStgStages * kBBytes;           // kStages x (2 x 16 KB + 32 KB)
+  unsigned char *staging = smem;                                   // C::kStg x 32 KB
+  unsigned char *operands = smem + C::kStg * kBBytes;              // kStages x (2 x 16 KB + 32 KB)
   uint64_t *stg_full = reinterpret_cast<uint64_t *>(operands + kStages * kStageBytes);
-  uint64_t *stg_empty = stg_full + kStgStages;
-  uint64_t *full = stg_empty + kStgStages;
+  uint64_t *stg_empty = stg_full + C::kStg;
+  uint64_t *full = stg_empty + C::kStg;
   uint64_t *empty = full + kStages;
   uint64_t *done = empty + kStages;
   uint32_t *tmem_base_slot = reinterpret_cast<uint32_t *>(done + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_base_slot + 1);
+  float *bsum = reinterpret_cast<float *>(operands + kStages * kStageBytes + 256);   // kM kMT floats (TF32 b column)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t s0 = (int64_t)blockIdx.x * (kM * kMT);
   const int64_t n0 = (int64_t)blockIdx.y * kN;
   const int64_t k_begin = (int64_t)blockIdx.z * args.rows_per_split;
   const int64_t k_end = min(args.m, k_begin + args.rows_per_split);
-  const int num_it = k_end > k_begin ? (int)((k_end - k_begin + kKStage - 1) / kKStage) : 0;
+  const int num_it = k_end > k_begin ? (int)((k_end - k_begin + C::kKOp - 1) / C::kKOp) : 0;
   const int64_t groups = (args.s + 7) / 8;     // Philox blocks per row of the sketch stream
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStgStages; ++i) {
+    for (int i = 0; i < C::kStg; ++i) {
       tc::mbar_init(&stg_full[i], 1);
       tc::mbar_init(&stg_empty[i], kTransWarps);
     }
     for (int i = 0; i < kStages; ++i) {
-      tc::mbar_init(&full[i], kTransWarps + kRngWarps);
+      tc::mbar_init(&full[i], kTransWarps + kRngWarps / (BF16 ? 1 : 2));   // transposers + the stage's drawers
       tc::mbar_init(&empty[i], 1);
     }
     tc::mbar_init(done, 1);
@@ -151,9 +173,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
     // ---------------------------------------------------------------- TMA: A rows into staging (row-major)
     if (lane == 0) {
       int issued = 0;
-      for (int it = 0; it < num_it; ++it) {
-        const int st = it % kStgStages;
-        const uint32_t ph = (it / kStgStages) & 1;
+      for (int is = 0; is < num_it * C::kStgPer; ++is) {
+        const int st = is % C::kStg;
+        const uint32_t ph = (is / C::kStg) & 1;
         if (*abort_flag || !tc::mbar_wait(&stg_empty[st], ph ^ 1)) {
           *abort_flag = 1;
           rmc_report(args.status, RMC_ETIMEOUT);
@@ -161,20 +183,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
         }
         unsigned char *dst = staging + st * kBBytes;
         tc::mbar_arrive_expect_tx(&stg_full[st], kBBytes);
-        const int32_t y = (int32_t)(k_begin + (int64_t)it * kKStage);
+        const int32_t y = (int32_t)(k_begin + (int64_t)is * kKStage);
 #pragma unroll
         for (int atom = 0; atom < kN / 32; ++atom)
           tc::tma_load_2d(dst + atom * kAtomBytes, &tmap_a, (int32_t)(n0 + atom * 32), y, &stg_full[st]);
         ++issued;
       }
       // copies still in flight land before the CTA may exit
-      for (int it = issued > kStgStages ? issued - kStgStages : 0; it < issued; ++it)
-        (void)tc::mbar_wait(&stg_full[it % kStgStages], (it / kStgStages) & 1);
+      for (int is = issued > C::kStg ? issued - C::kStg : 0; is < issued; ++is)
+        (void)tc::mbar_wait(&stg_full[is % C::kStg], (is / C::kStg) & 1);
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::instr_desc(2, 2, 0, 0, kN, kM);
+      constexpr uint32_t idesc = BF16 ? tc::instr_desc(1, 1, 0, 0, kN, kM) : tc::instr_desc(2, 2, 0, 0, kN, kM);
       for (int it = 0; it < num_it; ++it) {
         const int st = it % kStages;
         const uint32_t ph = (it / kStages) & 1;
@@ -192,7 +214,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
           for (int kk = 0; kk < kKStage / 8; ++kk) {
             const uint64_t adesc = tc::smem_desc(base + mt * kOmegaBytes + kk * 32, 16, 1024, tc::kSwizzle128B);
             const uint64_t bdesc = tc::smem_desc(b_addr + kk * 32, 16, 1024, tc::kSwizzle128B);
-            tc::mma_tf32(tmem + mt * kN, adesc, bdesc, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+            // K = 8 (TF32) or 16 (BF16) per instruction: 32 bytes of each 128-byte row either way
+            if (BF16) tc::mma_f16(tmem + mt * kN, adesc, bdesc, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+            else tc::mma_tf32(tmem + mt * kN, adesc, bdesc, idesc, (it > 0 || kk > 0) ? 1u : 0u);
           }
         tc::mma_commit(&empty[st]);
       }
@@ -200,63 +224,109 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
     }
   } else if (warp < kRngWarp0) {
     // ---------------------------------------------------------------- transposers: staging -> K-major
-    // Unit (kq, cq): rows 4kq..4kq+3 x columns 4cq..4cq+3.  Lane l of an 8-lane group takes kq = l and
-    // cq = (d + l) mod 64, so both the swizzled reads and the swizzled writes of a group hit 8 distinct
-    // 16-byte bank groups.
     const int tl = (warp - kTransWarp0) * 32 + lane;       // 0..63
     const int l = tl & 7, grp = tl >> 3;                   // 8 groups of 8 lanes
+    int is = 0;                                            // staging buffers consumed
     for (int it = 0; it < num_it; ++it) {
-      const int st = it % kStages, sst = it % kStgStages;
-      if (!warp_wait(&stg_full[sst], (it / kStgStages) & 1, abort_flag, args.status)) break;
-      if (!warp_wait(&empty[st], ((it / kStages) & 1) ^ 1, abort_flag, args.status)) break;
-      const unsigned char *src = staging + sst * kBBytes;
+      const int st = it % kStages;
       unsigned char *btile = operands + st * kStageBytes + kMT * kOmegaBytes;
+      bool ok = true;
+      for (int h = 0; h < C::kStgPer; ++h, ++is) {
+        const int sst = is % C::kStg;
+        // the first staging buffer of the stage, then the operand buffer (free once its MMAs completed)
+        if (!warp_wait(&stg_full[sst], (is / C::kStg) & 1, abort_flag, args.status) ||
+            (h == 0 && !warp_wait(&empty[st], ((it / kStages) & 1) ^ 1, abort_flag, args.status))) {
+          ok = false;
+          break;
+        }
+        const unsigned char *src = staging + sst * kBBytes;
+        if (!BF16) {
+          // Unit (kq, cq): rows 4kq..4kq+3 x columns 4cq..4cq+3.  Lane l of an 8-lane group takes kq = l and
+          // cq = (d + l) mod 64, so both the swizzled reads and the swizzled writes of a group hit 8 distinct
+          // 16-byte bank groups.
 #pragma unroll 2
-      for (int d = grp; d < 64; d += 8) {
-        const int kq = l, cq = (d + l) & 63;
-        const int atom = cq >> 3, cc = cq & 7;
-        float4 v[4];
+          for (int d = grp; d < 64; d += 8) {
+            const int kq = l, cq = (d + l) & 63;
+            const int atom = cq >> 3, cc = cq & 7;
+            float4 v[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
-          v[t] = *reinterpret_cast<const float4 *>(src + atom * kAtomBytes + swz_off(4 * kq + t, cc));
-        const int c4 = 4 * cq;
-        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 0, kq)) = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
-        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 1, kq)) = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
-        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 2, kq)) = make_float4(v[0].z, v[1].z, v[2].z, v[3].z);
-        *reinterpret_cast<float4 *>(btile + swz_off(c4 + 3, kq)) = make_float4(v[0].w, v[1].w, v[2].w, v[3].w);
+            for (int t = 0; t < 4; ++t)
+              v[t] = *reinterpret_cast<const float4 *>(src + atom * kAtomBytes + swz_off(4 * kq + t, cc));
+            const int c4 = 4 * cq;
+            *reinterpret_cast<float4 *>(btile + swz_off(c4 + 0, kq)) = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+            *reinterpret_cast<float4 *>(btile + swz_off(c4 + 1, kq)) = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
+            *reinterpret_cast<float4 *>(btile + swz_off(c4 + 2, kq)) = make_float4(v[0].z, v[1].z, v[2].z, v[3].z);
+            *reinterpret_cast<float4 *>(btile + swz_off(c4 + 3, kq)) = make_float4(v[0].w, v[1].w, v[2].w, v[3].w);
+          }
+        } else {
+          // Unit (qk, cq): staging rows 8qk..8qk+7 x columns 4cq..4cq+3, written as BF16 into 16-byte K-chunk
+          // 4h + qk of rows 4cq..4cq+3 of the K-major tile.  Lane l of group grp takes cq = 8 grp + 2 (l & 3) +
+          // (l >> 2) and qk = (l + d) & 3 in pass d: the 8 lanes read 8 distinct 16-byte chunks (cq mod 8
+          // distinct) and write 8 distinct ones ((qk, cq & 1) distinct), so neither side has bank conflicts.
+          const int cq = 8 * grp + 2 * (l & 3) + (l >> 2);
+          const int cc = cq & 7;
+#pragma unroll 2
+          for (int d = 0; d < 4; ++d) {
+            const int qk = (l + d) & 3;
+            float4 v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+              v[t] = *reinterpret_cast<const float4 *>(src + grp * kAtomBytes + swz_off(8 * qk + t, cc));
+            const int q = 4 * h + qk;
+            *reinterpret_cast<uint4 *>(btile + swz_off(4 * cq + 0, q)) =
+                make_uint4(pack_bf16x2(v[0].x, v[1].x), pack_bf16x2(v[2].x, v[3].x), pack_bf16x2(v[4].x, v[5].x),
+                           pack_bf16x2(v[6].x, v[7].x));
+            *reinterpret_cast<uint4 *>(btile + swz_off(4 * cq + 1, q)) =
+                make_uint4(pack_bf16x2(v[0].y, v[1].y), pack_bf16x2(v[2].y, v[3].y), pack_bf16x2(v[4].y, v[5].y),
+                           pack_bf16x2(v[6].y, v[7].y));
+            *reinterpret_cast<uint4 *>(btile + swz_off(4 * cq + 2, q)) =
+                make_uint4(pack_bf16x2(v[0].z, v[1].z), pack_bf16x2(v[2].z, v[3].z), pack_bf16x2(v[4].z, v[5].z),
+                           pack_bf16x2(v[6].z, v[7].z));
+            *reinterpret_cast<uint4 *>(btile + swz_off(4 * cq + 3, q)) =
+                make_uint4(pack_bf16x2(v[0].w, v[1].w), pack_bf16x2(v[2].w, v[3].w), pack_bf16x2(v[4].w, v[5].w),
+                           pack_bf16x2(v[6].w, v[7].w));
+          }
+        }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&stg_empty[sst]);   // this warp's reads of the staging buffer are done
       }
+      if (!ok) break;
       tc::fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) {
-        tc::mbar_arrive(&stg_empty[sst]);
-        tc::mbar_arrive(&full[st]);
-      }
+      if (lane == 0) tc::mbar_arrive(&full[st]);
     }
   } else {
     // ---------------------------------------------------------------- G^T producers (+ b column)
-    // Thread = (K-row pair kp: rows 2 kp, 2 kp + 1 of the stage; group of 8 sketch rows g8 of tile mt).  Each
-    // K-row takes one Philox block of the sketch stream (8 normals = the 8 sketch rows of the group), and each
-    // sketch row's two values fill one 8-byte half of a 16-byte K-chunk of the K-major tile.
+    // Each K-row of a stage takes one Philox block of the sketch stream per group of 8 sketch rows (8 normals),
+    // and each thread draws 4 K-rows of one group, so a sketch row's 4 values land together in the K-major tile.
+    //   TF32: 32 K-rows per stage, covered by 8 warps: warps 4-11 draw the even stages and warps 12-19 the odd
+    //         ones (four independent Philox blocks per thread, and two stage times to draw them).  Thread = (K-row
+    //         quad kq = lane mod 8: one whole 16-byte K-chunk; group 4 (warp mod 8) + lane / 8 of the 32 groups of
+    //         the two tiles).
+    //   BF16: 64 K-rows per stage, all 16 warps on every stage.  Thread = (K-row quad kq = lane mod 16: one 8-byte
+    //         half of a 16-byte K-chunk; group 2 (warp mod 8) + lane / 16 of tile warp / 8).
     const int rw = warp - kRngWarp0;                        // 0..15
-    const int mt = rw >> 3;                                 // sketch tile of this warp
-    const int kp = lane & 15;                               // K-row pair: 16-byte chunk kp / 2, half kp % 2
-    const int g8 = 2 * (rw & 7) + (lane >> 4);              // sketch rows 8 g8 .. 8 g8 + 7 of the tile
+    constexpr int kTurns = BF16 ? 1 : 2;                    // warp groups taking turns on the stages
+    const int turn = BF16 ? 0 : rw >> 3;
+    const int kq = BF16 ? (lane & 15) : (lane & 7);
+    const int g8all = BF16 ? (rw >> 3) * 16 + 2 * (rw & 7) + (lane >> 4) : 4 * (rw & 7) + (lane >> 3);
+    const int mt = g8all >> 4, g8 = g8all & 15;             // sketch tile, group of 8 sketch rows within it
     const bool with_b = args.b != nullptr && blockIdx.y == 0;
     const uint64_t gidx = (uint64_t)((s0 + mt * kM) / 8 + g8);
     float bacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int it = 0; it < num_it; ++it) {
+    for (int it = turn; it < num_it; it += kTurns) {
       const int st = it % kStages;
-      const int64_t row0 = k_begin + (int64_t)it * kKStage + 2 * kp;
-      // b for this stage's two rows, loaded first so its latency hides behind the draws
-      float bv[2] = {0.f, 0.f};
+      const int64_t row0 = k_begin + (int64_t)it * C::kKOp + 4 * kq;
+      // b for this stage's rows, loaded first so its latency hides behind the draws
+      float bv[4] = {0.f, 0.f, 0.f, 0.f};
       if (with_b) {
 #pragma unroll
-        for (int t = 0; t < 2; ++t)
+        for (int t = 0; t < 4; ++t)
           if (row0 + t < k_end) bv[t] = __ldg(args.b + row0 + t);
       }
-      float z[2][8];
+      float z[4][8];
 #pragma unroll
-      for (int t = 0; t < 2; ++t) {
+      for (int t = 0; t < 4; ++t) {
         const int64_t row = row0 + t;
         if (row < k_end) {
           const uint4 w = philox_block(args.seed, kStreamGaussSketch, args.instance, (uint64_t)row * groups + gidx);
@@ -274,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
       }
       if (with_b) {
 #pragma unroll
-        for (int t = 0; t < 2; ++t)
+        for (int t = 0; t < 4; ++t)
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) bacc[jj] = fmaf(z[t][jj], bv[t], bacc[jj]);
       }
@@ -283,20 +353,37 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
         const int r = 8 * g8 + jj;
-        *reinterpret_cast<float2 *>(otile + swz_off(r, kp >> 1) + 8 * (kp & 1)) =
-            make_float2(to_tf32(z[0][jj]), to_tf32(z[1][jj]));
+        if (BF16)
+          *reinterpret_cast<uint2 *>(otile + swz_off(r, kq >> 1) + 8 * (kq & 1)) =
+              make_uint2(pack_bf16x2(z[0][jj], z[1][jj]), pack_bf16x2(z[2][jj], z[3][jj]));
+        else
+          *reinterpret_cast<float4 *>(otile + swz_off(r, kq)) =
+              make_float4(to_tf32(z[0][jj]), to_tf32(z[1][jj]), to_tf32(z[2][jj]), to_tf32(z[3][jj]));
       }
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&full[st]);
     }
     if (with_b) {
-      // sum over the 16 lanes (K-row pairs) that share a group, then write the b column of the partial
+      // sum over the lanes (K-row quads) that share a group, then over the warp groups that took turns, and
+      // write the b column of the partial
+      constexpr int kLanes = BF16 ? 16 : 8;
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj)
 #pragma unroll
-        for (int o = 1; o < 16; o <<= 1) bacc[jj] += __shfl_xor_sync(0xffffffffu, bacc[jj], o);
-      if (kp == 0) {
+        for (int o = 1; o < kLanes; o <<= 1) bacc[jj] += __shfl_xor_sync(0xffffffffu, bacc[jj], o);
+      if (!BF16) {
+        if (turn == 0 && kq == 0) {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) bsum[mt * kM + 8 * g8 + jj] = bacc[jj];
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kRngWarps) : "memory");   // the producer warps only
+        if (turn == 1 && kq == 0) {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) bacc[jj] += bsum[mt * kM + 8 * g8 + jj];
+        }
+      }
+      if (turn == kTurns - 1 && kq == 0) {
         float *pb = args.part + ((int64_t)blockIdx.z * args.s) * args.ntot;
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) {
@@ -338,6 +425,33 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
   if (warp == 1) {
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// Drawing alone (the bound of the sketch kernel's producers): Philox blocks b = 0 .. m ceil(s / 8) - 1 of the
+// sketch stream (block b is (row b / ceil(s / 8), group b mod ceil(s / 8)) of the operator), each turned into
+// eight normals as the producers do and rounded to TF32, summed per thread; 16 warps per CTA, one CTA per SM.
+__global__ void __launch_bounds__(512, 1) draw_floor_kernel(uint64_t seed, int64_t blocks, double *part) {
+  float acc = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t blk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; blk < blocks; blk += stride) {
+    const uint4 w = philox_block(seed, kStreamGaussSketch, 0, (uint64_t)blk);
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 p = box_muller16_fast(ws[q]);
+      acc += to_tf32(p.x) + to_tf32(p.y);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32] = acc;
+}
+
+__global__ void draw_floor_sum_kernel(const double *part, int n, double *sum) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *sum = s;
   }
 }
 
@@ -406,6 +520,23 @@ int tc_splits(int64_t m, int64_t tiles, int num_sms) {
 
 int rmc_tc_available(void) { return encode_fn() != nullptr; }
 
+// Row-major FP32 matrix as a 2-D tensor with a box_cols x box_rows box and no swizzle (rows of the box packed
+// densely in shared memory); box_cols * 4 must be a multiple of 16 bytes.
+int rmc_make_tmap_dense(CUtensorMap *map, const float *base, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                        int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return RMC_ECUDA;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 4) & 15) || ((box_cols * 4) & 15)) return RMC_EALIGN;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RMC_OK : RMC_EALIGN;
+}
+
 // Split count for a sketch of s rows and ntot output columns (the same formula sizes the workspace).
 // Split count from the number of output tiles; ntot may include the b column, so the column-tile count is
 // estimated as floor(ntot / 256) (exact for the usual n = 256 * k with or without b).  The workspace and the
@@ -423,7 +554,9 @@ size_t rmc_tc_gauss_ws(int64_t m, int64_t ntot, int64_t s, int prec, int num_sms
 
 int rmc_tc_gauss_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *b, int64_t s,
                         uint64_t seed, uint32_t instance, int prec, float *C, int64_t ldc, float *Cb, void *ws) {
-  if (prec != RMC_TF32) return RMC_EINVAL;
+  if (prec != RMC_TF32 && prec != RMC_BF16) return RMC_EINVAL;
+  const bool bf16 = prec == RMC_BF16;
+  const int kop = bf16 ? GaussCfg<true>::kKOp : GaussCfg<false>::kKOp;
   const int64_t ntot = n + (b ? 1 : 0);
   CUtensorMap map;
   RMC_TRY(make_tmap(&map, A, m, n, lda, kKStage));
@@ -431,7 +564,7 @@ int rmc_tc_gauss_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int6
   // the same count the workspace was sized with (gauss_splits_tc of ntot)
   const int splits = gauss_splits_tc(m, ntot, s, ctx->num_sms);
   int64_t rows = (m + splits - 1) / splits;
-  rows = (rows + kKStage - 1) / kKStage * kKStage;
+  rows = (rows + kop - 1) / kop * kop;
   GaussArgs a;
   a.b = b;
   a.m = m;
@@ -443,14 +576,33 @@ int rmc_tc_gauss_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int6
   a.rows_per_split = rows;
   a.part = static_cast<float *>(ws);
   a.status = ctx->d_status;
-  RMC_TRY_CUDA(cudaFuncSetAttribute(tc_gauss_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
-  {
+  const dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)splits);
+  if (bf16) {
+    constexpr size_t smem = GaussCfg<true>::kSmem;
+    RMC_TRY_CUDA(cudaFuncSetAttribute(tc_gauss_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RmcProf prof(ctx, RMC_K_GAUSSIAN);
-    tc_gauss_kernel<<<dim3((unsigned)mt, (unsigned)nt, (unsigned)splits), kThreads, kSmemBytes, ctx->stream>>>(map,
-                                                                                                              a);
+    tc_gauss_kernel<true><<<grid, kThreads, smem, ctx->stream>>>(map, a);
+  } else {
+    constexpr size_t smem = GaussCfg<false>::kSmem;
+    RMC_TRY_CUDA(cudaFuncSetAttribute(tc_gauss_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RmcProf prof(ctx, RMC_K_GAUSSIAN);
+    tc_gauss_kernel<false><<<grid, kThreads, smem, ctx->stream>>>(map, a);
   }
   tc_reduce_kernel<<<rmc_blocks(s * ntot, 256, 8192), 256, 0, ctx->stream>>>(
       static_cast<float *>(ws), splits, s, n, ntot, 1.0f / sqrtf((float)s), C, ldc, Cb);
+  rmc_note_launch(2);
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
+extern "C" int rmc_gaussian_draw_floor(rmc_ctx *ctx, int64_t m, int64_t s, uint64_t seed, double *sum) {
+  if (!ctx || !sum || m < 1 || s < 1 || m > (int64_t(1) << 31) || s > (int64_t(1) << 31)) return RMC_EINVAL;
+  const int grid = ctx->num_sms;
+  const int nparts = grid * 16;
+  RMC_TRY(rmc_ws_reserve(ctx, sizeof(double) * (size_t)nparts));
+  double *part = static_cast<double *>(ctx->ws);
+  draw_floor_kernel<<<grid, 512, 0, ctx->stream>>>(seed, m * ((s + 7) / 8), part);
+  draw_floor_sum_kernel<<<1, 32, 0, ctx->stream>>>(part, nparts, sum);
   rmc_note_launch(2);
   RMC_LAUNCH_CHECK();
   return RMC_OK;
@@ -868,6 +1020,370 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
   }
 }
 
+// ============================================================================ BF16 products with A
+// RMC_BF16: both operands rounded to BF16 (8-bit mantissa), FP32 accumulation in tensor memory (kind::f16).
+// A stays FP32 in HBM and is converted on chip; X^T is converted once in global memory.  An operand stage holds
+// 64 values of K per 128-byte row (the TF32 stage holds 32), so the MMA issue and the descriptors are those of
+// the TF32 kernels with K = 16 per instruction.
+
+// Y = A X: A arrives as two 128 x 32 FP32 boxes per stage; warps 2-7 write its BF16 K-major tile (row r, 16-byte
+// K-chunk q from the FP32 chunks 2(q mod 4), 2(q mod 4) + 1 of half q / 4; 8 lanes on 8 rows, so reads and
+// writes both hit 8 distinct bank groups); the X^T tile arrives in BF16 by TMA.
+template <int NPAD>
+struct AnBfCfg {
+  static constexpr int kA32 = 128 * 64 * 4;            // FP32 staging: 128 rows x 64 values of K
+  static constexpr int kA16 = 128 * 128;               // BF16 operand: 128 rows x 64 values
+  static constexpr int kX = NPAD * 128;                // X^T: NPAD rows x 64 BF16
+  static constexpr int kStage = kA32 + kA16 + kX;
+  static constexpr int kFit = (int)((kSmemCap - 2048) / kStage);
+  static constexpr int kStages = kFit > 4 ? 4 : kFit;
+  static constexpr size_t kSmem = 1024 + (size_t)kStages * kStage + 256;
+};
+
+template <int NPAD>
+__global__ void __launch_bounds__(kAnThreads, 1) tc_an_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
+                                                                   const __grid_constant__ CUtensorMap tmap_x16,
+                                                                   int64_t m, int64_t n, int64_t l, float *Y,
+                                                                   int64_t ldy, int *status) {
+  using Cfg = AnBfCfg<NPAD>;
+  constexpr int kS = Cfg::kStages;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~uintptr_t(1023));
+  // stage: A FP32 (two 16 KB halves) | A BF16 | X^T BF16
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kS * Cfg::kStage);
+  uint64_t *conv = full + kS;
+  uint64_t *empty = conv + kS;
+  uint64_t *done = empty + kS;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = (int64_t)blockIdx.x * 128;
+  const int num_it = (int)((n + 63) / 64);
+  constexpr uint32_t kCols = NPAD < 32 ? 32 : NPAD;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kS; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&conv[i], kAnConvWarps);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(done, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmap_a);
+    tc::prefetch_tmap(&tmap_x16);
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, kCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < num_it; ++it) {
+        const int st = it % kS;
+        if (*abort_flag || !tc::mbar_wait(&empty[st], ((it / kS) & 1) ^ 1)) {
+          *abort_flag = 1;
+          rmc_report(status, RMC_ETIMEOUT);
+          break;
+        }
+        unsigned char *stage = smem + st * Cfg::kStage;
+        tc::mbar_arrive_expect_tx(&full[st], Cfg::kA32 + Cfg::kX);
+        const int32_t kx = (int32_t)((int64_t)it * 64);
+        tc::tma_load_2d(stage, &tmap_a, kx, (int32_t)row0, &full[st]);
+        tc::tma_load_2d(stage + Cfg::kA32 / 2, &tmap_a, kx + 32, (int32_t)row0, &full[st]);
+        tc::tma_load_2d(stage + Cfg::kA32 + Cfg::kA16, &tmap_x16, kx, 0, &full[st]);
+        ++issued;
+      }
+      for (int it = issued > kS ? issued - kS : 0; it < issued; ++it)
+        (void)tc::mbar_wait(&full[it % kS], (it / kS) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::instr_desc(1, 1, 0, 0, NPAD, 128);
+      for (int it = 0; it < num_it; ++it) {
+        const int st = it % kS;
+        if (*abort_flag || !tc::mbar_wait(&conv[st], (it / kS) & 1)) {
+          *abort_flag = 1;
+          rmc_report(status, RMC_ETIMEOUT);
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t a_addr = tc::smem_u32(smem + st * Cfg::kStage + Cfg::kA32);
+        const uint32_t x_addr = a_addr + Cfg::kA16;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t ad = tc::smem_desc(a_addr + kk * 32, 16, 1024, tc::kSwizzle128B);
+          const uint64_t xd = tc::smem_desc(x_addr + kk * 32, 16, 1024, tc::kSwizzle128B);
+          tc::mma_f16(tmem, ad, xd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+        }
+        tc::mma_commit(&empty[st]);
+      }
+      tc::mma_commit(done);
+    }
+  } else {
+    // warps 2-7: FP32 staging -> BF16 K-major operand
+    const int ct = threadIdx.x - 64;
+    for (int it = 0; it < num_it; ++it) {
+      const int st = it % kS;
+      if (!warp_wait(&full[st], (it / kS) & 1, abort_flag, status)) break;
+      const unsigned char *a32 = smem + st * Cfg::kStage;
+      unsigned char *a16 = smem + st * Cfg::kStage + Cfg::kA32;
+      for (int e = ct; e < 1024; e += 32 * kAnConvWarps) {
+        const int r = ((e >> 6) << 3) | (e & 7), q = (e >> 3) & 7;
+        const unsigned char *src = a32 + (q >> 2) * (Cfg::kA32 / 2);
+        const float4 u = *reinterpret_cast<const float4 *>(src + swz_off(r, 2 * (q & 3)));
+        const float4 v = *reinterpret_cast<const float4 *>(src + swz_off(r, 2 * (q & 3) + 1));
+        *reinterpret_cast<uint4 *>(a16 + swz_off(r, q)) =
+            make_uint4(pack_bf16x2(u.x, u.y), pack_bf16x2(u.z, u.w), pack_bf16x2(v.x, v.y), pack_bf16x2(v.z, v.w));
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&conv[st]);
+    }
+    if (warp >= 4) {
+      const int q = warp & 3;
+      const bool ok = warp_wait(done, 0, abort_flag, status);
+      tc::tc_fence_after();
+      const int64_t row = row0 + q * 32 + lane;
+      if (ok) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < NPAD; c0 += 32) {
+          float v[32];
+          tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+          if (row < m) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (c0 + i < l) Y[row * ldy + c0 + i] = v[i];
+          }
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, kCols);
+  }
+}
+
+// W = X^T A over a row range of A: the X^T tiles arrive in BF16 by TMA; A is staged in FP32 32 rows at a time
+// (two staging buffers per 64-row operand stage) and converted + transposed by warps 2-5 into the BF16 K-major
+// tile, with the lane mapping of the BF16 Gaussian kernel (conflict-free reads and writes).
+template <int MT>
+struct AtBfCfg {
+  static constexpr int NC = 256;
+  static constexpr int kStg = NC * kKStage * 4;        // 32 KB of FP32 staging per 32 rows
+  static constexpr int kStgRing = 3;
+  static constexpr int kXt = MT * 128 * 128;           // MT x (128 rows x 64 BF16)
+  static constexpr int kB = NC * 128;                  // NC rows x 64 BF16
+  static constexpr int kStage = kXt + kB;
+  static constexpr size_t kSmem = 1024 + (size_t)kStgRing * kStg + (size_t)kStages * kStage + 256;
+  static_assert(kSmem <= kSmemCap, "tc_at_bf16_kernel shared memory");
+};
+
+template <int MT>
+__global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_bf16_kernel(
+    const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_x16, int64_t m, int64_t n,
+    int64_t l, int64_t rows_per_split, float *part, int *status) {
+  using Cfg = AtBfCfg<MT>;
+  constexpr int NC = Cfg::NC, kR = Cfg::kStgRing;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~uintptr_t(1023));
+  unsigned char *staging = smem;
+  unsigned char *operands = smem + kR * Cfg::kStg;
+  uint64_t *stg_full = reinterpret_cast<uint64_t *>(operands + kStages * Cfg::kStage);
+  uint64_t *stg_empty = stg_full + kR;
+  uint64_t *full = stg_empty + kR;
+  uint64_t *empty = full + kStages;
+  uint64_t *done = empty + kStages;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n0 = (int64_t)blockIdx.x * NC;
+  const int64_t k_begin = (int64_t)blockIdx.z * rows_per_split;
+  const int64_t k_end = min(m, k_begin + rows_per_split);
+  const int num_it = k_end > k_begin ? (int)((k_end - k_begin + 63) / 64) : 0;
+  constexpr uint32_t kCols = MT * NC;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kR; ++i) {
+      tc::mbar_init(&stg_full[i], 1);
+      tc::mbar_init(&stg_empty[i], kAtTrans);
+    }
+    for (int i = 0; i < kStages; ++i) {
+      tc::mbar_init(&full[i], kAtTrans + 1);         // the transposer warps + the X^T TMA arrival
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(done, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmap_a);
+    tc::prefetch_tmap(&tmap_x16);
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, kCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;   // staging buffers
+      bool failed = false;
+      for (int it = 0; it < num_it && !failed; ++it) {
+        const int st = it % kStages;
+        // rows k_begin + 64 it .. +63 of A (row ranges are whole 64-row stages, so a stage never reaches into the
+        // next range; rows past m arrive as zeros)
+        for (int h = 0; h < 2; ++h) {
+          const int is = 2 * it + h, sst = is % kR;
+          if (*abort_flag || !tc::mbar_wait(&stg_empty[sst], ((is / kR) & 1) ^ 1)) {
+            failed = true;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&stg_full[sst], Cfg::kStg);
+          const int32_t y = (int32_t)(k_begin + (int64_t)is * kKStage);
+#pragma unroll
+          for (int atom = 0; atom < NC / 32; ++atom)
+            tc::tma_load_2d(staging + sst * Cfg::kStg + atom * kAtomBytes, &tmap_a, (int32_t)(n0 + atom * 32), y,
+                            &stg_full[sst]);
+          ++issued;
+        }
+        if (failed || !tc::mbar_wait(&empty[st], ((it / kStages) & 1) ^ 1)) {
+          failed = true;
+          break;
+        }
+        unsigned char *xt = operands + st * Cfg::kStage;
+        tc::mbar_arrive_expect_tx(&full[st], Cfg::kXt);
+        const int32_t y = (int32_t)(k_begin + (int64_t)it * 64);
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) tc::tma_load_2d(xt + mt * 128 * 128, &tmap_x16, y, mt * 128, &full[st]);
+      }
+      if (failed) {
+        *abort_flag = 1;
+        rmc_report(status, RMC_ETIMEOUT);
+      }
+      for (int is = issued > kR ? issued - kR : 0; is < issued; ++is)
+        (void)tc::mbar_wait(&stg_full[is % kR], (is / kR) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::instr_desc(1, 1, 0, 0, NC, kM);
+      for (int it = 0; it < num_it; ++it) {
+        const int st = it % kStages;
+        if (*abort_flag || !tc::mbar_wait(&full[st], (it / kStages) & 1)) {
+          *abort_flag = 1;
+          rmc_report(status, RMC_ETIMEOUT);
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t base = tc::smem_u32(operands + st * Cfg::kStage);
+        const uint32_t b_addr = base + Cfg::kXt;
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t xd = tc::smem_desc(base + mt * 128 * 128 + kk * 32, 16, 1024, tc::kSwizzle128B);
+            const uint64_t ad = tc::smem_desc(b_addr + kk * 32, 16, 1024, tc::kSwizzle128B);
+            tc::mma_f16(tmem + mt * NC, xd, ad, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+          }
+        tc::mma_commit(&empty[st]);
+      }
+      tc::mma_commit(done);
+    }
+  } else {
+    if (warp < 2 + kAtTrans) {
+      const int tl = (warp - 2) * 32 + lane;             // 0..127
+      const int l8 = tl & 7, grp = tl >> 3;              // 16 groups of 8 lanes
+      const int atom = grp & 7, dset = grp >> 3;         // two groups per 32-column atom, two passes each
+      const int cq = 8 * atom + 2 * (l8 & 3) + (l8 >> 2);
+      const int cc = cq & 7;
+      int is = 0;
+      for (int it = 0; it < num_it; ++it) {
+        const int st = it % kStages;
+        if (!warp_wait(&empty[st], ((it / kStages) & 1) ^ 1, abort_flag, status)) break;
+        unsigned char *btile = operands + st * Cfg::kStage + Cfg::kXt;
+        bool ok = true;
+        for (int h = 0; h < 2; ++h, ++is) {
+          const int sst = is % kR;
+          if (!warp_wait(&stg_full[sst], (is / kR) & 1, abort_flag, status)) {
+            ok = false;
+            break;
+          }
+          const unsigned char *src = staging + sst * Cfg::kStg;
+#pragma unroll
+          for (int dd = 0; dd < 2; ++dd) {
+            const int qk = (l8 + 2 * dset + dd) & 3;
+            float4 v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+              v[t] = *reinterpret_cast<const float4 *>(src + atom * kAtomBytes + swz_off(8 * qk + t, cc));
+            const int q = 4 * h + qk;
+            *reinterpret_cast<uint4 *>(btile + swz_off(4 * cq + 0, q)) =
+                make_uint4(pack_bf16x2(v[0].x, v[1].x), pack_bf16x2(v[2].x, v[3].x), pack_bf16x2(v[4].x, v[5].x),
+                           pack_bf16x2(v[6].x, v[7].x));
+            *reinterpret_cast<uint4 *>(btile + swz_off(4 * cq + 1, q)) =
+                make_uint4(pack_bf16x2(v[0].y, v[1].y), pack_bf16x2(v[2].y, v[3].y), pack_bf16x2(v[4].y, v[5].y),
+                           pack_bf16x2(v[6].y, v[7].y));
+            *reinterpret_cast<uint4 *>(btile + swz_off(4 * cq + 2, q)) =
+                make_uint4(pack_bf16x2(v[0].z, v[1].z), pack_bf16x2(v[2].z, v[3].z), pack_bf16x2(v[4].z, v[5].z),
+                           pack_bf16x2(v[6].z, v[7].z));
+            *reinterpret_cast<uint4 *>(btile + swz_off(4 * cq + 3, q)) =
+                make_uint4(pack_bf16x2(v[0].w, v[1].w), pack_bf16x2(v[2].w, v[3].w), pack_bf16x2(v[4].w, v[5].w),
+                           pack_bf16x2(v[6].w, v[7].w));
+          }
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&stg_empty[sst]);
+        }
+        if (!ok) break;
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&full[st]);
+      }
+    }
+    if (warp >= 4) {
+      const int ew = warp - 4, et = ew >> 2, q = warp & 3;
+      const bool ok = warp_wait(done, 0, abort_flag, status);
+      tc::tc_fence_after();
+      const int64_t row = (int64_t)et * kM + q * 32 + lane;    // row of W (index into l)
+      const int64_t ncols = min((int64_t)NC, n - n0);
+      if (ok) {
+        float *prow = part + ((int64_t)blockIdx.z * l + row) * n + n0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NC; c0 += 32) {
+          float v[32];
+          if (num_it > 0) {
+            tc::tmem_ld32(tmem + (uint32_t)(et * NC) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = 0.f;
+          }
+          if (row < l) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (c0 + i < ncols) prow[c0 + i] = v[i];
+          }
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, kCols);
+  }
+}
+
 __global__ void sum_parts_kernel(const float *__restrict__ part, int splits, int64_t rows, int64_t cols,
                                  float *__restrict__ W, int64_t ldw) {
   const int64_t total = rows * cols;
@@ -1016,6 +1532,60 @@ int launch_at_t(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda,
   return RMC_OK;
 }
 
+// Row-major BF16 matrix (rows x cols, leading dimension ld elements) as a 2-D tensor with a 64 x box_rows box
+// (128 bytes along the row) and 128-byte swizzle: the K-major BF16 operand layout.
+int make_tmap_bf16(CUtensorMap *map, const uint16_t *base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return RMC_ECUDA;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 2) & 15)) return RMC_EALIGN;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RMC_OK : RMC_EALIGN;
+}
+
+int64_t x16_ld(int64_t cols) { return (cols + 7) / 8 * 8; }   // 16-byte row pitch for TMA
+
+// X (rows x cols, row-major FP32, ldx) transposed and rounded to BF16: X16[c][r] (cols x rows, ld16).
+__global__ void transpose_bf16_kernel(const float *__restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                                      uint16_t *__restrict__ X16, int64_t ld16) {
+  __shared__ float tile[32][33];
+  const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = by + k, c = bx + threadIdx.x;
+    if (r < rows && c < cols) tile[k][threadIdx.x] = X[r * ldx + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t c = bx + k, r = by + threadIdx.x;
+    if (r < rows && c < cols) X16[c * ld16 + r] = (uint16_t)(pack_bf16x2(tile[threadIdx.x][k], 0.f) & 0xFFFFu);
+  }
+}
+
+template <int NP>
+int an_bf16_launch(rmc_ctx *ctx, const CUtensorMap &ma, const CUtensorMap &mx, int64_t m, int64_t n, int64_t l,
+                   float *Y, int64_t ldy) {
+  const size_t smem = AnBfCfg<NP>::kSmem;
+  RMC_TRY_CUDA(cudaFuncSetAttribute(tc_an_bf16_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  tc_an_bf16_kernel<NP><<<(unsigned)((m + 127) / 128), kAnThreads, smem, ctx->stream>>>(ma, mx, m, n, l, Y, ldy,
+                                                                                         ctx->d_status);
+  return RMC_OK;
+}
+
+template <int MT>
+int at_bf16_launch(rmc_ctx *ctx, const CUtensorMap &ma, const CUtensorMap &mx, int64_t m, int64_t n, int64_t l,
+                   int64_t rows, int splits, float *part) {
+  const size_t smem = AtBfCfg<MT>::kSmem;
+  RMC_TRY_CUDA(cudaFuncSetAttribute(tc_at_bf16_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)((n + AtBfCfg<MT>::NC - 1) / AtBfCfg<MT>::NC), 1, (unsigned)splits);
+  tc_at_bf16_kernel<MT><<<grid, 32 * (4 + 4 * MT), smem, ctx->stream>>>(ma, mx, m, n, l, rows, part, ctx->d_status);
+  return RMC_OK;
+}
+
 }  // namespace
 
 // Workspace of the public tensor-core products: X^T (padded pitch; 3xTF32 also its remainder) plus the split
@@ -1064,4 +1634,69 @@ int rmc_tc_matmul_at(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t
     rmc_note_launch();
   }
   return launch_at_t(ctx, A, m, n, lda, Xt, Xl, l, ld, W, ldw, part, x3);
+}
+
+// BF16 operands (RMC_BF16): X^T rounded to BF16 in the workspace, A converted on chip.  Workspace: X^T in BF16
+// (padded pitch) and, for W = X^T A, the split partials.
+size_t rmc_tc_matmul_bf16_ws(int64_t m, int64_t n, int64_t l, int which, int num_sms) {
+  WsCarve w;
+  w.take<uint16_t>((size_t)l * x16_ld(which == 0 ? n : m));
+  if (which == 1) w.take<float>((size_t)at_splits(m, n, false, num_sms) * l * n);
+  return w.off;
+}
+
+int rmc_tc_matmul_an_bf16(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
+                          int64_t ldx, float *Y, int64_t ldy, void *ws) {
+  WsCarve w;
+  w.base = static_cast<char *>(ws);
+  const int64_t ld = x16_ld(n);
+  uint16_t *X16 = w.take<uint16_t>((size_t)l * ld);
+  dim3 grid((unsigned)((l + 31) / 32), (unsigned)((n + 31) / 32));
+  transpose_bf16_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(X, n, l, ldx, X16, ld);
+  rmc_note_launch();
+  CUtensorMap ma, mx;
+  const int npad = l <= 32 ? 32 : l <= 64 ? 64 : l <= 128 ? 128 : 256;
+  RMC_TRY(make_tmap(&ma, A, m, n, lda, 128));
+  RMC_TRY(make_tmap_bf16(&mx, X16, l, n, ld, npad));
+  {
+    RmcProf prof(ctx, RMC_K_MATMUL_AN);
+    int rc;
+    switch (npad) {
+      case 32: rc = an_bf16_launch<32>(ctx, ma, mx, m, n, l, Y, ldy); break;
+      case 64: rc = an_bf16_launch<64>(ctx, ma, mx, m, n, l, Y, ldy); break;
+      case 128: rc = an_bf16_launch<128>(ctx, ma, mx, m, n, l, Y, ldy); break;
+      default: rc = an_bf16_launch<256>(ctx, ma, mx, m, n, l, Y, ldy); break;
+    }
+    RMC_TRY(rc);
+  }
+  rmc_note_launch();
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
+int rmc_tc_matmul_at_bf16(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t lda, const float *X, int64_t l,
+                          int64_t ldx, float *W, int64_t ldw, void *ws) {
+  WsCarve w;
+  w.base = static_cast<char *>(ws);
+  const int64_t ld = x16_ld(m);
+  uint16_t *X16 = w.take<uint16_t>((size_t)l * ld);
+  const int splits = at_splits(m, n, false, ctx->num_sms);
+  float *part = w.take<float>((size_t)splits * l * n);
+  dim3 grid((unsigned)((l + 31) / 32), (unsigned)((m + 31) / 32));
+  transpose_bf16_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(X, m, l, ldx, X16, ld);
+  rmc_note_launch();
+  CUtensorMap ma, mx;
+  RMC_TRY(make_tmap(&ma, A, m, n, lda, kKStage));
+  RMC_TRY(make_tmap_bf16(&mx, X16, l, m, ld, 128));
+  int64_t rows = (m + splits - 1) / splits;
+  rows = (rows + 63) / 64 * 64;
+  {
+    RmcProf prof(ctx, RMC_K_MATMUL_AT);
+    RMC_TRY(l <= 128 ? at_bf16_launch<1>(ctx, ma, mx, m, n, l, rows, splits, part)
+                     : at_bf16_launch<2>(ctx, ma, mx, m, n, l, rows, splits, part));
+  }
+  sum_parts_kernel<<<rmc_blocks(l * n, 256, 8192), 256, 0, ctx->stream>>>(part, splits, l, n, W, ldw);
+  rmc_note_launch(2);
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
 }

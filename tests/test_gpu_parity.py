@@ -72,6 +72,7 @@ SKETCH_CASES = [
     (5000, 1, 17, 0),
     (1, 4, 1, 0),
     (70000, 20, 128, 4),
+    (20000, 9, 5000, 0),   # SRHT with s > 4096: one 4096-row block per work unit (no folding)
 ]
 
 
@@ -266,6 +267,77 @@ def test_lsr_gaussian_tf32(R, m, n, s):
     # residual ratio ||A x - b||^2 / ||A x* - b||^2 is stated within 10% of the FP64 oracle's.
     xs = lsr.lsr_exact(A, b)
     assert lsr.residual_ratio(A, b, x.cpu().numpy(), xs) <= lsr.residual_ratio(A, b, xo, xs) * 1.10
+
+
+# ------------------------------------------------ BF16 operands (kind::f16): the sketch and the products with A
+# BF16 keeps 8 mantissa bits: rounding both operands of every product gives a relative error of about
+# 2^-9 sqrt(2/3) = 1.6e-3, also for a sum of random-sign products; sketches and products are tested at 5e-3.
+
+@pytest.mark.parametrize("m,n,s,pad", [(2048, 512, 256, 0), (4097, 64, 300, 0), (70000, 20, 128, 4),
+                                       (1000, 36, 100, 4), (1, 4, 1, 0), (300000, 256, 1024, 0), (130, 260, 513, 0)])
+def test_gaussian_bf16_parity(R, m, n, s, pad):
+    A = workloads.lowrank() if (m, n) == (2048, 512) else workloads.gaussian(m, n, seed=m + n)
+    Ad = torch.zeros(m, n + pad, device="cuda")
+    Ad[:, :n] = dev(A)
+    C = R.rmc_sketch(Ad[:, :n], s, "gaussian", seed=11, prec="bf16")
+    R.rmc_sync()
+    ref = sketch.sketch(A, s, "gaussian", 11)
+    assert relfro(C.cpu().numpy(), ref) < 5e-3
+
+
+@pytest.mark.parametrize("m,n,s", [(20000, 64, 1024), (4000, 20, 200)])
+def test_lsr_gaussian_bf16(R, m, n, s):
+    """An FP64 emulation of these sketches with both operands rounded to BF16 gives x within 7e-4 of the
+    oracle's and a residual ratio ||A x - b||^2 / ||A x* - b||^2 of 1.30 and 1.14 against the oracle's 1.08 and
+    1.10 (BF16's rounding of S^T A is several times this regression's noise): stated as x within 1e-2 and the
+    ratio within 1.5 times the oracle's."""
+    A, b, _ = workloads.tall_lsr_numpy(m, n, seed=m + n)
+    x = R.rmc_lsr_sketch(dev(A), dev(b), s, "gaussian", seed=5, prec="bf16")
+    R.rmc_sync()
+    xo = lsr.lsr_sketch(A, b, s, "gaussian", 5)
+    assert relfro(x.cpu().numpy(), xo) < 1e-2
+    xs = lsr.lsr_exact(A, b)
+    assert lsr.residual_ratio(A, b, x.cpu().numpy(), xs) <= lsr.residual_ratio(A, b, xo, xs) * 1.5
+
+
+@pytest.mark.parametrize("m,n,l", [(2048, 512, 20), (1000, 300, 33), (70000, 200, 120), (4096, 1000, 200),
+                                   (333, 4100, 64), (5000, 260, 256), (100, 64, 8)])
+def test_matmuls_bf16(R, m, n, l):
+    A = workloads.gaussian(m, n, 1)
+    X1 = workloads.gaussian(n, l, 2)
+    X2 = workloads.gaussian(m, l, 3)
+    Y = R.rmc_matmul_an(dev(A), dev(X1), prec="bf16")
+    W = R.rmc_matmul_at(dev(A), dev(X2), prec="bf16")
+    R.rmc_sync()
+    A64 = A.astype(np.float64)
+    assert relfro(Y.cpu().numpy(), A64 @ X1) < 5e-3
+    assert relfro(W.cpu().numpy(), X2.astype(np.float64).T @ A64) < 5e-3
+
+
+def test_rsvd_bf16_factor_rank_workload(R):
+    """An FP64 emulation of this rSVD with every product's operands rounded to BF16 puts sigma within 1.0e-4
+    (q = 1) of the oracle's; the tensor core's truncating FP32 accumulation adds to it: stated as 2e-3, and the
+    projection error ||A - U S V^T||_F within 1% of the oracle's."""
+    A = workloads.factor_rank_numpy(4096, 2048, 256, seed=3)
+    k, p, q = 20, 10, 1
+    U, s, V = R.rmc_rsvd(dev(A), k, p, q, seed=7, prec="bf16")
+    R.rmc_sync()
+    Uo, so, Vo, _ = rsvd.rsvd(A, k, p, q, 7)
+    np.testing.assert_allclose(s.cpu().numpy(), so, rtol=2e-3)
+    A64 = A.astype(np.float64)
+    err = np.linalg.norm(A64 - (U.cpu().numpy() * s.cpu().numpy()) @ V.cpu().numpy().T)
+    erro = np.linalg.norm(A64 - (Uo * so) @ Vo.T)
+    assert abs(err - erro) <= 0.01 * erro
+
+
+@pytest.mark.parametrize("m,s", [(100, 64), (333, 1000)])
+def test_gaussian_draw_floor_draws_the_sketch_operator(R, m, s):
+    """The drawing-bound kernel draws exactly the normals of the sketch's operator: their sum matches the
+    oracle's FP64 matrix up to the TF32 rounding (2^-11 relative) and the approximate special functions."""
+    got = float(R.rmc_gaussian_draw_floor(m, s, 21).item())
+    R.rmc_sync()
+    G = philox.sketch_gaussian_matrix(21, m, s)
+    assert abs(got - G.sum()) <= 1e-3 * np.abs(G).sum()
 
 
 def test_lsr_ill_conditioned_falls_back_to_fp64(R):

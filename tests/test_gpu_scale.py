@@ -51,7 +51,7 @@ GAUSS_ROWS = [4 * g + j for g in (0, 317, 640, 1023) for j in range(4)]
 SRHT_POS = [0, 1, 777, 2048, 3000, 4095]
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("tf32", 2e-3)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("tf32", 2e-3), ("bf16", 5e-3)])
 def test_gaussian_sketch_full_size_sampled_rows(R, tall, prec, tol):
     _, _, Ab, Ab_h = tall
     C = R.rmc_sketch(Ab, 4096, "gaussian", SEED, prec=prec)
@@ -82,7 +82,7 @@ def test_countsketch_full_size_whole(R, tall):
 
 
 @pytest.mark.parametrize("kind,prec", [("countsketch", "fp32"), ("srht", "fp32"), ("gaussian", "tf32"),
-                                       ("gaussian", "fp32")])
+                                       ("gaussian", "fp32"), ("gaussian", "bf16")])
 @pytest.mark.parametrize("s", [1024, 4096])
 def test_lsr_full_size_solves_its_sketch(R, tall, kind, prec, s):
     """x of rmc_lsr_sketch is the FP64 least-squares solution of the FP32 sketch [S^T A, S^T b] (the same
@@ -122,7 +122,7 @@ def test_rsvd_full_size(R, big, q):
         return np.sqrt(a2 - float(np.sum(P * P)))
 
     res_k = proj_residual(Uo)
-    for prec, tol in (("fp32", 1e-4), ("tf32x3", 1e-4), ("tf32", 2e-3)):
+    for prec, tol in (("fp32", 1e-4), ("tf32x3", 1e-4), ("tf32", 2e-3), ("bf16", 5e-3)):
         U, s, V = R.rmc_rsvd(A, k, p, q, SEED, prec=prec)
         R.rmc_sync()
         np.testing.assert_allclose(s.cpu().numpy(), so, rtol=tol, err_msg=prec)
