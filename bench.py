@@ -36,9 +36,9 @@ GAUSS_PREC = os.environ.get("RMC_BENCH_GAUSS_PREC", "tf32")
 # DRAM bytes per row of A per launch from ncu captures of `python bench.py --probe <kind>` (A 262,144 x 256 + b):
 # dram__bytes_read.sum + dram__bytes_write.sum divided by 262,144.  Re-capture when a kernel changes.
 PROFILED_DRAM_BYTES_PER_ROW = {
-    "gaussian_sketch": (270.093056e6 + 4.715008e6) / 262144,
+    "gaussian_sketch": (270.385920e6 + 5.209600e6) / 262144,
     "srht_stage1": (268.572928e6 + 42.968832e6) / 262144,
-    "countsketch_gather": (271.633408e6 + 4.247552e6) / 262144,
+    "countsketch_gather": (271.636992e6 + 3.304704e6) / 262144,
 }
 
 

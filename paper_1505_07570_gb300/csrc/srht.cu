@@ -94,29 +94,31 @@ __device__ __forceinline__ void cp_async16(float4 *dst, const void *src, int byt
 //     and the phases take bits 0-3, 4-7, 8-11.
 // Swizzled slot of row r: r ^ ((r >> 4) & 7) (16-byte units).  Thread (q, h) = (t / 2, t % 2) transforms column
 // pair h (a float2) of 16 rows per phase, so 16 warps share the work; after the last phase the thread owns rows
-// r2 = q + 256 j (j < 16) and folds each into the pairs (c, r2) of the sample: pair p = off[r2] + u
-// (u < off[r2 + 1] - off[r2]) has group index cval[p].  A pair belongs to one thread and one h, so the
-// accumulators need no synchronisation.  Every wait is bounded (RMC_ETIMEOUT).  T out: [N1 / G][umax][slabs].
+// r2 = q + 256 j (j < 16); the pairs (c, r2) of the sample (pinfo[p] = (r2 << 3) | c) are then folded
+// pair-major: pair p, column pair h belongs to thread (p mod 256, h) in every block, so the accumulators need no
+// synchronisation.  Every wait is bounded (RMC_ETIMEOUT).  T out: [N1 / G][umax][slabs].
 template <bool kTma>
 __global__ void __launch_bounds__(kThreads, 1) srht_stage1_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                    const float *__restrict__ A, int64_t m, int64_t n,
                                                                    int64_t lda, const float *__restrict__ b,
                                                                    const uint32_t *__restrict__ sign_bits,
-                                                                   const uint32_t *__restrict__ off_g,
-                                                                   const uint8_t *__restrict__ cval_g, int64_t umax,
+                                                                   const uint32_t *__restrict__ npairs_g,
+                                                                   const uint16_t *__restrict__ pinfo_g, int64_t umax,
                                                                    int64_t slabs, int64_t N1, int G,
                                                                    float4 *__restrict__ T, bool vec, int *status) {
-  extern __shared__ __align__(16) float4 sm[];   // two tile buffers, sign words, pair offsets, groups, accumulators
+  // two tile buffers, sign words, pair records, accumulators; the base is aligned by hand (TMA destinations
+  // must be 128-byte aligned, and the static shared variables below come first)
+  extern __shared__ __align__(16) unsigned char srht_raw[];
+  float4 *sm = reinterpret_cast<float4 *>((reinterpret_cast<uintptr_t>(srht_raw) + 1023) & ~uintptr_t(1023));
   uint32_t *sgn = reinterpret_cast<uint32_t *>(sm + 2 * kRowsCta);   // 2 x kRowsCta / 32 sign words
-  uint32_t *off = sgn + 2 * (kRowsCta / 32);                           // kRowsCta + 1 pair offsets
-  uint8_t *cval = reinterpret_cast<uint8_t *>(off + kRowsCta + 4);     // kRowsCta pair groups
-  float2 *acc = reinterpret_cast<float2 *>(cval + kRowsCta);           // kRowsCta pairs x 2 halves (G > 1)
+  uint16_t *pinfo = reinterpret_cast<uint16_t *>(sgn + 2 * (kRowsCta / 32));   // (r2 << 3) | c of each pair
+  float2 *acc = reinterpret_cast<float2 *>(pinfo + kRowsCta);          // kRowsCta pairs x 2 halves (G > 1)
   __shared__ __align__(8) uint64_t full[2];
   __shared__ int go;
   const int64_t units = slabs * (N1 / G);
   const int t = threadIdx.x, q = t >> 1, h = t & 1;
-  for (int r = t; r <= kRowsCta; r += kThreads) off[r] = off_g[r];
-  for (int r = t; r < kRowsCta; r += kThreads) cval[r] = cval_g[r];
+  const int npairs = (int)*npairs_g;
+  for (int p = t; p < npairs; p += kThreads) pinfo[p] = pinfo_g[p];
   if (kTma && t == 0) {
     tc::mbar_init(&full[0], 1);
     tc::mbar_init(&full[1], 1);
@@ -260,29 +262,25 @@ __global__ void __launch_bounds__(kThreads, 1) srht_stage1_kernel(const __grid_c
       }
       __syncthreads();
     }
-    // phase 3: bits 8..11 (written back to the thread's own slots), then every pair (c, r2) of the rows r2 this
-    // thread holds, in a loop that is not unrolled (most rows have no pair; the code stays small)
+    // phase 3: bits 8..11, written back; then, after a barrier, thread (q, h) folds pairs q, q + 256, ... of the
+    // sample (column pair h): the same amount of work on every thread, whichever rows the pairs fall on
     {
 #pragma unroll
       for (int j = 0; j < 16; ++j) v[j] = S2[2 * swz(q | (j << 8))];
       fwht16(v);
 #pragma unroll
       for (int j = 0; j < 16; ++j) S2[2 * swz(q | (j << 8))] = v[j];
+      __syncthreads();
       float2 *Tout = reinterpret_cast<float2 *>(T + a * umax * slabs + slab) + h;
       const bool first = bb == 0, last = bb == G - 1;
-#pragma unroll 1
-      for (int j = 0; j < 16; ++j) {
-        const int r2 = q | (j << 8);
-        const uint32_t p0 = off[r2], p1 = off[r2 + 1];
-        if (p0 == p1) continue;
-        const float2 xv = S2[2 * swz(r2)];
-        for (uint32_t p = p0; p < p1; ++p) {
-          const float sg = (__popc((uint32_t)cval[p] & (uint32_t)bb) & 1) ? -1.f : 1.f;
-          float2 y = first ? make_float2(0.f, 0.f) : acc[2 * p + h];
-          y = make_float2(fmaf(sg, xv.x, y.x), fmaf(sg, xv.y, y.y));
-          if (last) Tout[(int64_t)p * slabs * 2] = y;
-          else acc[2 * p + h] = y;
-        }
+      for (int p = q; p < npairs; p += kThreads / 2) {
+        const uint32_t info = pinfo[p];
+        const float2 xv = S2[2 * swz((int)(info >> 3))];
+        const float sg = (__popc(info & 7u & (uint32_t)bb) & 1) ? -1.f : 1.f;
+        float2 y = first ? make_float2(0.f, 0.f) : acc[2 * p + h];
+        y = make_float2(fmaf(sg, xv.x, y.x), fmaf(sg, xv.y, y.y));
+        if (last) Tout[(int64_t)p * slabs * 2] = y;
+        else acc[2 * p + h] = y;
       }
     }
   }
@@ -322,15 +320,15 @@ __global__ void srht_stage2_kernel(const float4 *__restrict__ T, int64_t groups,
 }
 
 // The pairs (c, r2) of the sample: v = r mod (4096 G) = c 4096 + r2 for every sampled row r.  mark[v] = 1, then in
-// one block: off[r2] = number of pairs with a smaller r2 (pairs ordered by r2, then c), cval[off[r2] + u] = the
-// u-th group index c present for r2, slotv[v] = that pair's position.
+// one block: off[r2] = number of pairs with a smaller r2 (pairs ordered by r2, then c; off[4096] = their count),
+// pinfo[p] = (r2 << 3) | c of pair p, slotv[v] = that pair's position.
 __global__ void srht_mark_pairs_kernel(const int64_t *idx, int64_t s, int64_t span, uint32_t *mark) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < s; k += (int64_t)gridDim.x * blockDim.x)
     mark[idx[k] % span] = 1u;
 }
 
-__global__ void __launch_bounds__(1024) srht_pairs_kernel(const uint32_t *mark, int G, uint32_t *off, uint8_t *cval,
-                                                          uint32_t *slotv) {
+__global__ void __launch_bounds__(1024) srht_pairs_kernel(const uint32_t *mark, int G, uint32_t *off,
+                                                          uint32_t *slotv, uint16_t *pinfo) {
   __shared__ uint32_t part[1024];
   constexpr int per = kRowsCta / 1024;
   const int lo = threadIdx.x * per;
@@ -351,7 +349,7 @@ __global__ void __launch_bounds__(1024) srht_pairs_kernel(const uint32_t *mark, 
     off[r2] = run;
     for (int c = 0; c < G; ++c)
       if (mark[c * kRowsCta + r2]) {
-        cval[run] = (uint8_t)c;
+        pinfo[run] = (uint16_t)((r2 << 3) | c);
         slotv[c * kRowsCta + r2] = run;
         ++run;
       }
@@ -395,7 +393,7 @@ struct SrhtBufs {
   int64_t *idx;
   uint32_t *sign_bits;
   uint32_t *mark, *off, *slotv;
-  uint8_t *cval;
+  uint16_t *pinfo;
   float4 *T;
   void *sample_ws;
 };
@@ -407,7 +405,7 @@ SrhtBufs srht_carve(WsCarve &w, const SrhtPlan &p, int64_t s) {
   b.mark = w.take<uint32_t>(p.N2 * p.G);
   b.off = w.take<uint32_t>(p.N2 + 4);
   b.slotv = w.take<uint32_t>(p.N2 * p.G);
-  b.cval = w.take<uint8_t>(p.N2);
+  b.pinfo = w.take<uint16_t>(p.N2);
   b.T = w.take<float4>((p.N1 / p.G) * p.umax * p.slabs);
   b.sample_ws = w.take<char>(rmc_srht_sample_ws(p.N));
   return b;
@@ -434,7 +432,7 @@ int rmc_launch_srht(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t 
   RMC_TRY(rmc_launch_srht_sample(ctx, seed, instance, p.N, s, bf.idx, bf.sample_ws));
   RMC_TRY_CUDA(cudaMemsetAsync(bf.mark, 0, sizeof(uint32_t) * span, st));
   srht_mark_pairs_kernel<<<rmc_blocks(s, 256, 1024), 256, 0, st>>>(bf.idx, s, span, bf.mark);
-  srht_pairs_kernel<<<1, 1024, 0, st>>>(bf.mark, p.G, bf.off, bf.cval, bf.slotv);
+  srht_pairs_kernel<<<1, 1024, 0, st>>>(bf.mark, p.G, bf.off, bf.slotv, bf.pinfo);
   srht_signs_kernel<<<rmc_blocks(m, 256, 4096), 256, 0, st>>>(seed, instance, m, bf.sign_bits);
   rmc_note_launch(3);
   RMC_LAUNCH_CHECK();
@@ -445,9 +443,9 @@ int rmc_launch_srht(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t 
   CUtensorMap map;
   memset(&map, 0, sizeof(map));
   const bool tma = vec && rmc_make_tmap_dense(&map, A, m, n, lda, 4, 256) == RMC_OK;
-  // tiles, sign words, pair offsets and groups, and (G > 1) the accumulators of 4096 pairs
-  const size_t smem = 2 * sizeof(float4) * kRowsCta + sizeof(uint32_t) * (2 * (kRowsCta / 32) + kRowsCta + 4) +
-                      kRowsCta + (p.G > 1 ? sizeof(float4) * kRowsCta : 0);
+  // alignment slack, tiles, sign words, pair records and (G > 1) the accumulators of 4096 pairs
+  const size_t smem = 1024 + 2 * sizeof(float4) * kRowsCta + sizeof(uint32_t) * 2 * (kRowsCta / 32) +
+                      sizeof(uint16_t) * kRowsCta + (p.G > 1 ? sizeof(float4) * kRowsCta : 0);
   auto kern = tma ? srht_stage1_kernel<true> : srht_stage1_kernel<false>;
   RMC_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // as many CTAs as are co-resident (one per SM), each looping over (a, slab) units of G items
@@ -462,7 +460,7 @@ int rmc_launch_srht(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t 
   {
     RmcProf prof(ctx, RMC_K_SRHT);
     kern<<<(unsigned)grid, kThreads, smem, st>>>(map, A, m, n, lda, b, (const uint32_t *)bf.sign_bits,
-                                                 (const uint32_t *)bf.off, (const uint8_t *)bf.cval, p.umax, p.slabs,
+                                                 (const uint32_t *)(bf.off + p.N2), (const uint16_t *)bf.pinfo, p.umax, p.slabs,
                                                  p.N1, p.G, bf.T, vec, ctx->d_status);
   }
   const float scale = 1.0f / sqrtf((float)s);
