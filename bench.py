@@ -526,7 +526,13 @@ def gaussian_forms_measure(torch, rmc, A, b):
     the product 2 m (n + 1) s, and the relative Frobenius difference from the FP32 form's sketch (the FP32 form
     is pinned to the oracle at 1e-5 by the tests; TF32 and BF16 differ from it by their operand rounding)."""
     m, n = A.shape
-    Ab = torch.cat([A, b[:, None]], dim=1).contiguous()
+    # [A, b] with a 16-byte row pitch, as the tensor-core and TMA paths need (a 257-float pitch would send every
+    # form to the CUDA-core fallback)
+    ld = (n + 1 + 3) // 4 * 4
+    Abp = torch.empty(m, ld, device=A.device, dtype=A.dtype)
+    Abp[:, :n] = A
+    Abp[:, n] = b
+    Ab = Abp[:, :n + 1]
     pk = peaks()
     out = {"workload": "tall-lsr %dx%d + b, Gaussian sketch of [A, b]" % (m, n), "calls": {}}
     # whole calls of the HBM-bound kinds (every kernel of the call, e.g. both SRHT stages), one call at a time
@@ -578,7 +584,7 @@ def gaussian_forms_measure(torch, rmc, A, b):
                                               torch.linalg.matrix_norm(ref))
                 rec["draw_floor_over_ms"] = floor_ms / ms   # 1.0: the sketch costs no more than drawing its normals
             out["calls"]["%s_s%d" % (prec, s)] = rec
-    del Ab
+    del Ab, Abp
     torch.cuda.empty_cache()
     return out
 
