@@ -722,7 +722,9 @@ def serve_measure(torch, rmc, rates=(100, 1000, 2500, 5000), window_s=2.0, pool=
     same 1e-4 singular-value tolerance against the oracle: equal stated error).  Reports completed requests/s
     and p50/p99 latency (submit to completion).  Load shedding: an arrival that finds max_outstanding requests
     queued or in flight is rejected and counted (their outputs hold device memory, so an overloaded stream would
-    otherwise grow without bound)."""
+    otherwise grow without bound).  Resident runs ("_resident"): every least-squares request on a problem shares
+    that problem's sketch (seed = pool index) and brings one of four right-hand sides of the problem; the server
+    keeps S^T A and its factor resident, so only the first request per problem sketches A."""
     import time
     import workloads
     ms_, ns_ = workloads.serve_pool(pool, seed=SEED)
@@ -737,54 +739,64 @@ def serve_measure(torch, rmc, rates=(100, 1000, 2500, 5000), window_s=2.0, pool=
     out = {"workload": "poisson stream, pool of %d resident problems m~logU[1e3,2e5] n~logU[32,1024]; 60%% lsr "
                        "(countsketch s=4n) / 40%% rsvd (k in {8,32,64}, p=8, q=1); budget 64 GB, %d streams"
                        % (pool, nstreams), "window_s": window_s, "runs": {}}
-    for prec in ("fp32", "tf32x3"):
-        for rate in rates:
-            arr = workloads.serve_arrivals(rate, window_s, pool, seed=SEED + rate)
-            srv = rmc.Server(budget, nstreams=nstreams, max_batch=256)
-            live, lat = {}, []
-            rejected, failed, spec_of = 0, [], {}
-            i, t0 = 0, time.perf_counter()
-            while True:
-                now = time.perf_counter() - t0
-                while i < len(arr) and arr[i]["t"] <= now:
-                    a = arr[i]
-                    if len(live) >= max_outstanding:
-                        rejected += 1
-                        i += 1
-                        continue
-                    A, b = mats[a["pool"]]
-                    n = A.shape[1]
-                    if a["kind"] == "lsr":
-                        r, o = rmc.lsr_request(A, b, a["s_factor"] * n, a["seed"])
-                        tk = srv.submit(r, sketch="countsketch", prec="fp32")
-                        spec_of[tk] = ("lsr", int(A.shape[0]), int(n), a["s_factor"] * n, a["seed"], a["pool"])
-                    else:
-                        k = max(1, min(a["k"], n - a["p"]))
-                        r, o = rmc.rsvd_request(A, k, a["p"], a["q"], a["seed"])
-                        tk = srv.submit(r, prec=prec)
-                        spec_of[tk] = ("rsvd", int(A.shape[0]), int(n), k, a["p"], a["q"], a["seed"], a["pool"])
-                    live[tk] = o
+    # the resident variant: one sketch per problem (seed = pool index) and a fresh right-hand side per least-squares
+    # request from a bank of four per problem; the server keeps S^T A and its factor resident (16 GB cap)
+    rhs_bank = [[torch.randn(A.shape[0], generator=g, device="cuda", dtype=torch.float32) for _ in range(4)]
+                for A, _ in mats]
+    variants = [(prec, False, rate) for prec in ("fp32", "tf32x3") for rate in rates]
+    variants += [(prec, True, rate) for prec in ("fp32", "tf32x3") for rate in rates if rate >= 2500]
+    for prec, resident, rate in variants:
+        arr = workloads.serve_arrivals(rate, window_s, pool, seed=SEED + rate)
+        srv = rmc.Server(budget, nstreams=nstreams, max_batch=256)
+        if resident:
+            srv.resident(16 << 30)
+        live, lat = {}, []
+        rejected, failed, spec_of = 0, [], {}
+        i, t0 = 0, time.perf_counter()
+        while True:
+            now = time.perf_counter() - t0
+            while i < len(arr) and arr[i]["t"] <= now:
+                a = arr[i]
+                if len(live) >= max_outstanding:
+                    rejected += 1
                     i += 1
-                srv.progress()
-                for tk, st, l in srv.poll():
-                    if st != rmc.RMC_OK:
-                        failed.append((st,) + spec_of[tk])
-                    else:
-                        lat.append(l)
-                    del live[tk]
-                    del spec_of[tk]
-                if i == len(arr) and not live:
-                    break
-            t_end = time.perf_counter() - t0
-            srv.close()
-            lat_ms = np.sort(np.array(lat)) * 1e3
-            out["runs"]["%s_rate%d" % (prec, rate)] = {
-                "offered_per_s": len(arr) / window_s, "completed": len(lat), "rejected": rejected,
-                "failed": len(failed), "failed_first": failed[:8],
-                "completed_per_s": len(lat) / t_end,
-                "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-                "mean_ms": float(lat_ms.mean()), "drain_s": t_end}
-    del mats
+                    continue
+                A, b = mats[a["pool"]]
+                n = A.shape[1]
+                if a["kind"] == "lsr":
+                    if resident:
+                        b = rhs_bank[a["pool"]][a["seed"] % 4]
+                    seed = a["pool"] if resident else a["seed"]
+                    r, o = rmc.lsr_request(A, b, a["s_factor"] * n, seed)
+                    tk = srv.submit(r, sketch="countsketch", prec="fp32")
+                    spec_of[tk] = ("lsr", int(A.shape[0]), int(n), a["s_factor"] * n, a["seed"], a["pool"])
+                else:
+                    k = max(1, min(a["k"], n - a["p"]))
+                    r, o = rmc.rsvd_request(A, k, a["p"], a["q"], a["seed"])
+                    tk = srv.submit(r, prec=prec)
+                    spec_of[tk] = ("rsvd", int(A.shape[0]), int(n), k, a["p"], a["q"], a["seed"], a["pool"])
+                live[tk] = o
+                i += 1
+            srv.progress()
+            for tk, st, l in srv.poll():
+                if st != rmc.RMC_OK:
+                    failed.append((st,) + spec_of[tk])
+                else:
+                    lat.append(l)
+                del live[tk]
+                del spec_of[tk]
+            if i == len(arr) and not live:
+                break
+        t_end = time.perf_counter() - t0
+        srv.close()
+        lat_ms = np.sort(np.array(lat)) * 1e3
+        out["runs"]["%s%s_rate%d" % (prec, "_resident" if resident else "", rate)] = {
+            "offered_per_s": len(arr) / window_s, "completed": len(lat), "rejected": rejected,
+            "failed": len(failed), "failed_first": failed[:8],
+            "completed_per_s": len(lat) / t_end,
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "mean_ms": float(lat_ms.mean()), "drain_s": t_end}
+    del mats, rhs_bank
     torch.cuda.empty_cache()
     return out
 

@@ -347,6 +347,19 @@ int rmc_server_progress(rmc_server *srv, int *inflight, int *queued);
 int rmc_server_poll(rmc_server *srv, uint64_t *tickets, int *status, double *latency_s, int max, int *count);
 /* Progress until nothing is queued or in flight (blocks, yielding the CPU between checks). */
 int rmc_server_drain(rmc_server *srv);
+/* Residency of served least-squares state (the paper has no counterpart; a serving concern).  With a nonzero
+ * byte cap, least-squares requests submitted afterwards take the resident route: for each (A, m, n, lda, sketch
+ * kind, s, seed, precision) the server keeps the sketch S^T A and the preconditioner of its factor (the M of
+ * rmc_lsr_sketch's refinement) in device memory, so a later request on the same matrix and sketch sketches only
+ * its own b and refines against them.  Requests that find no resident state sketch and factor first (into a new
+ * entry when the cap allows, evicting the least recently used entries that no launch reads, else into the
+ * lane's workspace); the values are the same either way, so a result does not depend on what is resident.  The
+ * route solves [S^T A, S^T b] with S^T b sketched on its own (not as one more column of A), so its x can differ
+ * from rmc_lsr_sketch's in the last bits.  Resident memory is allocated stream-ordered and held in addition to
+ * the lanes' workspaces.  A matrix with resident state must stay unchanged until rmc_server_release(A) (call it
+ * before modifying or freeing A); bytes = 0 turns residency off and drops the state.  Errors: RMC_EINVAL. */
+int rmc_server_resident(rmc_server *srv, size_t bytes);
+int rmc_server_release(rmc_server *srv, const float *A);
 
 /* ------------------------------------------------------------------------------- measurement hooks */
 

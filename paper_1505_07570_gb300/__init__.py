@@ -570,8 +570,10 @@ lib.rmc_server_progress.argtypes = [_p, ctypes.POINTER(_int), ctypes.POINTER(_in
 lib.rmc_server_poll.argtypes = [_p, ctypes.POINTER(_u64), ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_double),
                                 _int, ctypes.POINTER(_int)]
 lib.rmc_server_drain.argtypes = [_p]
+lib.rmc_server_resident.argtypes = [_p, _sz]
+lib.rmc_server_release.argtypes = [_p, _p]
 for _f in ("rmc_server_create", "rmc_server_destroy", "rmc_server_submit", "rmc_server_progress",
-           "rmc_server_poll", "rmc_server_drain"):
+           "rmc_server_poll", "rmc_server_drain", "rmc_server_resident", "rmc_server_release"):
     getattr(lib, _f).restype = ctypes.c_int
 
 
@@ -612,6 +614,14 @@ class Server:
 
     def drain(self):
         _check(lib.rmc_server_drain(self.handle), "rmc_server_drain")
+
+    def resident(self, nbytes):
+        """Keep least-squares sketches and their factors resident, up to nbytes of device memory (0: off)."""
+        _check(lib.rmc_server_resident(self.handle, _sz(nbytes)), "rmc_server_resident")
+
+    def release(self, A):
+        """Drop the resident state derived from A (before A is modified or freed)."""
+        _check(lib.rmc_server_release(self.handle, _p(A.data_ptr())), "rmc_server_release")
 
     def close(self):
         if self.handle:

@@ -1960,3 +1960,103 @@ int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n_, i
   RMC_LAUNCH_CHECK();
   return RMC_OK;
 }
+
+// --------------------------------------------------------------------- resident least squares (request server)
+// The preconditioner of rmc_launch_lsr_solve computed from S^T A alone and kept by the caller, and the solve of
+// one right-hand side against it: the server keeps S^T A and this factor resident between requests on the same
+// matrix and sketch, so that a request only sketches its b and refines.
+
+__global__ void lsr_flag_out_kernel(const int *flags, int *fail) { *fail = flags[0]; }
+
+__global__ void lsr_flags_in_kernel(int *flags, const int *fail) {
+  if (threadIdx.x < kLsrFlagWords) flags[threadIdx.x] = threadIdx.x == 0 ? *fail : 0;
+}
+
+// the solve's buffers, then the partials of the n x n Gram matrix (its tiling differs from the (n+1)-column one)
+size_t rmc_lsr_factor_ws(int64_t s, int64_t n, int num_sms) {
+  WsCarve w;
+  lsr_carve(w, s, n, num_sms);
+  w.take<char>(gram_ws(s, (int)n, num_sms));
+  return w.off;
+}
+
+// M (n x n FP32) = R^-1 R^-T for the FP32 Cholesky factor R of (S^T A)^T (S^T A), S^T A (s x n, ldsa); *fail
+// (device) = 1 where that factor broke down (the solves then take the FP64 path).
+int rmc_launch_lsr_factor(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n_, int64_t ldsa, float *M, int *fail,
+                          void *ws) {
+  cudaStream_t st = ctx->stream;
+  const int n = (int)n_;
+  WsCarve w;
+  w.base = static_cast<char *>(ws);
+  const LsrBufs b = lsr_carve(w, s, n, ctx->num_sms);
+  double *gpart = reinterpret_cast<double *>(w.take<char>(gram_ws(s, n, ctx->num_sms)));
+  RMC_TRY(launch_gram(ctx, SA, s, n, ldsa, b.G, gpart, kGramF32));
+  {
+    RmcProf prof(ctx, RMC_K_SMALL);
+    lsr_rf_init_kernel<<<rmc_blocks((int64_t)n * n, 256, 1024), 256, 0, st>>>(b.G, n, n, b.Rf, b.flags);
+    rmc_note_launch();
+    for (int j0 = 0; j0 < n; j0 += kPanel) {
+      const int bw = std::min(kPanel, n - j0), rest = n - j0 - bw;
+      lsr_chol_panel_kernel<<<std::max(1, (rest + 255) / 256), 256, 0, st>>>(b.Rf, n, j0, b.Dinv, &b.flags[0]);
+      rmc_note_launch();
+      if (rest > 0) {
+        const int T = (rest + 63) / 64;
+        lsr_chol_update_kernel<<<T * (T + 1) / 2, 256, 0, st>>>(b.Rf, n, j0, &b.flags[0]);
+        rmc_note_launch();
+      }
+    }
+    const int nb = (n + kPanel - 1) / kPanel;
+    const size_t tri_smem = sizeof(float) * ((size_t)nb * kPanel * kPanel + kPanel * kPanel);
+    if (tri_smem > 48 * 1024)
+      RMC_TRY_CUDA(cudaFuncSetAttribute(lsr_tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)tri_smem));
+    lsr_tri_inv_kernel<<<nb, 1024, tri_smem, st>>>(b.Rf, b.Dinv, n, b.Ri, &b.flags[0]);
+    const int T64 = (n + 63) / 64;
+    lsr_inv_gram_kernel<<<T64 * (T64 + 1) / 2, 256, 0, st>>>(b.Ri, n, M, &b.flags[0]);
+    lsr_flag_out_kernel<<<1, 1, 0, st>>>(b.flags, fail);
+    rmc_note_launch(3);
+  }
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}
+
+size_t rmc_lsr_refine_ws(int64_t s, int64_t n, int num_sms) { return rmc_lsr_solve_ws(s, n, num_sms); }
+
+// x = argmin ||S^T A x - S^T b|| for SAb = [S^T A, S^T b] (s x (n+1), ldsab) with the factor of
+// rmc_launch_lsr_factor: refinement with FP64 residuals preconditioned by M, and the FP64 Cholesky of the
+// augmented Gram matrix where the factor failed or the refinement did not converge (as rmc_launch_lsr_solve).
+int rmc_launch_lsr_refine(rmc_ctx *ctx, const float *SAb, int64_t s, int64_t n_, int64_t ldsab, const float *M,
+                          const int *fail, double *x, void *ws) {
+  cudaStream_t st = ctx->stream;
+  const int n = (int)n_, l = n + 1;
+  WsCarve w;
+  w.base = static_cast<char *>(ws);
+  const LsrBufs b = lsr_carve(w, s, n, ctx->num_sms);
+  {
+    RmcProf prof(ctx, RMC_K_SMALL);
+    lsr_flags_in_kernel<<<1, 32, 0, st>>>(b.flags, fail);
+    rmc_note_launch();
+    RMC_TRY_CUDA(cudaMemsetAsync(b.xs, 0, sizeof(double) * n, st));
+    const int nb = (n + kPanel - 1) / kPanel;
+    const int chunks = atr_chunks(s);
+    const int64_t rows_per = (s + chunks - 1) / chunks;
+    for (int it = 0; it < kRefineSteps; ++it) {
+      lsr_resid_kernel<<<rmc_blocks(s * 32, 256, 4096), 256, 0, st>>>(SAb, s, n, ldsab, b.xs, b.r, it, b.flags);
+      lsr_atr_kernel<<<dim3((n + 255) / 256, chunks), 256, 0, st>>>(SAb, s, n, ldsab, b.r, rows_per, b.part, it,
+                                                                    b.flags);
+      lsr_apply_kernel<<<nb, 256, sizeof(float) * n, st>>>(M, n, b.part, chunks, b.xs, it, b.flags);
+      rmc_note_launch(3);
+    }
+    lsr_refine_finish_kernel<<<1, 256, 0, st>>>(b.xs, n, kRefineSteps - 1, x, b.flags);
+    rmc_note_launch();
+  }
+  RMC_TRY(launch_gram(ctx, SAb, s, l, ldsab, b.G, b.gpart, kGramF64, &b.flags[0]));
+  {
+    RmcProf prof(ctx, RMC_K_SMALL);
+    chol64_fallback_kernel<<<1, 1024, 0, st>>>(b.G, l, &b.flags[0], ctx->d_status, &b.flags[1]);
+    lsr_backsub_kernel<<<1, 32, sizeof(double) * n, st>>>(b.G, n, x, &b.flags[0], &b.flags[1]);
+  }
+  rmc_note_launch(2);
+  RMC_LAUNCH_CHECK();
+  return RMC_OK;
+}

@@ -119,6 +119,13 @@ int rmc_launch_countsketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, i
 
 // srht.cu
 size_t rmc_srht_ws(int64_t m, int64_t n_total, int64_t s, int num_sms);
+// dense.cu: least squares against a resident sketch (the request server keeps S^T A and its factor)
+size_t rmc_lsr_factor_ws(int64_t s, int64_t n, int num_sms);
+int rmc_launch_lsr_factor(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n, int64_t ldsa, float *M, int *fail,
+                          void *ws);
+size_t rmc_lsr_refine_ws(int64_t s, int64_t n, int num_sms);
+int rmc_launch_lsr_refine(rmc_ctx *ctx, const float *SAb, int64_t s, int64_t n, int64_t ldsab, const float *M,
+                          const int *fail, double *x, void *ws);
 // tc_gemm.cu: a dense (unswizzled) 2-D TMA map of a row-major FP32 matrix
 int rmc_make_tmap_dense(CUtensorMap *map, const float *base, int64_t rows, int64_t cols, int64_t ld, int box_cols,
                         int box_rows);

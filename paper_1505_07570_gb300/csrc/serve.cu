@@ -9,7 +9,16 @@
 // each lane's event; a request's latency runs from its submit call to the progress call that retires it.
 //
 // Results do not depend on the mix: a request always takes the same route (decided by its own size and
-// precision), and both routes compute a problem with arithmetic that is independent of other problems.
+// precision, and by whether residency was on when it was submitted), and every route computes a problem with
+// arithmetic that is independent of other problems.
+//
+// Residency (rmc_server_resident): least-squares requests take the resident route.  The server keeps, per
+// (matrix, sketch kind, s, seed, precision), the sketch S^T A and the preconditioner M of its factor in device
+// memory (a byte cap, least recently used entries evicted once no launch uses them).  A request whose entry is
+// resident copies S^T A, sketches its own b with the same operator and refines against M; one whose entry is not
+// resident first sketches A and factors (into a new entry, or into the lane's workspace when the cap leaves no
+// room) and then does the same.  Both cases run the same kernels on the same values, so a result does not depend
+// on what is resident.
 
 #include <algorithm>
 #include <chrono>
@@ -24,11 +33,46 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Resident state of one (matrix, sketch) pair: S^T A (s x n, row stride n), M (n x n) and the factor's failure
+// flag, in one stream-ordered allocation.
+struct ResKey {
+  const float *A;
+  int64_t m, n, lda, s;
+  int sketch, prec;
+  uint64_t seed;
+  bool operator==(const ResKey &o) const {
+    return A == o.A && m == o.m && n == o.n && lda == o.lda && s == o.s && sketch == o.sketch && prec == o.prec &&
+           seed == o.seed;
+  }
+};
+
+struct Resident {
+  ResKey key;
+  void *mem = nullptr;
+  float *SA = nullptr, *M = nullptr;
+  int *fail = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t ready = nullptr;   // recorded once S^T A and M are complete
+  uint64_t last_use = 0;
+  int users = 0;                 // launches in flight that read it
+  bool dead = false;             // released: freed once unused
+};
+
+size_t resident_bytes(int64_t s, int64_t n) {
+  WsCarve w;
+  w.take<float>((size_t)s * n);
+  w.take<float>((size_t)n * n);
+  w.take<int>(4);
+  return w.off;
+}
+
 struct Queued {
   rmc_serve_request r;
   uint64_t ticket;
   Clock::time_point t_submit;
   bool batch;
+  bool resident = false;         // least squares through the resident route
+  Resident *res = nullptr;       // the entry its launch reads
 };
 
 struct Lane {
@@ -83,6 +127,9 @@ struct rmc_server {
   std::vector<Lane> lanes;
   std::deque<Queued> queue;
   std::vector<Done> done;
+  size_t res_cap = 0, res_used = 0;   // resident state: byte cap and bytes held
+  uint64_t res_tick = 0;
+  std::vector<Resident *> res;
 };
 
 namespace {
@@ -96,11 +143,141 @@ void retire(rmc_server *srv) {
     if (e != cudaSuccess) (void)cudaGetLastError();
     if (st == RMC_OK && *L.ctx->h_status != RMC_OK) st = *L.ctx->h_status;
     const Clock::time_point now = Clock::now();
-    for (const Queued &w : L.work)
+    for (const Queued &w : L.work) {
       srv->done.push_back({w.ticket, st, std::chrono::duration<double>(now - w.t_submit).count()});
+      if (w.res) --w.res->users;
+    }
     L.work.clear();
     L.busy = false;
   }
+}
+
+// Free an unused entry (its last reader has retired, so any stream may order the free).
+void res_free(rmc_server *srv, Resident *e, cudaStream_t st) {
+  if (e->mem) (void)cudaFreeAsync(e->mem, st);
+  if (e->ready) (void)cudaEventDestroy(e->ready);
+  srv->res_used -= e->bytes;
+  delete e;
+}
+
+// Drop released entries that no launch reads any more.
+void res_collect(rmc_server *srv) {
+  cudaStream_t st = srv->lanes[0].stream;
+  for (size_t i = 0; i < srv->res.size();) {
+    Resident *e = srv->res[i];
+    if (e->dead && e->users == 0) {
+      res_free(srv, e, st);
+      srv->res.erase(srv->res.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+// A new entry for `key`, evicting unused entries (least recently used first) to stay within the cap; nullptr
+// when it cannot be made (the request then uses the lane's workspace).
+Resident *res_make(rmc_server *srv, const ResKey &key, cudaStream_t st) {
+  const size_t bytes = resident_bytes(key.s, key.n);
+  if (bytes > srv->res_cap) return nullptr;
+  while (srv->res_used + bytes > srv->res_cap) {
+    int victim = -1;
+    for (int i = 0; i < (int)srv->res.size(); ++i)
+      if (srv->res[i]->users == 0 && (victim < 0 || srv->res[i]->last_use < srv->res[victim]->last_use)) victim = i;
+    if (victim < 0) return nullptr;
+    res_free(srv, srv->res[victim], st);
+    srv->res.erase(srv->res.begin() + victim);
+  }
+  Resident *e = new (std::nothrow) Resident();
+  if (!e) return nullptr;
+  e->key = key;
+  e->bytes = bytes;
+  if (cudaMallocAsync(&e->mem, bytes, st) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e->ready, cudaEventDisableTiming) != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (e->mem) (void)cudaFreeAsync(e->mem, st);
+    if (e->ready) (void)cudaEventDestroy(e->ready);
+    delete e;
+    return nullptr;
+  }
+  WsCarve w;
+  w.base = static_cast<char *>(e->mem);
+  e->SA = w.take<float>((size_t)key.s * key.n);
+  e->M = w.take<float>((size_t)key.n * key.n);
+  e->fail = w.take<int>(4);
+  srv->res_used += bytes;
+  srv->res.push_back(e);
+  return e;
+}
+
+// Lane workspace of the resident route: [S^T A, S^T b] (s x (n+1)), S^T A, M and the failure flag when they are
+// not resident, then the largest scratch of the sketches, the factor and the refinement.
+size_t resident_plan(rmc_ctx *ctx, const rmc_request &r, int sketch, int prec, float **SAb, float **SA, float **M,
+                     int **fail, void **rest, char *base) {
+  size_t scratch = rmc_sketch_plan_bytes(ctx, r.m, r.n, r.s, sketch, prec);
+  scratch = std::max(scratch, rmc_sketch_plan_bytes(ctx, r.m, 1, r.s, sketch, prec));
+  scratch = std::max(scratch, rmc_lsr_factor_ws(r.s, r.n, ctx->num_sms));
+  scratch = std::max(scratch, rmc_lsr_refine_ws(r.s, r.n, ctx->num_sms));
+  WsCarve w;
+  w.base = base;
+  *SAb = w.take<float>((size_t)r.s * (r.n + 1));
+  *SA = w.take<float>((size_t)r.s * r.n);
+  *M = w.take<float>((size_t)r.n * r.n);
+  *fail = w.take<int>(4);
+  *rest = w.take<char>(scratch);
+  return w.off;
+}
+
+// Least squares through the resident route on lane L (see the header comment).  Returns the entry read, if any.
+int launch_resident(rmc_server *srv, Lane &L, const rmc_serve_request &q, Resident **used) {
+  const rmc_request &r = q.req;
+  rmc_ctx *ctx = L.ctx;
+  cudaStream_t st = L.stream;
+  *used = nullptr;
+  float *SAb, *SA, *M;
+  int *fail;
+  void *rest;
+  const size_t need = resident_plan(ctx, r, q.sketch, q.prec, &SAb, &SA, &M, &fail, &rest, nullptr);
+  RMC_TRY(rmc_ws_reserve(ctx, need));
+  resident_plan(ctx, r, q.sketch, q.prec, &SAb, &SA, &M, &fail, &rest, static_cast<char *>(ctx->ws));
+  const ResKey key{r.A, r.m, r.n, r.lda, r.s, q.sketch, q.prec, r.seed};
+  Resident *e = nullptr;
+  for (Resident *c : srv->res)
+    if (!c->dead && c->key == key) e = c;
+  bool fresh = false;
+  if (!e) {
+    e = res_make(srv, key, st);
+    fresh = true;
+  }
+  if (e) {
+    SA = e->SA;
+    M = e->M;
+    fail = e->fail;
+    e->last_use = ++srv->res_tick;
+    ++e->users;
+    *used = e;
+  }
+  if (!e || fresh) {
+    // S^T A (row stride n) and its factor; an entry whose filling could not be enqueued is never read
+    int rc = rmc_run_sketch(ctx, r.A, r.m, r.n, r.lda, nullptr, r.s, q.sketch, r.seed, q.prec, SA, r.n, nullptr,
+                            rest);
+    if (rc == RMC_OK) rc = rmc_launch_lsr_factor(ctx, SA, r.s, r.n, r.n, M, fail, rest);
+    if (rc == RMC_OK && e && cudaEventRecord(e->ready, st) != cudaSuccess) {
+      (void)cudaGetLastError();
+      rc = RMC_ECUDA;
+    }
+    if (rc != RMC_OK) {
+      if (e) e->dead = true;
+      return rc;
+    }
+  } else {
+    RMC_TRY_CUDA(cudaStreamWaitEvent(st, e->ready, 0));
+  }
+  // [S^T A, S^T b]: the resident sketch, and this request's b through the same operator
+  RMC_TRY_CUDA(cudaMemcpy2DAsync(SAb, sizeof(float) * (r.n + 1), SA, sizeof(float) * r.n, sizeof(float) * r.n,
+                                 r.s, cudaMemcpyDeviceToDevice, st));
+  RMC_TRY(rmc_run_sketch(ctx, r.b, r.m, 1, 1, nullptr, r.s, q.sketch, r.seed, q.prec, SAb + r.n, r.n + 1, nullptr,
+                         rest));
+  return rmc_launch_lsr_refine(ctx, SAb, r.s, r.n, r.n + 1, M, fail, r.x, rest);
 }
 
 // Close a launch: fetch the device status word behind it and mark its end with the lane's event.
@@ -119,10 +296,12 @@ void seal(Lane &L, int rc) {
   L.busy = true;
 }
 
-void launch_single(Lane &L, Queued &&w) {
+void launch_single(rmc_server *srv, Lane &L, Queued &&w) {
   const rmc_request &r = w.r.req;
   int rc;
-  if (r.kind == RMC_REQ_LSR)
+  if (w.resident)
+    rc = launch_resident(srv, L, w.r, &w.res);
+  else if (r.kind == RMC_REQ_LSR)
     rc = rmc_lsr_sketch(L.ctx, r.A, r.m, r.n, r.lda, r.b, r.s, w.r.sketch, r.seed, w.r.prec, r.x);
   else
     rc = rmc_rsvd(L.ctx, r.A, r.m, r.n, r.lda, r.k, r.p, r.q, r.seed, w.r.prec, r.U, r.k, r.sigma, r.V, r.k);
@@ -137,7 +316,7 @@ void admit(rmc_server *srv) {
     if (!srv->queue.front().batch) {
       Queued w = std::move(srv->queue.front());
       srv->queue.pop_front();
-      launch_single(L, std::move(w));
+      launch_single(srv, L, std::move(w));
       continue;
     }
     // every batchable request queued so far, in order, while the launch fits the lane's memory
@@ -192,8 +371,14 @@ int rmc_server_create(rmc_server **out, size_t hbm_budget, int nstreams, int max
 int rmc_server_destroy(rmc_server *srv) {
   if (!srv) return RMC_OK;
   int rc = RMC_OK;
-  for (Lane &L : srv->lanes) {
+  for (Lane &L : srv->lanes)
     if (L.stream && cudaStreamSynchronize(L.stream) != cudaSuccess) rc = RMC_ECUDA;
+  if (!srv->lanes.empty() && srv->lanes[0].stream) {
+    for (Resident *e : srv->res) res_free(srv, e, srv->lanes[0].stream);
+    srv->res.clear();
+    if (cudaStreamSynchronize(srv->lanes[0].stream) != cudaSuccess) rc = RMC_ECUDA;
+  }
+  for (Lane &L : srv->lanes) {
     if (L.ctx) rmc_destroy(L.ctx);
     if (L.done) cudaEventDestroy(L.done);
     if (L.stream) cudaStreamDestroy(L.stream);
@@ -206,11 +391,16 @@ int rmc_server_submit(rmc_server *srv, const rmc_serve_request *req, uint64_t *t
   if (!srv || !req || !ticket) return RMC_EINVAL;
   Queued w;
   w.r = *req;
-  w.batch = batchable(*req);
-  if (!w.batch && !valid_single(*req)) return RMC_EINVAL;
   const rmc_request &r = req->req;
+  w.resident = srv->res_cap > 0 && r.kind == RMC_REQ_LSR;
+  w.batch = !w.resident && batchable(*req);
+  if (!w.batch && !valid_single(*req)) return RMC_EINVAL;
   rmc_ctx *ctx = srv->lanes[0].ctx;
-  const size_t bytes = w.batch ? rmc_batch_plan_bytes(&r, 1)
+  float *p0, *p1, *p2;
+  int *p3;
+  void *p4;
+  const size_t bytes = w.resident ? resident_plan(ctx, r, req->sketch, req->prec, &p0, &p1, &p2, &p3, &p4, nullptr)
+                       : w.batch  ? rmc_batch_plan_bytes(&r, 1)
                        : r.kind == RMC_REQ_LSR
                            ? rmc_lsr_plan_bytes(ctx, r.m, r.n, r.s, req->sketch, req->prec)
                            : rmc_rsvd_plan_bytes(ctx, r.m, r.n, int64_t(r.k) + r.p, req->prec);
@@ -225,6 +415,7 @@ int rmc_server_submit(rmc_server *srv, const rmc_serve_request *req, uint64_t *t
 int rmc_server_progress(rmc_server *srv, int *inflight, int *queued) {
   if (!srv) return RMC_EINVAL;
   retire(srv);
+  res_collect(srv);
   admit(srv);
   if (inflight) {
     int n = 0;
@@ -245,6 +436,28 @@ int rmc_server_poll(rmc_server *srv, uint64_t *tickets, int *status, double *lat
   }
   srv->done.erase(srv->done.begin(), srv->done.begin() + n);
   *count = n;
+  return RMC_OK;
+}
+
+int rmc_server_resident(rmc_server *srv, size_t bytes) {
+  if (!srv) return RMC_EINVAL;
+  srv->res_cap = bytes;
+  // entries beyond the new cap (all of them for 0) are dropped as soon as no launch reads them
+  size_t keep = 0;
+  for (Resident *e : srv->res) {
+    if (e->dead) continue;
+    if (keep + e->bytes > bytes) e->dead = true;
+    else keep += e->bytes;
+  }
+  res_collect(srv);
+  return RMC_OK;
+}
+
+int rmc_server_release(rmc_server *srv, const float *A) {
+  if (!srv || !A) return RMC_EINVAL;
+  for (Resident *e : srv->res)
+    if (e->key.A == A) e->dead = true;
+  res_collect(srv);
   return RMC_OK;
 }
 

@@ -157,3 +157,86 @@ def test_served_results_match_the_oracle(R, problems):
             err = np.linalg.norm(A64 - (U * s) @ V.T)
             erro = np.linalg.norm(A64 - (Uo * so) @ Vo.T)
             assert abs(err - erro) <= 0.01 * erro, SPECS[i]
+
+
+# ------------------------------------------------------------------------ resident least-squares state
+# With residency on, every least-squares request takes the resident route: S^T A and its factor are kept per
+# (matrix, sketch) and a later request only sketches its own b and refines.  Its result must not depend on what
+# is resident (first request, repeat, evicted, or no room at all), must match the oracle, and must follow a
+# matrix that changed after rmc_server_release.
+LSR_IDX = [i for i, sp in enumerate(SPECS) if sp[0] == "lsr"]
+
+
+def run_resident(R, probs, order, cap, nstreams=2, rhs=None):
+    """Least-squares requests `order` (problem indices; repeats reuse a problem's resident state) on a server
+    with a resident cap of `cap` bytes; rhs[pos] replaces the problem's b at position pos.  Returns the x's."""
+    srv = R.Server(8 << 30, nstreams=nstreams, max_batch=64)
+    srv.resident(cap)
+    outs, tickets = [], {}
+    for pos, i in enumerate(order):
+        sp, A, b, sketch, prec = probs[i]
+        r, x = R.lsr_request(A, b if rhs is None else rhs[pos], sp["s"], sp["seed"])
+        outs.append(x)
+        tickets[srv.submit(r, sketch=sketch, prec=prec)] = pos
+        if pos % 2:
+            srv.progress()
+    srv.drain()
+    done = srv.poll()
+    srv.close()
+    assert sorted(t for t, _, _ in done) == sorted(tickets)
+    assert all(st == R.RMC_OK for _, st, _ in done)
+    return outs
+
+
+def test_resident_results_do_not_depend_on_residency(R, problems):
+    probs, _ = problems
+    order = LSR_IDX * 3
+    roomy = run_resident(R, probs, order, 1 << 30)
+    one_entry = run_resident(R, probs, order, 2 << 20, nstreams=1)   # evictions between problems
+    no_room = run_resident(R, probs, order, 1)                        # never resident, same route
+    for pos in range(len(order)):
+        first = order.index(order[pos])
+        assert torch.equal(roomy[pos], roomy[first]), SPECS[order[pos]]
+        assert torch.equal(one_entry[pos], roomy[pos]), SPECS[order[pos]]
+        assert torch.equal(no_room[pos], roomy[pos]), SPECS[order[pos]]
+
+
+def test_resident_results_match_the_oracle(R, problems):
+    """x within 1e-4 of the FP64 oracle's sketch-and-solve on the same inputs, for each problem's own b and two
+    fresh right-hand sides per problem (served against the resident sketch)."""
+    from oracle import lsr
+    probs, _ = problems
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    order, rhs = [], []
+    for i in LSR_IDX:
+        b = probs[i][2]
+        for j in range(3):
+            order.append(i)
+            rhs.append(b if j == 0 else torch.randn(b.shape[0], generator=gen, device="cuda"))
+    outs = run_resident(R, probs, order, 1 << 30, rhs=rhs)
+    for pos, i in enumerate(order):
+        sp, A, _, sketch, _ = probs[i]
+        xo = lsr.lsr_sketch(A.cpu().numpy(), rhs[pos].cpu().numpy(), sp["s"], sketch, sp["seed"])
+        x = outs[pos].cpu().numpy()
+        assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-4, SPECS[i]
+
+
+def test_resident_state_released_with_its_matrix(R, problems):
+    """After rmc_server_release(A), a changed A is sketched and factored again: doubling A halves x."""
+    probs, _ = problems
+    sp, A, b, sketch, prec = probs[LSR_IDX[0]]
+    A2 = A.clone()
+    srv = R.Server(8 << 30, nstreams=1, max_batch=8)
+    srv.resident(1 << 30)
+    r, x1 = R.lsr_request(A2, b, sp["s"], sp["seed"])
+    srv.submit(r, sketch=sketch, prec=prec)
+    srv.drain()
+    A2.mul_(2.0)
+    srv.release(A2)
+    r, x2 = R.lsr_request(A2, b, sp["s"], sp["seed"])
+    srv.submit(r, sketch=sketch, prec=prec)
+    srv.drain()
+    assert all(st == R.RMC_OK for _, st, _ in srv.poll())
+    srv.close()
+    torch.testing.assert_close(x2 * 2, x1, rtol=1e-5, atol=1e-7)
