@@ -713,7 +713,7 @@ def batch_measure(torch, rmc, count=4096, m_range=(512, 32768), reps=3):
     return out
 
 
-def serve_measure(torch, rmc, rates=(100, 1000, 2500, 5000), window_s=2.0, pool=48, budget=64 << 30, nstreams=4,
+def serve_measure(torch, rmc, rates=(100, 1000, 2500, 5000), window_s=2.0, pool=48, budget=64 << 30, nstreams=8,
                   max_outstanding=4096):
     """The served stream: Poisson arrivals at each rate for window_s seconds over a pool of resident problems
     (m log-uniform [1e3, 2e5], n log-uniform [32, 1024]; 60% count-sketch least squares with s = 4n, 40%
@@ -817,7 +817,7 @@ def main():
                     help="run only the served-stream measurement (with --serve-window / --serve-rates) and exit")
     ap.add_argument("--serve-window", type=float, default=2.0, help="seconds of Poisson arrivals per rate")
     ap.add_argument("--serve-rates", type=str, default="100,1000,2500,5000", help="offered rates, requests/s")
-    ap.add_argument("--serve-streams", type=int, default=4, help="streams of the request server")
+    ap.add_argument("--serve-streams", type=int, default=8, help="streams of the request server")
     args = ap.parse_args()
     if args.probe:
         return run_probe(args.probe)

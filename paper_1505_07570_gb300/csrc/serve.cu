@@ -1,8 +1,10 @@
 // Continuous-batching request server (host code).
 //
 // Requests queue in arrival order.  Each stream ("lane") has its own context, whose workspace is capped at
-// the lane's share of the HBM budget, and at most one launch in flight.  Whenever a lane is free the head of
-// the queue is admitted: a request too large for the batched kernel runs alone through rmc_lsr_sketch or
+// the lane's share of the HBM budget, at most one launch in flight, and a host thread that issues the lane's
+// launches (the kernel launches of a request cost host time; with one thread per lane the lanes' launches are
+// issued in parallel, and the caller's thread only queues, admits and retires).  Whenever a lane is free the
+// head of the queue is admitted: a request too large for the batched kernel runs alone through rmc_lsr_sketch or
 // rmc_rsvd; otherwise every batchable request queued so far (in order, up to max_batch and the lane's memory)
 // goes into one rmc_batch_run launch.  Requests that arrive while launches are in flight are admitted as soon
 // as a lane frees up, so launches of different sizes overlap on the device.  Completion is seen by polling
@@ -21,8 +23,12 @@
 // on what is resident.
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <deque>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
@@ -56,6 +62,7 @@ struct Resident {
   uint64_t last_use = 0;
   int users = 0;                 // launches in flight that read it
   bool dead = false;             // released: freed once unused
+  bool recorded = false;         // `ready` recorded: other lanes may read it
 };
 
 size_t resident_bytes(int64_t s, int64_t n) {
@@ -75,13 +82,24 @@ struct Queued {
   Resident *res = nullptr;       // the entry its launch reads
 };
 
+// Lane states: the main thread moves kIdle -> kPosted (work handed to the lane's thread), the lane's thread
+// kPosted -> kEnqueued (launches issued, `done` recorded), the main thread kEnqueued -> kIdle once `done` has
+// completed and the requests are retired.
+enum LaneState { kIdle = 0, kPosted = 1, kEnqueued = 2 };
+
 struct Lane {
   cudaStream_t stream = nullptr;
   rmc_ctx *ctx = nullptr;
   cudaEvent_t done = nullptr;
-  bool busy = false;
   int launch_status = RMC_OK;
-  std::vector<Queued> work;  // the requests of the launch in flight
+  std::vector<Queued> work;        // the requests of the launch in flight
+  std::vector<rmc_request> reqs;   // a batched launch's problems
+  bool batch_job = false;
+  std::atomic<int> state{kIdle};
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  std::thread thread;
 };
 
 struct Done {
@@ -124,31 +142,38 @@ struct rmc_server {
   size_t lane_budget = 0;
   int max_batch = 0;
   uint64_t next_ticket = 1;
-  std::vector<Lane> lanes;
+  int device = 0;
+  std::vector<std::unique_ptr<Lane>> lanes;
   std::deque<Queued> queue;
   std::vector<Done> done;
   size_t res_cap = 0, res_used = 0;   // resident state: byte cap and bytes held
   uint64_t res_tick = 0;
   std::vector<Resident *> res;
+  std::mutex res_mu;                  // the resident entries (lane threads make and read them)
 };
 
 namespace {
 
 void retire(rmc_server *srv) {
-  for (Lane &L : srv->lanes) {
-    if (!L.busy) continue;
+  for (auto &Lp : srv->lanes) {
+    Lane &L = *Lp;
+    if (L.state.load(std::memory_order_acquire) != kEnqueued) continue;
     const cudaError_t e = cudaEventQuery(L.done);
     if (e == cudaErrorNotReady) continue;
     int st = e == cudaSuccess ? L.launch_status : RMC_ECUDA;
     if (e != cudaSuccess) (void)cudaGetLastError();
     if (st == RMC_OK && *L.ctx->h_status != RMC_OK) st = *L.ctx->h_status;
     const Clock::time_point now = Clock::now();
-    for (const Queued &w : L.work) {
-      srv->done.push_back({w.ticket, st, std::chrono::duration<double>(now - w.t_submit).count()});
-      if (w.res) --w.res->users;
+    {
+      std::lock_guard<std::mutex> lk(srv->res_mu);
+      for (const Queued &w : L.work) {
+        srv->done.push_back({w.ticket, st, std::chrono::duration<double>(now - w.t_submit).count()});
+        if (w.res) --w.res->users;
+      }
     }
     L.work.clear();
-    L.busy = false;
+    L.reqs.clear();
+    L.state.store(kIdle, std::memory_order_release);
   }
 }
 
@@ -160,9 +185,9 @@ void res_free(rmc_server *srv, Resident *e, cudaStream_t st) {
   delete e;
 }
 
-// Drop released entries that no launch reads any more.
+// Drop released entries that no launch reads any more (caller holds res_mu).
 void res_collect(rmc_server *srv) {
-  cudaStream_t st = srv->lanes[0].stream;
+  cudaStream_t st = srv->lanes[0]->stream;
   for (size_t i = 0; i < srv->res.size();) {
     Resident *e = srv->res[i];
     if (e->dead && e->users == 0) {
@@ -241,19 +266,29 @@ int launch_resident(rmc_server *srv, Lane &L, const rmc_serve_request &q, Reside
   resident_plan(ctx, r, q.sketch, q.prec, &SAb, &SA, &M, &fail, &rest, static_cast<char *>(ctx->ws));
   const ResKey key{r.A, r.m, r.n, r.lda, r.s, q.sketch, q.prec, r.seed};
   Resident *e = nullptr;
-  for (Resident *c : srv->res)
-    if (!c->dead && c->key == key) e = c;
   bool fresh = false;
-  if (!e) {
-    e = res_make(srv, key, st);
-    fresh = true;
+  {
+    // an entry still being filled by another lane's thread (its ready event not yet recorded) is not used: this
+    // request computes into its own workspace instead (the same values)
+    std::lock_guard<std::mutex> lk(srv->res_mu);
+    Resident *found = nullptr;
+    for (Resident *c : srv->res)
+      if (!c->dead && c->key == key) found = c;
+    if (found && found->recorded) {
+      e = found;
+    } else if (!found) {
+      e = res_make(srv, key, st);
+      fresh = e != nullptr;
+    }
+    if (e) {
+      e->last_use = ++srv->res_tick;
+      ++e->users;
+    }
   }
   if (e) {
     SA = e->SA;
     M = e->M;
     fail = e->fail;
-    e->last_use = ++srv->res_tick;
-    ++e->users;
     *used = e;
   }
   if (!e || fresh) {
@@ -265,10 +300,12 @@ int launch_resident(rmc_server *srv, Lane &L, const rmc_serve_request &q, Reside
       (void)cudaGetLastError();
       rc = RMC_ECUDA;
     }
-    if (rc != RMC_OK) {
-      if (e) e->dead = true;
-      return rc;
+    if (e) {
+      std::lock_guard<std::mutex> lk(srv->res_mu);
+      if (rc == RMC_OK) e->recorded = true;
+      else e->dead = true;
     }
+    if (rc != RMC_OK) return rc;
   } else {
     RMC_TRY_CUDA(cudaStreamWaitEvent(st, e->ready, 0));
   }
@@ -293,34 +330,58 @@ void seal(Lane &L, int rc) {
     (void)cudaStreamSynchronize(L.stream);
     (void)cudaEventRecord(L.done, L.stream);
   }
-  L.busy = true;
 }
 
-void launch_single(rmc_server *srv, Lane &L, Queued &&w) {
-  const rmc_request &r = w.r.req;
-  int rc;
-  if (w.resident)
-    rc = launch_resident(srv, L, w.r, &w.res);
-  else if (r.kind == RMC_REQ_LSR)
-    rc = rmc_lsr_sketch(L.ctx, r.A, r.m, r.n, r.lda, r.b, r.s, w.r.sketch, r.seed, w.r.prec, r.x);
-  else
-    rc = rmc_rsvd(L.ctx, r.A, r.m, r.n, r.lda, r.k, r.p, r.q, r.seed, w.r.prec, r.U, r.k, r.sigma, r.V, r.k);
-  L.work.push_back(std::move(w));
-  seal(L, rc);
+// The lane's thread: issues the launches of the work posted to it, then marks the lane enqueued.
+void lane_thread(rmc_server *srv, Lane *Lp) {
+  Lane &L = *Lp;
+  (void)cudaSetDevice(srv->device);
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(L.mu);
+      L.cv.wait(lk, [&] { return L.stop || L.state.load(std::memory_order_acquire) == kPosted; });
+      if (L.stop) return;
+    }
+    int rc;
+    if (L.batch_job) {
+      rc = rmc_batch_run(L.ctx, L.reqs.data(), (int)L.reqs.size());
+    } else {
+      Queued &w = L.work.front();
+      const rmc_request &r = w.r.req;
+      if (w.resident)
+        rc = launch_resident(srv, L, w.r, &w.res);
+      else if (r.kind == RMC_REQ_LSR)
+        rc = rmc_lsr_sketch(L.ctx, r.A, r.m, r.n, r.lda, r.b, r.s, w.r.sketch, r.seed, w.r.prec, r.x);
+      else
+        rc = rmc_rsvd(L.ctx, r.A, r.m, r.n, r.lda, r.k, r.p, r.q, r.seed, w.r.prec, r.U, r.k, r.sigma, r.V, r.k);
+    }
+    seal(L, rc);
+    L.state.store(kEnqueued, std::memory_order_release);
+  }
+}
+
+void post(Lane &L) {
+  {
+    std::lock_guard<std::mutex> lk(L.mu);
+    L.state.store(kPosted, std::memory_order_release);
+  }
+  L.cv.notify_one();
 }
 
 void admit(rmc_server *srv) {
-  for (Lane &L : srv->lanes) {
-    if (L.busy) continue;
+  for (auto &Lp : srv->lanes) {
+    Lane &L = *Lp;
+    if (L.state.load(std::memory_order_acquire) != kIdle) continue;
     if (srv->queue.empty()) return;
     if (!srv->queue.front().batch) {
-      Queued w = std::move(srv->queue.front());
+      L.work.push_back(std::move(srv->queue.front()));
       srv->queue.pop_front();
-      launch_single(srv, L, std::move(w));
+      L.batch_job = false;
+      post(L);
       continue;
     }
     // every batchable request queued so far, in order, while the launch fits the lane's memory
-    std::vector<rmc_request> reqs;
+    std::vector<rmc_request> &reqs = L.reqs;
     for (auto it = srv->queue.begin(); it != srv->queue.end() && (int)reqs.size() < srv->max_batch;) {
       if (!it->batch) {
         ++it;
@@ -334,7 +395,20 @@ void admit(rmc_server *srv) {
       L.work.push_back(std::move(*it));
       it = srv->queue.erase(it);
     }
-    seal(L, rmc_batch_run(L.ctx, reqs.data(), (int)reqs.size()));
+    L.batch_job = true;
+    post(L);
+  }
+}
+
+void stop_threads(rmc_server *srv) {
+  for (auto &Lp : srv->lanes) {
+    if (!Lp->thread.joinable()) continue;
+    {
+      std::lock_guard<std::mutex> lk(Lp->mu);
+      Lp->stop = true;
+    }
+    Lp->cv.notify_one();
+    Lp->thread.join();
   }
 }
 
@@ -350,8 +424,21 @@ int rmc_server_create(rmc_server **out, size_t hbm_budget, int nstreams, int max
   if (!srv) return RMC_ENOMEM;
   srv->lane_budget = hbm_budget / nstreams;
   srv->max_batch = max_batch;
-  srv->lanes.resize(nstreams);
-  for (Lane &L : srv->lanes) {
+  if (cudaGetDevice(&srv->device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete srv;
+    return RMC_ECUDA;
+  }
+  for (int i = 0; i < nstreams; ++i) {
+    srv->lanes.emplace_back(new (std::nothrow) Lane());
+    if (!srv->lanes.back()) {
+      srv->lanes.pop_back();
+      rmc_server_destroy(srv);
+      return RMC_ENOMEM;
+    }
+  }
+  for (auto &Lp : srv->lanes) {
+    Lane &L = *Lp;
     int rc = RMC_OK;
     if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) {
@@ -364,6 +451,12 @@ int rmc_server_create(rmc_server **out, size_t hbm_budget, int nstreams, int max
       return rc;
     }
   }
+  try {
+    for (auto &Lp : srv->lanes) Lp->thread = std::thread(lane_thread, srv, Lp.get());
+  } catch (...) {
+    rmc_server_destroy(srv);
+    return RMC_ENOMEM;
+  }
   *out = srv;
   return RMC_OK;
 }
@@ -371,14 +464,16 @@ int rmc_server_create(rmc_server **out, size_t hbm_budget, int nstreams, int max
 int rmc_server_destroy(rmc_server *srv) {
   if (!srv) return RMC_OK;
   int rc = RMC_OK;
-  for (Lane &L : srv->lanes)
-    if (L.stream && cudaStreamSynchronize(L.stream) != cudaSuccess) rc = RMC_ECUDA;
-  if (!srv->lanes.empty() && srv->lanes[0].stream) {
-    for (Resident *e : srv->res) res_free(srv, e, srv->lanes[0].stream);
+  stop_threads(srv);   // a posted launch is issued before its thread stops
+  for (auto &Lp : srv->lanes)
+    if (Lp->stream && cudaStreamSynchronize(Lp->stream) != cudaSuccess) rc = RMC_ECUDA;
+  if (!srv->lanes.empty() && srv->lanes[0]->stream) {
+    for (Resident *e : srv->res) res_free(srv, e, srv->lanes[0]->stream);
     srv->res.clear();
-    if (cudaStreamSynchronize(srv->lanes[0].stream) != cudaSuccess) rc = RMC_ECUDA;
+    if (cudaStreamSynchronize(srv->lanes[0]->stream) != cudaSuccess) rc = RMC_ECUDA;
   }
-  for (Lane &L : srv->lanes) {
+  for (auto &Lp : srv->lanes) {
+    Lane &L = *Lp;
     if (L.ctx) rmc_destroy(L.ctx);
     if (L.done) cudaEventDestroy(L.done);
     if (L.stream) cudaStreamDestroy(L.stream);
@@ -395,7 +490,7 @@ int rmc_server_submit(rmc_server *srv, const rmc_serve_request *req, uint64_t *t
   w.resident = srv->res_cap > 0 && r.kind == RMC_REQ_LSR;
   w.batch = !w.resident && batchable(*req);
   if (!w.batch && !valid_single(*req)) return RMC_EINVAL;
-  rmc_ctx *ctx = srv->lanes[0].ctx;
+  rmc_ctx *ctx = srv->lanes[0]->ctx;   // plans read only the context's SM count
   float *p0, *p1, *p2;
   int *p3;
   void *p4;
@@ -415,11 +510,14 @@ int rmc_server_submit(rmc_server *srv, const rmc_serve_request *req, uint64_t *t
 int rmc_server_progress(rmc_server *srv, int *inflight, int *queued) {
   if (!srv) return RMC_EINVAL;
   retire(srv);
-  res_collect(srv);
+  {
+    std::lock_guard<std::mutex> lk(srv->res_mu);
+    res_collect(srv);
+  }
   admit(srv);
   if (inflight) {
     int n = 0;
-    for (const Lane &L : srv->lanes) n += (int)L.work.size();
+    for (const auto &Lp : srv->lanes) n += (int)Lp->work.size();
     *inflight = n;
   }
   if (queued) *queued = (int)srv->queue.size();
@@ -441,6 +539,7 @@ int rmc_server_poll(rmc_server *srv, uint64_t *tickets, int *status, double *lat
 
 int rmc_server_resident(rmc_server *srv, size_t bytes) {
   if (!srv) return RMC_EINVAL;
+  std::lock_guard<std::mutex> lk(srv->res_mu);
   srv->res_cap = bytes;
   // entries beyond the new cap (all of them for 0) are dropped as soon as no launch reads them
   size_t keep = 0;
@@ -455,6 +554,7 @@ int rmc_server_resident(rmc_server *srv, size_t bytes) {
 
 int rmc_server_release(rmc_server *srv, const float *A) {
   if (!srv || !A) return RMC_EINVAL;
+  std::lock_guard<std::mutex> lk(srv->res_mu);
   for (Resident *e : srv->res)
     if (e->key.A == A) e->dead = true;
   res_collect(srv);
