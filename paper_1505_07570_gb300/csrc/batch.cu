@@ -1320,7 +1320,7 @@ extern "C" int rmc_batch_run(rmc_ctx *ctx, const rmc_request *reqs, int nreq) {
   RMC_TRY_CUDA(cudaMemcpyAsync(d_order, stage + items_bytes, sizeof(int) * nreq, cudaMemcpyHostToDevice, st));
   RMC_TRY_CUDA(cudaEventRecord(ctx->stage_ev, st));
   RMC_TRY_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), st));
-  RMC_TRY_CUDA(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+  RMC_TRY_CUDA(rmc_allow_smem(batch_kernel, kSmemBytes));
   const int grid = std::min(nreq, ctx->num_sms);
   {
     RmcProf prof(ctx, RMC_K_BATCH);

@@ -1465,10 +1465,8 @@ int launch_rowblock(cudaStream_t st, const float *in, int64_t m, int li, int64_t
   if (li >= 1 && li <= 128 && lo <= 128) {
     const size_t smem2 = sizeof(float) * ((size_t)li * RB2_LD + (size_t)li * 128);
     if (smem2 > 48 * 1024) {
-      RMC_TRY_CUDA(cudaFuncSetAttribute(rowblock_tile_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem2));
-      RMC_TRY_CUDA(cudaFuncSetAttribute(rowblock_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem2));
+      RMC_TRY_CUDA(rmc_allow_smem(rowblock_tile_kernel<false>, smem2));
+      RMC_TRY_CUDA(rmc_allow_smem(rowblock_tile_kernel<true>, smem2));
     }
     if (subtract)
       rowblock_tile_kernel<true><<<rmc_blocks(m, RB2), 256, smem2, st>>>(in, m, li, ldi, M, lo, ldm, out, ldo);
@@ -1480,10 +1478,8 @@ int launch_rowblock(cudaStream_t st, const float *in, int64_t m, int li, int64_t
   }
   const size_t smem = sizeof(float) * RB * li;
   if (smem > 48 * 1024) {
-    RMC_TRY_CUDA(cudaFuncSetAttribute(rowblock_mul_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-    RMC_TRY_CUDA(cudaFuncSetAttribute(rowblock_mul_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+    RMC_TRY_CUDA(rmc_allow_smem(rowblock_mul_kernel<false>, smem));
+    RMC_TRY_CUDA(rmc_allow_smem(rowblock_mul_kernel<true>, smem));
   }
   if (subtract) rowblock_mul_kernel<true><<<rmc_blocks(m, RB), 256, smem, st>>>(in, m, li, ldi, M, lo, ldm, out, ldo);
   else rowblock_mul_kernel<false><<<rmc_blocks(m, RB), 256, smem, st>>>(in, m, li, ldi, M, lo, ldm, out, ldo);
@@ -1615,19 +1611,17 @@ static int launch_factor(rmc_ctx *ctx, double *G, int l, double *Rinv, float *Ri
   } else if (l <= kCholFusedMaxL) {
     const size_t smem_f = chol32_fused_smem_bytes(l);
     if (smem_f > 48 * 1024)
-      RMC_TRY_CUDA(cudaFuncSetAttribute(chol32_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f));
+      RMC_TRY_CUDA(rmc_allow_smem(chol32_fused_kernel, smem_f));
     chol32_fused_kernel<<<1, kCholFusedThreads, smem_f, st>>>(G, l, Rinv32, fail);
   } else {
     const size_t smem_x = smem + sizeof(float) * (size_t)l * l;
     if (smem_x <= kMaxPackedBytes) {
       if (smem_x > 48 * 1024)
-        RMC_TRY_CUDA(cudaFuncSetAttribute(chol32_inv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem_x));
+        RMC_TRY_CUDA(rmc_allow_smem(chol32_inv_kernel<true>, smem_x));
       chol32_inv_kernel<true><<<1, 512, smem_x, st>>>(G, l, Rinv32, fail);
     } else {
       if (smem > 48 * 1024)
-        RMC_TRY_CUDA(cudaFuncSetAttribute(chol32_inv_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
+        RMC_TRY_CUDA(rmc_allow_smem(chol32_inv_kernel<false>, smem));
       chol32_inv_kernel<false><<<1, 512, smem, st>>>(G, l, Rinv32, fail);
     }
   }
@@ -1702,8 +1696,7 @@ static int launch_jacobi_vec(cudaStream_t st, float *W, int l, float tol, int *s
 #define RMC_JV(NV)                                                                                            \
   case NV:                                                                                                    \
     if (smem > 48 * 1024)                                                                                     \
-      RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_vec_kernel<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                        (int)smem));                                                          \
+      RMC_TRY_CUDA(rmc_allow_smem(jacobi_vec_kernel<NV>, smem));                                              \
     jacobi_vec_kernel<NV><<<1, threads, smem, st>>>(W, l, tol, 60, status);                                   \
     break;
     RMC_JV(1)
@@ -1728,13 +1721,11 @@ static int launch_jacobi_grp(rmc_ctx *ctx, const double *R, int l, double *work,
     to_colmajor_kernel<double><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, work);
     if (l <= 128) {
       if (smem > 48 * 1024)
-        RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_grp_kernel<double, 16>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RMC_TRY_CUDA(rmc_allow_smem(jacobi_grp_kernel<double, 16>, smem));
       jacobi_grp_kernel<double, 16><<<1, 1024, smem, st>>>(work, l, tol, 60, ctx->d_status);
     } else {
       if (smem > 48 * 1024)
-        RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_grp_kernel<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
+        RMC_TRY_CUDA(rmc_allow_smem(jacobi_grp_kernel<double, 8>, smem));
       jacobi_grp_kernel<double, 8><<<1, 1024, smem, st>>>(work, l, tol, 60, ctx->d_status);
     }
     jacobi_left_kernel<double><<<1, 256, sizeof(double) * l, st>>>(work, l, M, sigma);
@@ -1747,8 +1738,7 @@ static int launch_jacobi_grp(rmc_ctx *ctx, const double *R, int l, double *work,
       RMC_TRY(launch_jacobi_vec(st, Wf, l, tol, ctx->d_status));
     } else {
       if (smem > 48 * 1024)
-        RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_grp_kernel<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
+        RMC_TRY_CUDA(rmc_allow_smem(jacobi_grp_kernel<float, 8>, smem));
       jacobi_grp_kernel<float, 8><<<1, 1024, smem, st>>>(Wf, l, tol, 60, ctx->d_status);
     }
     jacobi_left_kernel<float><<<1, 256, sizeof(double) * l, st>>>(Wf, l, M, sigma);
@@ -1803,8 +1793,7 @@ int rmc_launch_svd_wide(rmc_ctx *ctx, const float *B, int64_t l_, int64_t n, int
       to_colmajor_kernel<float><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, Wf);
       if (smem32 <= 200 * 1024) {
         if (smem32 > 48 * 1024)
-          RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_smem_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem32));
+          RMC_TRY_CUDA(rmc_allow_smem(jacobi_smem_kernel<float>, smem32));
         jacobi_smem_kernel<float><<<1, 1024, smem32, st>>>(Wf, Vf, l, tol, 60, ctx->d_status);
       } else {
         jacobi_kernel<float><<<1, 1024, 0, st>>>(Wf, Vf, l, tol, 60, ctx->d_status);
@@ -1842,8 +1831,7 @@ int rmc_launch_jacobi_square(rmc_ctx *ctx, const double *Wrm, int l, float *Ml, 
     to_colmajor_kernel<float><<<rmc_blocks(l * l, 256), 256, 0, st>>>(Wrm, l, Wf);
     if (smem32 <= 200 * 1024) {
       if (smem32 > 48 * 1024)
-        RMC_TRY_CUDA(cudaFuncSetAttribute(jacobi_smem_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem32));
+        RMC_TRY_CUDA(rmc_allow_smem(jacobi_smem_kernel<float>, smem32));
       jacobi_smem_kernel<float><<<1, 1024, smem32, st>>>(Wf, Vf, l, tol, 60, ctx->d_status);
     } else {
       jacobi_kernel<float><<<1, 1024, 0, st>>>(Wf, Vf, l, tol, 60, ctx->d_status);
@@ -1929,8 +1917,7 @@ int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n_, i
     const int nb = (n + kPanel - 1) / kPanel;
     const size_t tri_smem = sizeof(float) * ((size_t)nb * kPanel * kPanel + kPanel * kPanel);
     if (tri_smem > 48 * 1024)
-      RMC_TRY_CUDA(cudaFuncSetAttribute(lsr_tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)tri_smem));
+      RMC_TRY_CUDA(rmc_allow_smem(lsr_tri_inv_kernel, tri_smem));
     lsr_tri_inv_kernel<<<nb, 1024, tri_smem, st>>>(b.Rf, b.Dinv, n, b.Ri, &b.flags[0]);
     const int T64 = (n + 63) / 64;
     lsr_inv_gram_kernel<<<T64 * (T64 + 1) / 2, 256, 0, st>>>(b.Ri, n, b.M, &b.flags[0]);
@@ -2008,8 +1995,7 @@ int rmc_launch_lsr_factor(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n_, 
     const int nb = (n + kPanel - 1) / kPanel;
     const size_t tri_smem = sizeof(float) * ((size_t)nb * kPanel * kPanel + kPanel * kPanel);
     if (tri_smem > 48 * 1024)
-      RMC_TRY_CUDA(cudaFuncSetAttribute(lsr_tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)tri_smem));
+      RMC_TRY_CUDA(rmc_allow_smem(lsr_tri_inv_kernel, tri_smem));
     lsr_tri_inv_kernel<<<nb, 1024, tri_smem, st>>>(b.Rf, b.Dinv, n, b.Ri, &b.flags[0]);
     const int T64 = (n + 63) / 64;
     lsr_inv_gram_kernel<<<T64 * (T64 + 1) / 2, 256, 0, st>>>(b.Ri, n, M, &b.flags[0]);

@@ -242,11 +242,10 @@ static int launch_cols(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64
   {
     RmcProf prof(ctx, RMC_K_COUNTSKETCH);
     if (vec) {
-      RMC_TRY_CUDA(cudaFuncSetAttribute(cs_cols_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      RMC_TRY_CUDA(rmc_allow_smem(cs_cols_kernel<true>, smem));
       cs_cols_kernel<true><<<grid, kMaxBuckets, smem, st>>>(a);
     } else {
-      RMC_TRY_CUDA(cudaFuncSetAttribute(cs_cols_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
+      RMC_TRY_CUDA(rmc_allow_smem(cs_cols_kernel<false>, smem));
       cs_cols_kernel<false><<<grid, kMaxBuckets, smem, st>>>(a);
     }
   }

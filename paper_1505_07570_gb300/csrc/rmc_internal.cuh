@@ -90,6 +90,22 @@ __device__ __forceinline__ void rmc_report(int *status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
+// Allow `bytes` of dynamic shared memory for `kern`.  The cap is only ever raised, straight to the device's
+// opt-in maximum: launches issued from several host threads at once (the request server's lanes, or callers'
+// own threads) then never find it lowered below their own request by another thread's smaller problem.
+template <typename K>
+inline cudaError_t rmc_allow_smem(K kern, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, kern);
+  if (e != cudaSuccess) return e;
+  if ((size_t)a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  int dev = 0, optin = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+}
+
 static inline unsigned rmc_blocks(int64_t work, int per_block, int64_t cap = 1 << 30) {
   int64_t b = (work + per_block - 1) / per_block;
   if (b < 1) b = 1;

@@ -144,7 +144,7 @@ struct rmc_server {
   uint64_t next_ticket = 1;
   int device = 0;
   std::vector<std::unique_ptr<Lane>> lanes;
-  std::deque<Queued> queue;
+  std::deque<Queued> singles, batchables;   // the queue in arrival order, split by route (tickets increase)
   std::vector<Done> done;
   size_t res_cap = 0, res_used = 0;   // resident state: byte cap and bytes held
   uint64_t res_tick = 0;
@@ -372,28 +372,28 @@ void admit(rmc_server *srv) {
   for (auto &Lp : srv->lanes) {
     Lane &L = *Lp;
     if (L.state.load(std::memory_order_acquire) != kIdle) continue;
-    if (srv->queue.empty()) return;
-    if (!srv->queue.front().batch) {
-      L.work.push_back(std::move(srv->queue.front()));
-      srv->queue.pop_front();
+    if (srv->singles.empty() && srv->batchables.empty()) return;
+    // the request that arrived first decides the launch
+    if (!srv->singles.empty() &&
+        (srv->batchables.empty() || srv->singles.front().ticket < srv->batchables.front().ticket)) {
+      L.work.push_back(std::move(srv->singles.front()));
+      srv->singles.pop_front();
       L.batch_job = false;
       post(L);
       continue;
     }
-    // every batchable request queued so far, in order, while the launch fits the lane's memory
+    // the batchable requests queued so far, in order, up to max_batch; halved until the launch fits the lane's
+    // memory (one plan in the usual case)
     std::vector<rmc_request> &reqs = L.reqs;
-    for (auto it = srv->queue.begin(); it != srv->queue.end() && (int)reqs.size() < srv->max_batch;) {
-      if (!it->batch) {
-        ++it;
-        continue;
-      }
-      reqs.push_back(it->r.req);
-      if (reqs.size() > 1 && rmc_batch_plan_bytes(reqs.data(), (int)reqs.size()) > srv->lane_budget) {
-        reqs.pop_back();
-        break;
-      }
-      L.work.push_back(std::move(*it));
-      it = srv->queue.erase(it);
+    int take = (int)std::min<size_t>(srv->batchables.size(), (size_t)srv->max_batch);
+    for (int i = 0; i < take; ++i) reqs.push_back(srv->batchables[i].r.req);
+    while (take > 1 && rmc_batch_plan_bytes(reqs.data(), take) > srv->lane_budget) {
+      take = (take + 1) / 2;
+      reqs.resize(take);
+    }
+    for (int i = 0; i < take; ++i) {
+      L.work.push_back(std::move(srv->batchables.front()));
+      srv->batchables.pop_front();
     }
     L.batch_job = true;
     post(L);
@@ -503,7 +503,8 @@ int rmc_server_submit(rmc_server *srv, const rmc_serve_request *req, uint64_t *t
   w.ticket = srv->next_ticket++;
   w.t_submit = Clock::now();
   *ticket = w.ticket;
-  srv->queue.push_back(std::move(w));
+  if (w.batch) srv->batchables.push_back(std::move(w));
+  else srv->singles.push_back(std::move(w));
   return RMC_OK;
 }
 
@@ -520,7 +521,7 @@ int rmc_server_progress(rmc_server *srv, int *inflight, int *queued) {
     for (const auto &Lp : srv->lanes) n += (int)Lp->work.size();
     *inflight = n;
   }
-  if (queued) *queued = (int)srv->queue.size();
+  if (queued) *queued = (int)(srv->singles.size() + srv->batchables.size());
   return RMC_OK;
 }
 

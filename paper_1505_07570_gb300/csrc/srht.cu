@@ -447,7 +447,7 @@ int rmc_launch_srht(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int64_t 
   const size_t smem = 1024 + 2 * sizeof(float4) * kRowsCta + sizeof(uint32_t) * 2 * (kRowsCta / 32) +
                       sizeof(uint16_t) * kRowsCta + (p.G > 1 ? sizeof(float4) * kRowsCta : 0);
   auto kern = tma ? srht_stage1_kernel<true> : srht_stage1_kernel<false>;
-  RMC_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  RMC_TRY_CUDA(rmc_allow_smem(kern, smem));
   // as many CTAs as are co-resident (one per SM), each looping over (a, slab) units of G items
   const int64_t units = p.slabs * (p.N1 / p.G);
   int per_sm = 0;

@@ -579,12 +579,12 @@ int rmc_tc_gauss_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int6
   const dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)splits);
   if (bf16) {
     constexpr size_t smem = GaussCfg<true>::kSmem;
-    RMC_TRY_CUDA(cudaFuncSetAttribute(tc_gauss_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RMC_TRY_CUDA(rmc_allow_smem(tc_gauss_kernel<true>, smem));
     RmcProf prof(ctx, RMC_K_GAUSSIAN);
     tc_gauss_kernel<true><<<grid, kThreads, smem, ctx->stream>>>(map, a);
   } else {
     constexpr size_t smem = GaussCfg<false>::kSmem;
-    RMC_TRY_CUDA(cudaFuncSetAttribute(tc_gauss_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RMC_TRY_CUDA(rmc_allow_smem(tc_gauss_kernel<false>, smem));
     RmcProf prof(ctx, RMC_K_GAUSSIAN);
     tc_gauss_kernel<false><<<grid, kThreads, smem, ctx->stream>>>(map, a);
   }
@@ -1449,7 +1449,7 @@ template <int NP, bool X3>
 int an_launch(rmc_ctx *ctx, const CUtensorMap &ma, const CUtensorMap &mx, const CUtensorMap &ml, int64_t m,
               int64_t n, int64_t l, float *Y, int64_t ldy, int splits) {
   const size_t smem = AnCfg<NP, X3>::kSmem;
-  RMC_TRY_CUDA(cudaFuncSetAttribute(tc_an_kernel<NP, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  RMC_TRY_CUDA(rmc_allow_smem(tc_an_kernel<NP, X3>, smem));
   int64_t per = (n + splits - 1) / splits;
   per = (per + kKStage - 1) / kKStage * kKStage;
   tc_an_kernel<NP, X3><<<dim3((unsigned)((m + 127) / 128), (unsigned)splits), kAnThreads, smem, ctx->stream>>>(
@@ -1498,7 +1498,7 @@ template <int MT, bool X3>
 int at_launch(rmc_ctx *ctx, const CUtensorMap &ma, const CUtensorMap &mx, const CUtensorMap &ml, int64_t m,
               int64_t n, int64_t l, int64_t rows, int splits, float *part) {
   const size_t smem = AtCfg<MT, X3>::kSmem;
-  RMC_TRY_CUDA(cudaFuncSetAttribute(tc_at_kernel<MT, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  RMC_TRY_CUDA(rmc_allow_smem(tc_at_kernel<MT, X3>, smem));
   dim3 grid((unsigned)((n + AtCfg<MT, X3>::NC - 1) / AtCfg<MT, X3>::NC), 1, (unsigned)splits);
   tc_at_kernel<MT, X3><<<grid, 32 * (4 + 4 * MT), smem, ctx->stream>>>(ma, mx, ml, m, n, l, rows, part,
                                                                        ctx->d_status);
@@ -1570,7 +1570,7 @@ template <int NP>
 int an_bf16_launch(rmc_ctx *ctx, const CUtensorMap &ma, const CUtensorMap &mx, int64_t m, int64_t n, int64_t l,
                    float *Y, int64_t ldy) {
   const size_t smem = AnBfCfg<NP>::kSmem;
-  RMC_TRY_CUDA(cudaFuncSetAttribute(tc_an_bf16_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  RMC_TRY_CUDA(rmc_allow_smem(tc_an_bf16_kernel<NP>, smem));
   tc_an_bf16_kernel<NP><<<(unsigned)((m + 127) / 128), kAnThreads, smem, ctx->stream>>>(ma, mx, m, n, l, Y, ldy,
                                                                                          ctx->d_status);
   return RMC_OK;
@@ -1580,7 +1580,7 @@ template <int MT>
 int at_bf16_launch(rmc_ctx *ctx, const CUtensorMap &ma, const CUtensorMap &mx, int64_t m, int64_t n, int64_t l,
                    int64_t rows, int splits, float *part) {
   const size_t smem = AtBfCfg<MT>::kSmem;
-  RMC_TRY_CUDA(cudaFuncSetAttribute(tc_at_bf16_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  RMC_TRY_CUDA(rmc_allow_smem(tc_at_bf16_kernel<MT>, smem));
   dim3 grid((unsigned)((n + AtBfCfg<MT>::NC - 1) / AtBfCfg<MT>::NC), 1, (unsigned)splits);
   tc_at_bf16_kernel<MT><<<grid, 32 * (4 + 4 * MT), smem, ctx->stream>>>(ma, mx, m, n, l, rows, part, ctx->d_status);
   return RMC_OK;

@@ -119,6 +119,32 @@ def test_serve_interleaved_equals_alone(R, problems):
                 assert torch.equal(g, e), (nstreams, SPECS[i])
 
 
+def test_serve_eight_lanes_repeated_mix(R, problems):
+    """Eight lanes, each issuing its launches from its own host thread, on the mix repeated four times: every
+    request completes without error and equals the request alone (kernels whose shared-memory cap depends on
+    the problem are launched from several threads at once)."""
+    probs, refs = problems
+    waves = [list(range(len(probs)))] * 4
+    srv_outs = []
+    srv = R.Server(8 << 30, nstreams=8, max_batch=64)
+    tickets = {}
+    for w, wave in enumerate(waves):
+        for i in wave:
+            sp, A, b, sketch, prec = probs[i]
+            r, o = new_request(R, sp, A, b)
+            srv_outs.append((i, outputs(o)))
+            tickets[srv.submit(r, sketch=sketch, prec=prec)] = len(srv_outs) - 1
+        srv.progress()
+    srv.drain()
+    done = srv.poll()
+    srv.close()
+    assert sorted(t for t, _, _ in done) == sorted(tickets)
+    assert all(st == R.RMC_OK for _, st, _ in done), [st for _, st, _ in done if st != R.RMC_OK]
+    for i, outs in srv_outs:
+        for g, e in zip(outs, outputs(refs[i])):
+            assert torch.equal(g, e), SPECS[i]
+
+
 def test_serve_budget_and_invalid(R, problems):
     probs, _ = problems
     srv = R.Server(1 << 20, nstreams=1, max_batch=8)   # 1 MB: too small for the n = 300 least squares
