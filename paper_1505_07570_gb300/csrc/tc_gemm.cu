@@ -816,8 +816,12 @@ struct AtCfg {
   static constexpr int kXt = MT * kOmegaBytes;         // MT x (128 rows x 32 TF32)
   static constexpr int kHalf = kXt + kStg;
   static constexpr int kStage = (X3 ? 2 : 1) * kHalf;
-  static constexpr size_t kSmem = 1024 + (size_t)kStgStages * kStg + (size_t)kStages * kStage + 256;
-  static_assert(kSmem <= kSmemCap, "tc_at_kernel shared memory");
+  // staging ring: as many 32-row buffers of A as fit beside the operand stages, up to four, so that the loads of
+  // A run ahead of the transpose by more than the two operand stages
+  static constexpr int kFitRing = (int)((kSmemCap - 1024 - 256 - (size_t)kStages * kStage) / kStg);
+  static constexpr int kRing = kFitRing > 4 ? 4 : kFitRing;
+  static constexpr size_t kSmem = 1024 + (size_t)kRing * kStg + (size_t)kStages * kStage + 256;
+  static_assert(kRing >= 2 && kSmem <= kSmemCap, "tc_at_kernel shared memory");
 };
 
 template <int MT, bool X3>
@@ -833,10 +837,11 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~uintptr_t(1023));
   unsigned char *staging = smem;
-  unsigned char *operands = smem + kStgStages * Cfg::kStg;
+  constexpr int R = Cfg::kRing;
+  unsigned char *operands = smem + R * Cfg::kStg;
   uint64_t *stg_full = reinterpret_cast<uint64_t *>(operands + kStages * Cfg::kStage);
-  uint64_t *stg_empty = stg_full + kStgStages;
-  uint64_t *full = stg_empty + kStgStages;
+  uint64_t *stg_empty = stg_full + R;
+  uint64_t *full = stg_empty + R;
   uint64_t *empty = full + kStages;
   uint64_t *done = empty + kStages;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
@@ -850,7 +855,7 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
   constexpr uint32_t kCols = (X3 ? 2 : 1) * MT * NC;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStgStages; ++i) {
+    for (int i = 0; i < R; ++i) {
       tc::mbar_init(&stg_full[i], 1);
       tc::mbar_init(&stg_empty[i], kAtTrans);
     }
@@ -875,21 +880,28 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
-      for (int it = 0; it < num_it; ++it) {
-        const int st = it % kStages, sst = it % kStgStages;
-        if (*abort_flag || !tc::mbar_wait(&stg_empty[sst], ((it / kStgStages) & 1) ^ 1) ||
-            !tc::mbar_wait(&empty[st], ((it / kStages) & 1) ^ 1)) {
-          *abort_flag = 1;
-          rmc_report(status, RMC_ETIMEOUT);
+      int ia = 0;   // A tiles issued into the staging ring (up to R - 1 stages ahead of the operand stage)
+      bool ok = true;
+      for (int it = 0; it < num_it && ok; ++it) {
+        const int st = it % kStages;
+        for (; ia < num_it && ia < it + R; ++ia) {
+          const int sst = ia % R;
+          if (*abort_flag || !tc::mbar_wait(&stg_empty[sst], ((ia / R) & 1) ^ 1)) {
+            ok = false;
+            break;
+          }
+          const int32_t ya = (int32_t)(k_begin + (int64_t)ia * kKStage);
+          unsigned char *dst = staging + sst * Cfg::kStg;
+          tc::mbar_arrive_expect_tx(&stg_full[sst], Cfg::kStg);
+#pragma unroll
+          for (int atom = 0; atom < NC / 32; ++atom)
+            tc::tma_load_2d(dst + atom * kAtomBytes, &tmap_a, (int32_t)(n0 + atom * 32), ya, &stg_full[sst]);
+        }
+        if (!ok || *abort_flag || !tc::mbar_wait(&empty[st], ((it / kStages) & 1) ^ 1)) {
+          ok = false;
           break;
         }
         const int32_t y = (int32_t)(k_begin + (int64_t)it * kKStage);
-        unsigned char *dst = staging + sst * Cfg::kStg;
-        tc::mbar_arrive_expect_tx(&stg_full[sst], Cfg::kStg);
-#pragma unroll
-        for (int atom = 0; atom < NC / 32; ++atom)
-          tc::tma_load_2d(dst + atom * kAtomBytes, &tmap_a, (int32_t)(n0 + atom * 32), y, &stg_full[sst]);
         unsigned char *xt = operands + st * Cfg::kStage;
         tc::mbar_arrive_expect_tx(&full[st], (X3 ? 2 : 1) * Cfg::kXt);
 #pragma unroll
@@ -897,10 +909,13 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
           tc::tma_load_2d(xt + mt * kOmegaBytes, &tmap_xt, y, mt * 128, &full[st]);
           if (X3) tc::tma_load_2d(xt + Cfg::kHalf + mt * kOmegaBytes, &tmap_xl, y, mt * 128, &full[st]);
         }
-        ++issued;
       }
-      for (int it = issued > kStgStages ? issued - kStgStages : 0; it < issued; ++it)
-        (void)tc::mbar_wait(&stg_full[it % kStgStages], (it / kStgStages) & 1);
+      if (!ok) {
+        *abort_flag = 1;
+        rmc_report(status, RMC_ETIMEOUT);
+      }
+      // copies still in flight land before the CTA may exit
+      for (int k = ia > R ? ia - R : 0; k < ia; ++k) (void)tc::mbar_wait(&stg_full[k % R], (k / R) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -943,8 +958,8 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
     const int tl = (warp - 2) * 32 + lane;
     const int lq = tl & 7, grp = tl >> 3;
     for (int it = 0; it < num_it; ++it) {
-      const int st = it % kStages, sst = it % kStgStages;
-      if (!warp_wait(&stg_full[sst], (it / kStgStages) & 1, abort_flag, status)) break;
+      const int st = it % kStages, sst = it % R;
+      if (!warp_wait(&stg_full[sst], (it / R) & 1, abort_flag, status)) break;
       if (!warp_wait(&empty[st], ((it / kStages) & 1) ^ 1, abort_flag, status)) break;
       const unsigned char *src = staging + sst * Cfg::kStg;
       unsigned char *btile = operands + st * Cfg::kStage + Cfg::kXt;
