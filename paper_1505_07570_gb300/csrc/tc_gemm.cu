@@ -101,6 +101,57 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // Byte offset of (row r, 16-byte chunk q) in a tile with 128-byte rows and 128-byte swizzle.
 __device__ __forceinline__ int swz_off(int r, int q) { return r * 128 + ((q ^ (r & 7)) << 4); }
 
+// v with its 13 low mantissa bits cleared (the TF32 head), and the exact remainder.
+__device__ __forceinline__ float tf32_head(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+
+__device__ __forceinline__ void split4(float4 v, float4 &h, float4 &l) {
+  h = make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
+  l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+}
+
+// Transpose one staged tile of 32 rows of A x (32 kAtoms) columns -- kAtoms column atoms of 32 rows x 128 bytes,
+// 128-byte swizzled, as a 32 x 32 TMA box writes them -- into the K-major, 128-byte-swizzled operand tile (row c
+// = column c of A, its 32 K values in one 128-byte row).  The 8 kHalves lanes-groups of 8 split the work: unit
+// (kq, cq) = rows 4kq..4kq+3 x columns 4cq..4cq+3; lane lq of group g = 8 gh + gl takes kq = lq and the units
+// cq = c0 + 8 (gh + kHalves i), c0 = (gl + lq) mod 8.  Within a group the reads (chunk c0 ^ (4 (lq & 1) + t) of a
+// row) and the writes (chunk lq ^ (4 (c0 & 1) + t)) of the 8 lanes fall on 8 distinct 16-byte bank groups, and
+// every address is a per-thread constant plus a multiple of 4096 bytes (one column atom), so the loop carries
+// no address arithmetic.  X3: the remainder tile (the exact v - head) is written half_off bytes after the head.
+template <int kAtoms, int kHalves, bool X3>
+__device__ __forceinline__ void transpose_tile_tf32(const unsigned char *src, unsigned char *dst, int half_off,
+                                                    int tl) {
+  const int lq = tl & 7, gl = (tl >> 3) & 7, gh = tl >> 6;
+  const int c0 = (gl + lq) & 7;
+  int roff[4], woff[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    roff[t] = swz_off(4 * lq + t, c0);
+    woff[t] = swz_off(4 * c0 + t, lq);
+  }
+#pragma unroll
+  for (int i = 0; i < kAtoms / kHalves; ++i) {
+    const int atom = gh + kHalves * i;
+    const unsigned char *sa = src + atom * (32 * 128);
+    unsigned char *da = dst + atom * (32 * 128);
+    float4 v[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) v[t] = *reinterpret_cast<const float4 *>(sa + roff[t]);
+    const float4 o[4] = {make_float4(v[0].x, v[1].x, v[2].x, v[3].x), make_float4(v[0].y, v[1].y, v[2].y, v[3].y),
+                         make_float4(v[0].z, v[1].z, v[2].z, v[3].z), make_float4(v[0].w, v[1].w, v[2].w, v[3].w)};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (X3) {
+        float4 h, lo;
+        split4(o[j], h, lo);
+        *reinterpret_cast<float4 *>(da + woff[j]) = h;
+        *reinterpret_cast<float4 *>(da + half_off + woff[j]) = lo;
+      } else {
+        *reinterpret_cast<float4 *>(da + woff[j]) = o[j];
+      }
+    }
+  }
+}
+
 struct GaussArgs {
   const float *b;
   int64_t m, n, ntot, s;
@@ -241,23 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
         }
         const unsigned char *src = staging + sst * kBBytes;
         if (!BF16) {
-          // Unit (kq, cq): rows 4kq..4kq+3 x columns 4cq..4cq+3.  Lane l of an 8-lane group takes kq = l and
-          // cq = (d + l) mod 64, so both the swizzled reads and the swizzled writes of a group hit 8 distinct
-          // 16-byte bank groups.
-#pragma unroll 2
-          for (int d = grp; d < 64; d += 8) {
-            const int kq = l, cq = (d + l) & 63;
-            const int atom = cq >> 3, cc = cq & 7;
-            float4 v[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-              v[t] = *reinterpret_cast<const float4 *>(src + atom * kAtomBytes + swz_off(4 * kq + t, cc));
-            const int c4 = 4 * cq;
-            *reinterpret_cast<float4 *>(btile + swz_off(c4 + 0, kq)) = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
-            *reinterpret_cast<float4 *>(btile + swz_off(c4 + 1, kq)) = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
-            *reinterpret_cast<float4 *>(btile + swz_off(c4 + 2, kq)) = make_float4(v[0].z, v[1].z, v[2].z, v[3].z);
-            *reinterpret_cast<float4 *>(btile + swz_off(c4 + 3, kq)) = make_float4(v[0].w, v[1].w, v[2].w, v[3].w);
-          }
+          transpose_tile_tf32<kN / 32, 1, false>(src, btile, 0, tl);
         } else {
           // Unit (qk, cq): staging rows 8qk..8qk+7 x columns 4cq..4cq+3, written as BF16 into 16-byte K-chunk
           // 4h + qk of rows 4cq..4cq+3 of the K-major tile.  Lane l of group grp takes cq = 8 grp + 2 (l & 3) +
@@ -624,13 +659,6 @@ namespace {
 // split once in global memory; A's are split on chip (converter warps for Y = A X, the transposer warps for
 // W = X^T A, which write both parts of the transposed tile).
 
-// v with its 13 low mantissa bits cleared (the TF32 head), and the exact remainder.
-__device__ __forceinline__ float tf32_head(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
-
-__device__ __forceinline__ void split4(float4 v, float4 &h, float4 &l) {
-  h = make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
-  l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-}
 
 constexpr int kAnThreads = 256;   // warp 0 TMA, warp 1 MMA, warps 4-7 epilogue (X3: warps 2-7 also split A)
 constexpr int kAnConvWarps = 6;   // warps 2-7
@@ -951,41 +979,17 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_kernel(const __gri
     }
   } else {
    if (warp < 2 + kAtTrans) {
-    // transposers: staging (row-major, swizzled) -> K-major B tile (see the Gaussian kernel); X3 also writes the
-    // remainder tile.  Unit (kq, cq): rows 4kq..4kq+3 x columns 4cq..4cq+3, cq < NC/4; lane lq of a group of
-    // eight takes kq = lq and cq = (d + lq) mod NC/4, so each group's reads and writes hit 8 distinct 16-byte
-    // bank groups.
+    // transposers: staging (row-major, swizzled) -> K-major B tile, 16 groups of 8 lanes in two halves; X3 also
+    // writes the remainder tile
+    static_assert(kAtTrans == 4, "two halves of 8 lane groups");
     const int tl = (warp - 2) * 32 + lane;
-    const int lq = tl & 7, grp = tl >> 3;
     for (int it = 0; it < num_it; ++it) {
       const int st = it % kStages, sst = it % R;
       if (!warp_wait(&stg_full[sst], (it / R) & 1, abort_flag, status)) break;
       if (!warp_wait(&empty[st], ((it / kStages) & 1) ^ 1, abort_flag, status)) break;
       const unsigned char *src = staging + sst * Cfg::kStg;
       unsigned char *btile = operands + st * Cfg::kStage + Cfg::kXt;
-#pragma unroll 2
-      for (int d = grp; d < NC / 4; d += 4 * kAtTrans) {
-        const int kq = lq, cq = (d + lq) & (NC / 4 - 1);
-        const int atom = cq >> 3, cc = cq & 7;
-        float4 v[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          v[t] = *reinterpret_cast<const float4 *>(src + atom * kAtomBytes + swz_off(4 * kq + t, cc));
-        const int c4 = 4 * cq;
-        float4 o[4] = {make_float4(v[0].x, v[1].x, v[2].x, v[3].x), make_float4(v[0].y, v[1].y, v[2].y, v[3].y),
-                       make_float4(v[0].z, v[1].z, v[2].z, v[3].z), make_float4(v[0].w, v[1].w, v[2].w, v[3].w)};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (X3) {
-            float4 h, lo;
-            split4(o[j], h, lo);
-            *reinterpret_cast<float4 *>(btile + swz_off(c4 + j, kq)) = h;
-            *reinterpret_cast<float4 *>(btile + Cfg::kHalf + swz_off(c4 + j, kq)) = lo;
-          } else {
-            *reinterpret_cast<float4 *>(btile + swz_off(c4 + j, kq)) = o[j];
-          }
-        }
-      }
+      transpose_tile_tf32<NC / 32, 2, X3>(src, btile, Cfg::kHalf, tl);
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
@@ -1195,12 +1199,14 @@ template <int MT>
 struct AtBfCfg {
   static constexpr int NC = 256;
   static constexpr int kStg = NC * kKStage * 4;        // 32 KB of FP32 staging per 32 rows
-  static constexpr int kStgRing = 3;
   static constexpr int kXt = MT * 128 * 128;           // MT x (128 rows x 64 BF16)
   static constexpr int kB = NC * 128;                  // NC rows x 64 BF16
   static constexpr int kStage = kXt + kB;
+  // staging ring: as many 32-row FP32 buffers as fit beside the operand stages, up to four (two operand stages)
+  static constexpr int kFitRing = (int)((kSmemCap - 1024 - 256 - (size_t)kStages * kStage) / kStg);
+  static constexpr int kStgRing = kFitRing > 4 ? 4 : kFitRing;
   static constexpr size_t kSmem = 1024 + (size_t)kStgRing * kStg + (size_t)kStages * kStage + 256;
-  static_assert(kSmem <= kSmemCap, "tc_at_bf16_kernel shared memory");
+  static_assert(kStgRing >= 2 && kSmem <= kSmemCap, "tc_at_bf16_kernel shared memory");
 };
 
 template <int MT>
@@ -1253,27 +1259,28 @@ __global__ void __launch_bounds__(32 * (4 + 4 * MT), 1) tc_at_bf16_kernel(
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;   // staging buffers
+      // 32-row staging buffers issued: buffers 2 it and 2 it + 1 hold rows k_begin + 64 it .. +63 of A (row
+      // ranges are whole 64-row stages, so a stage never reaches into the next range; rows past m arrive as
+      // zeros).  The loads of A run up to kR - 2 buffers ahead of the operand stage, so they do not wait for the
+      // MMAs that free the next X^T buffer.
+      int issued = 0;
       bool failed = false;
       for (int it = 0; it < num_it && !failed; ++it) {
         const int st = it % kStages;
-        // rows k_begin + 64 it .. +63 of A (row ranges are whole 64-row stages, so a stage never reaches into the
-        // next range; rows past m arrive as zeros)
-        for (int h = 0; h < 2; ++h) {
-          const int is = 2 * it + h, sst = is % kR;
-          if (*abort_flag || !tc::mbar_wait(&stg_empty[sst], ((is / kR) & 1) ^ 1)) {
+        for (; issued < 2 * num_it && issued < 2 * it + kR; ++issued) {
+          const int sst = issued % kR;
+          if (*abort_flag || !tc::mbar_wait(&stg_empty[sst], ((issued / kR) & 1) ^ 1)) {
             failed = true;
             break;
           }
           tc::mbar_arrive_expect_tx(&stg_full[sst], Cfg::kStg);
-          const int32_t y = (int32_t)(k_begin + (int64_t)is * kKStage);
+          const int32_t y = (int32_t)(k_begin + (int64_t)issued * kKStage);
 #pragma unroll
           for (int atom = 0; atom < NC / 32; ++atom)
             tc::tma_load_2d(staging + sst * Cfg::kStg + atom * kAtomBytes, &tmap_a, (int32_t)(n0 + atom * 32), y,
                             &stg_full[sst]);
-          ++issued;
         }
-        if (failed || !tc::mbar_wait(&empty[st], ((it / kStages) & 1) ^ 1)) {
+        if (failed || *abort_flag || !tc::mbar_wait(&empty[st], ((it / kStages) & 1) ^ 1)) {
           failed = true;
           break;
         }
