@@ -36,6 +36,26 @@ __device__ __forceinline__ uint4 philox_block(uint64_t seed, uint32_t stream, ui
                   (uint32_t)(seed >> 32));
 }
 
+// The same rounds with each product written as one 32 x 32 -> 64-bit multiply (bit-identical results).  The
+// instruction selection differs: inside the tensor-core Gaussian sketch, where the draws share the SM with the
+// transposes and MMAs, this form measured about 4% faster; in a kernel that only draws, about 12% slower.
+__device__ __forceinline__ uint4 philox10_wide(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * c.x, p1 = (uint64_t)kPhiloxM1 * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 philox_block_wide(uint64_t seed, uint32_t stream, uint32_t instance,
+                                                   uint64_t index) {
+  return philox10_wide(make_uint4((uint32_t)index, (uint32_t)(index >> 32), stream, instance), (uint32_t)seed,
+                       (uint32_t)(seed >> 32));
+}
+
 // ((w >> 9) + 1/2) * 2^-23: exact in FP32, strictly inside (0, 1).  Built from the bit pattern of
 // 1 + (w >> 9) 2^-23 in [1, 2) minus (1 - 2^-24): the difference (2 (w >> 9) + 1) 2^-24 has at most 24
 // significant bits, so the subtraction is exact and no integer-to-float conversion is needed.

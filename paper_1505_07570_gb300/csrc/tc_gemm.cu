@@ -7,9 +7,10 @@
 //   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators) and issues tcgen05.mma
 //               (M=128, N=256, K=8) from one lane
 //   warps 2-3   transpose the 32 x 256 tile of A (staged by TMA) into the K-major, 128-byte-swizzled layout
+//               (BF16: rounding to BF16 on the way)
 //   warps 4-19  per stage of 32 rows: draw G^T (32 x 256) from Philox (the sketch stream: eight normals per
 //               block) straight into the same K-major layout, and fold the b column in with FP32 FMAs
-//   warps 4-7   epilogue: tcgen05.ld of the accumulators, written as this row range's partial sum
+//   8 of them   epilogue: tcgen05.ld of the accumulators, written as this row range's partial sum
 // Both sketch tiles share each transposed A tile.  Three stages of 64 KB are in flight; every wait is bounded
 // (RMC_ETIMEOUT after one second).
 #include <cuda.h>
@@ -32,15 +33,17 @@ constexpr int kAtomBytes = kKStage * 128;         // staging: 32 rows x 32 colum
 constexpr int kStgStages = 2;                     // TMA staging buffers (A rows, row-major)
 constexpr int kStages = 2;                        // operand buffers (G^T tiles + transposed A)
 constexpr int kStageBytes = kMT * kOmegaBytes + kBBytes;
-constexpr int kTransWarp0 = 2, kTransWarps = 2;   // warps 2-3 transpose staging -> K-major
-constexpr int kRngWarp0 = 4, kRngWarps = 16;      // warps 4-19 draw G^T
-constexpr int kThreads = 32 * (kRngWarp0 + kRngWarps);
+constexpr int kTransWarp0 = 2;                    // the transposers (staging -> K-major) start at warp 2
+constexpr int kRngWarps = 16;                     // the warps that draw G^T follow them
 constexpr int kTmemCols = kMT * kN;               // 512
 
 // TF32: an operand stage holds 32 rows of A (128 bytes of TF32 along K).  BF16: the same bytes hold 64 rows
 // (128 bytes of BF16), filled from two 32-row staging buffers.
 template <bool BF16>
 struct GaussCfg {
+  static constexpr int kTransWarps = 2;               // warps 2-3 transpose (four measured slower for TF32)
+  static constexpr int kRngWarp0 = kTransWarp0 + kTransWarps;
+  static constexpr int kThreads = 32 * (kRngWarp0 + kRngWarps);
   static constexpr int kKOp = BF16 ? 64 : 32;         // rows of A per operand stage
   static constexpr int kStgPer = kKOp / kKStage;      // staging buffers per operand stage
   static constexpr int kStg = BF16 ? 3 : kStgStages;  // staging ring
@@ -175,7 +178,7 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
 
 // grid: x = 256-row sketch range, y = 256-column tile of A, z = row range of A.
 template <bool BF16>
-__global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_constant__ CUtensorMap tmap_a,
+__global__ void __launch_bounds__(GaussCfg<BF16>::kThreads, 1) tc_gauss_kernel(const __grid_constant__ CUtensorMap tmap_a,
                                                                GaussArgs args) {
   using C = GaussCfg<BF16>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -203,10 +206,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
   if (threadIdx.x == 0) {
     for (int i = 0; i < C::kStg; ++i) {
       tc::mbar_init(&stg_full[i], 1);
-      tc::mbar_init(&stg_empty[i], kTransWarps);
+      tc::mbar_init(&stg_empty[i], C::kTransWarps);
     }
     for (int i = 0; i < kStages; ++i) {
-      tc::mbar_init(&full[i], kTransWarps + kRngWarps / (BF16 ? 1 : 2));   // transposers + the stage's drawers
+      tc::mbar_init(&full[i], C::kTransWarps + kRngWarps / (BF16 ? 1 : 2));   // transposers + the stage's drawers
       tc::mbar_init(&empty[i], 1);
     }
     tc::mbar_init(done, 1);
@@ -273,9 +276,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
       }
       tc::mma_commit(done);   // also issued after an abort: completes once the issued MMAs have
     }
-  } else if (warp < kRngWarp0) {
+  } else if (warp < C::kRngWarp0) {
     // ---------------------------------------------------------------- transposers: staging -> K-major
-    const int tl = (warp - kTransWarp0) * 32 + lane;       // 0..63
+    const int tl = (warp - kTransWarp0) * 32 + lane;       // 0 .. 32 kTransWarps - 1
     const int l = tl & 7, grp = tl >> 3;                   // 8 groups of 8 lanes
     int is = 0;                                            // staging buffers consumed
     for (int it = 0; it < num_it; ++it) {
@@ -292,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
         }
         const unsigned char *src = staging + sst * kBBytes;
         if (!BF16) {
-          transpose_tile_tf32<kN / 32, 1, false>(src, btile, 0, tl);
+          transpose_tile_tf32<kN / 32, C::kTransWarps / 2, false>(src, btile, 0, tl);
         } else {
           // Unit (qk, cq): staging rows 8qk..8qk+7 x columns 4cq..4cq+3, written as BF16 into 16-byte K-chunk
           // 4h + qk of rows 4cq..4cq+3 of the K-major tile.  Lane l of group grp takes cq = 8 grp + 2 (l & 3) +
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
     //         the two tiles).
     //   BF16: 64 K-rows per stage, all 16 warps on every stage.  Thread = (K-row quad kq = lane mod 16: one 8-byte
     //         half of a 16-byte K-chunk; group 2 (warp mod 8) + lane / 16 of tile warp / 8).
-    const int rw = warp - kRngWarp0;                        // 0..15
+    const int rw = warp - C::kRngWarp0;                        // 0..15
     constexpr int kTurns = BF16 ? 1 : 2;                    // warp groups taking turns on the stages
     const int turn = BF16 ? 0 : rw >> 3;
     const int kq = BF16 ? (lane & 15) : (lane & 7);
@@ -364,7 +367,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gauss_kernel(const __grid_cons
       for (int t = 0; t < 4; ++t) {
         const int64_t row = row0 + t;
         if (row < k_end) {
-          const uint4 w = philox_block(args.seed, kStreamGaussSketch, args.instance, (uint64_t)row * groups + gidx);
+          const uint4 w =
+              philox_block_wide(args.seed, kStreamGaussSketch, args.instance, (uint64_t)row * groups + gidx);
           const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
@@ -616,12 +620,12 @@ int rmc_tc_gauss_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int6
     constexpr size_t smem = GaussCfg<true>::kSmem;
     RMC_TRY_CUDA(rmc_allow_smem(tc_gauss_kernel<true>, smem));
     RmcProf prof(ctx, RMC_K_GAUSSIAN);
-    tc_gauss_kernel<true><<<grid, kThreads, smem, ctx->stream>>>(map, a);
+    tc_gauss_kernel<true><<<grid, GaussCfg<true>::kThreads, smem, ctx->stream>>>(map, a);
   } else {
     constexpr size_t smem = GaussCfg<false>::kSmem;
     RMC_TRY_CUDA(rmc_allow_smem(tc_gauss_kernel<false>, smem));
     RmcProf prof(ctx, RMC_K_GAUSSIAN);
-    tc_gauss_kernel<false><<<grid, kThreads, smem, ctx->stream>>>(map, a);
+    tc_gauss_kernel<false><<<grid, GaussCfg<false>::kThreads, smem, ctx->stream>>>(map, a);
   }
   tc_reduce_kernel<<<rmc_blocks(s * ntot, 256, 8192), 256, 0, ctx->stream>>>(
       static_cast<float *>(ws), splits, s, n, ntot, 1.0f / sqrtf((float)s), C, ldc, Cb);
