@@ -36,7 +36,7 @@ GAUSS_PREC = os.environ.get("RMC_BENCH_GAUSS_PREC", "tf32")
 # DRAM bytes per row of A per launch from ncu captures of `python bench.py --probe <kind>` (A 262,144 x 256 + b):
 # dram__bytes_read.sum + dram__bytes_write.sum divided by 262,144.  Re-capture when a kernel changes.
 PROFILED_DRAM_BYTES_PER_ROW = {
-    "gaussian_sketch": (270.385920e6 + 5.209600e6) / 262144,
+    "gaussian_sketch": (271.001344e6 + 5.668096e6) / 262144,
     "srht_stage1": (268.572928e6 + 42.968832e6) / 262144,
     "countsketch_gather": (271.636992e6 + 3.304704e6) / 262144,
 }
@@ -304,6 +304,17 @@ def run_ours(args, world, rank, local):
     e2e_seconds, _ = combine_over_ranks(e0.elapsed_time(e1) / 1e3, 0, world)
     e2e_value = step_bytes * args.steps * world / e2e_seconds / 1e9
     assert all(bool(torch.isfinite(x).all()) for x in xs)
+    # the host-to-device copy alone (pinned host memory, the copy stream, nothing else running): the e2e step
+    # cannot beat max(device step, this copy)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(copy_stream):
+        c0.record(copy_stream)
+        for _ in range(3):
+            bufs[1][0].copy_(A_h, non_blocking=True)
+            bufs[1][1].copy_(b_h, non_blocking=True)
+        c1.record(copy_stream)
+    torch.cuda.synchronize()
+    h2d_ms = c0.elapsed_time(c1) / 3
 
     if rank != 0:
         if world > 1:
@@ -398,7 +409,9 @@ def run_ours(args, world, rank, local):
                                " x s {1024, 4096}", "gaussian_prec": GAUSS_PREC, "l2": "inputs (1.07 GB) > L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof, "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": 1e3 * e2e_seconds / args.steps, "h2d_alone_ms": h2d_ms,
+                "h2d_alone_gbs": h2d / h2d_ms / 1e6},
         "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernels, "kernels_isolated": isolated,
         "gaussian_forms": forms_info, "lsr_precise": precise_info, "rsvd": rsvd_info, "batch": batch_info,
         "serve": serve_info,

@@ -836,7 +836,7 @@ __global__ void jacobi_finish_kernel(const T *W, const T *V, int l, float *Ub, f
 // accumulator: the other singular factor is recovered afterwards, see jacobi_right_kernel) and a group of G lanes
 // per column pair instead of a warp: a 1024-thread block rotates up to 1024 / G disjoint pairs per round, each
 // lane holding every G-th row (G = 16 up to l = 128 and 8 above in FP64; FP32 uses it above l = 128 with G = 8,
-// and jacobi_vec_kernel below that).
+// and jacobi_oe_kernel below that).
 // G lanes per pair (8 or 16; 1024 / G pairs per round at most).
 template <typename T, int G>
 __global__ void __launch_bounds__(1024) jacobi_grp_kernel(T *Wg, int l, T tol, int max_sweeps, int *status) {
@@ -911,79 +911,122 @@ __device__ __forceinline__ void rotation_fast(float alpha, float beta, float gam
   s = c * t;
 }
 
-// One-sided Jacobi for l <= 128 (FP32), the rotations and ordering of jacobi_grp_kernel with 8 lanes per column
-// pair, columns padded with zero rows to ldw = 32 NV (zeros change neither inner products nor rotations): lane j
-// of a group holds rows 4 j + 32 v .. +3 (v < NV) of both columns as float4 registers, so a pair is loaded once,
-// reduced, rotated in registers and stored once.  The block has exactly (l' / 2) x 8 threads (l' = l rounded up
-// to even) and the round-robin indices advance without divisions.
+
+// One-sided Jacobi for l <= 128 (FP32) in the odd-even ordering: the l' = l rounded up to even columns sit on
+// positions 0 .. l'-1; even rounds rotate the pairs of positions (2i, 2i+1), odd rounds (2i+1, 2i+2), and every
+// rotated pair swaps positions, so that in l' rounds (one sweep) each pair of columns meets exactly once (the
+// swaps of odd-even transposition reverse the order).  Group i (8 lanes, rows 4j + 32v .. +3 of each column in
+// float4 registers; padding rows are zeros) takes pair i of every round, and one of its two columns stays with it
+// into the next round: per round a group stores the column that leaves for its neighbour into that position's
+// shared-memory slot and, after the round's barrier, loads the one that arrives -- half the shared-memory traffic
+// of reloading both.  Even round: group i holds positions 2i (loaded) and 2i+1 (kept), sends 2i to group i-1 and
+// receives 2i+2 from group i+1; odd round: it holds 2i+1 (kept) and 2i+2, sends 2i+2 and receives 2i (group l'/2-1
+// only joins the shuffles in odd rounds; position 0 waits in its slot).  Each slot is written by one group and
+// read by one group per round, on opposite sides of the barrier, so one barrier per round suffices.  A zero padding column (odd l)
+// is never rotated; after an odd number of sweeps it sits at position 0, else at l'-1, and is skipped on output.
+// Columns leave in position order (a permutation of the input's): the callers rank them by norm.
 template <int NV>
-__global__ void __launch_bounds__(512) jacobi_vec_kernel(float *Wg, int l, float tol, int max_sweeps, int *status) {
+__global__ void __launch_bounds__(512) jacobi_oe_kernel(float *Wg, int l, float tol, int max_sweeps, int *status) {
   extern __shared__ __align__(16) float jv[];
   constexpr int ldw = 32 * NV;
   __shared__ int rotated;
-#pragma unroll 8
-  for (int e = threadIdx.x; e < l * ldw; e += blockDim.x) {
-    const int col = e / ldw, r = e % ldw;
-    jv[e] = r < l ? Wg[(int64_t)col * l + r] : 0.f;
-  }
   const int lp = (l + 1) & ~1;
-  const int grp = threadIdx.x >> 3, j = threadIdx.x & 7;
-  const int a = grp, b = lp - 1 - grp;
-  int ia = a - 1, ib = b - 1;   // (a - 1 + round) mod (lp - 1), (b - 1 + round) mod (lp - 1)
+#pragma unroll 8
+  for (int e = threadIdx.x; e < lp * ldw; e += blockDim.x) {
+    const int col = e / ldw, r = e % ldw;
+    jv[e] = (r < l && col < l) ? Wg[(int64_t)col * l + r] : 0.f;
+  }
+  __syncthreads();
+  // The block is a whole number of warps: groups past the l'/2 pairs ("real" false) hold zeros, touch no slot
+  // and only join the warp shuffles, so every lane of every warp runs the same shuffle sequence.
+  const int gi = threadIdx.x >> 3, j = threadIdx.x & 7;
+  const int last = lp / 2 - 1;
+  const bool real = gi <= last;
   const float tol2 = tol * tol;
+  float4 arr[NV], keep[NV];
+  auto store = [&](int pos, const float4 (&x)[NV]) {
+    float4 *d = reinterpret_cast<float4 *>(jv + (size_t)pos * ldw) + j;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) d[8 * v] = x[v];
+  };
+  auto load = [&](int pos, float4 (&x)[NV]) {
+    const float4 *a = reinterpret_cast<const float4 *>(jv + (size_t)pos * ldw) + j;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = a[8 * v];
+  };
+#pragma unroll
+  for (int v = 0; v < NV; ++v) arr[v] = keep[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (real) {
+    load(2 * gi, arr);
+    load(2 * gi + 1, keep);
+  }
+  // Rotate (x, y) in place (x <- c x - s y, y <- s x + c y) where live and the pair's inner products ask for it.
+  // Called by every thread in every round: the inner products are reduced over the group's 8 lanes by shuffles
+  // that name the whole warp.
+  auto rotate = [&](float4 (&x)[NV], float4 (&y)[NV], bool live) {
+    float alpha = 0.f, beta = 0.f, gamma = 0.f;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      alpha = fmaf(x[v].x, x[v].x, fmaf(x[v].y, x[v].y, fmaf(x[v].z, x[v].z, fmaf(x[v].w, x[v].w, alpha))));
+      beta = fmaf(y[v].x, y[v].x, fmaf(y[v].y, y[v].y, fmaf(y[v].z, y[v].z, fmaf(y[v].w, y[v].w, beta))));
+      gamma = fmaf(x[v].x, y[v].x, fmaf(x[v].y, y[v].y, fmaf(x[v].z, y[v].z, fmaf(x[v].w, y[v].w, gamma))));
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {   // the 8 lanes of a group are aligned in the warp
+      alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+      beta += __shfl_xor_sync(0xffffffffu, beta, o);
+      gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
+    }
+    if (live && gamma != 0.f && gamma * gamma > tol2 * alpha * beta) {
+      float c, sn;
+      rotation_fast(alpha, beta, gamma, c, sn);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float4 u = x[v], w = y[v];
+        x[v] = make_float4(c * u.x - sn * w.x, c * u.y - sn * w.y, c * u.z - sn * w.z, c * u.w - sn * w.w);
+        y[v] = make_float4(sn * u.x + c * w.x, sn * u.y + c * w.y, sn * u.z + c * w.z, sn * u.w + c * w.w);
+      }
+      if (j == 0) rotated = 1;
+    }
+  };
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
-    for (int round = 0; round < lp - 1; ++round) {
-      int p = a == 0 ? 0 : 1 + ia, q = b == 0 ? 0 : 1 + ib;
-      if (p > q) {
-        const int tt = p;
-        p = q;
-        q = tt;
-      }
-      ia = (ia + 1 == lp - 1) ? 0 : ia + 1;
-      ib = (ib + 1 == lp - 1) ? 0 : ib + 1;
-      // the padding column of an odd l sits out: its partner p (< l, touched by no other group in this round)
-      // stands in for it and nothing is stored
-      const bool live = q < l;
-      float4 x[NV], y[NV];
-      float alpha = 0.f, beta = 0.f, gamma = 0.f;
-      float4 *wp = reinterpret_cast<float4 *>(jv + (size_t)p * ldw) + j;
-      float4 *wq = reinterpret_cast<float4 *>(jv + (size_t)(live ? q : p) * ldw) + j;
+#pragma unroll 1
+    for (int round = 0; round < lp; round += 2) {
+      // even round: (2i, 2i+1) = (arr, keep); after the swap position 2i holds the rotated keep
+      rotate(arr, keep, real);
+      if (real) {
+        store(2 * gi, keep);                    // leaves for group i-1 (position 2i)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        x[v] = wp[8 * v];
-        y[v] = wq[8 * v];
-        alpha = fmaf(x[v].x, x[v].x, fmaf(x[v].y, x[v].y, fmaf(x[v].z, x[v].z, fmaf(x[v].w, x[v].w, alpha))));
-        beta = fmaf(y[v].x, y[v].x, fmaf(y[v].y, y[v].y, fmaf(y[v].z, y[v].z, fmaf(y[v].w, y[v].w, beta))));
-        gamma = fmaf(x[v].x, y[v].x, fmaf(x[v].y, y[v].y, fmaf(x[v].z, y[v].z, fmaf(x[v].w, y[v].w, gamma))));
-      }
-#pragma unroll
-      for (int o = 1; o < 8; o <<= 1) {   // the 8 lanes of a group are aligned in the warp
-        alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
-        beta += __shfl_xor_sync(0xffffffffu, beta, o);
-        gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
-      }
-      if (live && gamma != 0.f && gamma * gamma > tol2 * alpha * beta) {
-        float c, sn;
-        rotation_fast(alpha, beta, gamma, c, sn);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const float4 u = x[v], w = y[v];
-          wp[8 * v] = make_float4(c * u.x - sn * w.x, c * u.y - sn * w.y, c * u.z - sn * w.z, c * u.w - sn * w.w);
-          wq[8 * v] = make_float4(sn * u.x + c * w.x, sn * u.y + c * w.y, sn * u.z + c * w.z, sn * u.w + c * w.w);
-        }
-        if (j == 0) rotated = 1;
+        for (int v = 0; v < NV; ++v) keep[v] = arr[v];   // position 2i+1 stays
       }
       __syncthreads();
+      if (real && gi < last) load(2 * gi + 2, arr);      // arrives from group i+1
+      // odd round: (2i+1, 2i+2) = (keep, arr); after the swap position 2i+2 holds the rotated keep
+      rotate(keep, arr, real && gi < last);
+      if (real && gi < last) {
+        store(2 * gi + 2, keep);                // leaves for group i+1 (position 2i+2)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) keep[v] = arr[v];   // position 2i+1 stays
+      }
+      __syncthreads();
+      if (real) load(2 * gi, arr);              // arrives from group i-1 (group 0: position 0, unchanged)
     }
     if (!rotated) break;
     __syncthreads();
   }
   if (sweep == max_sweeps && threadIdx.x == 0) rmc_report(status, RMC_ENUMERIC);
+  const int done = sweep < max_sweeps ? sweep + 1 : max_sweeps;
+  if (real) store(2 * gi + 1, keep);            // position 2i+1 lived in registers
   __syncthreads();
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) Wg[e] = jv[(e / l) * ldw + e % l];
+  const int pad = (lp == l) ? -1 : ((done & 1) ? 0 : lp - 1);
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int c = e / l, r = e % l;
+    const int pos = (pad >= 0 && c >= pad) ? c + 1 : c;
+    Wg[e] = jv[(size_t)pos * ldw + r];
+  }
 }
 
 // After jacobi_grp_kernel on R (R V = W, columns of W orthogonal): sigma_j = ||w_j|| (FP64 sum), the columns
@@ -1690,14 +1733,15 @@ static bool jacobi_grp_fits(int l, bool fp64) {
 // FP32 Jacobi of the column-major l x l W (l <= 128) with the vectorised kernel.
 static int launch_jacobi_vec(cudaStream_t st, float *W, int l, float tol, int *status) {
   const int nv = (l + 31) / 32;
-  const size_t smem = sizeof(float) * 32 * nv * (size_t)l;
-  const unsigned threads = (unsigned)(((l + 1) & ~1) / 2 * 8);
+  const size_t smem = sizeof(float) * 32 * nv * (size_t)((l + 1) & ~1);   // one slot per position
+  // eight lanes per column pair, rounded up to whole warps (the kernel's shuffles name every lane of a warp)
+  const unsigned threads = (unsigned)((((l + 1) & ~1) / 2 * 8 + 31) / 32 * 32);
   switch (nv) {
 #define RMC_JV(NV)                                                                                            \
   case NV:                                                                                                    \
     if (smem > 48 * 1024)                                                                                     \
-      RMC_TRY_CUDA(rmc_allow_smem(jacobi_vec_kernel<NV>, smem));                                              \
-    jacobi_vec_kernel<NV><<<1, threads, smem, st>>>(W, l, tol, 60, status);                                   \
+      RMC_TRY_CUDA(rmc_allow_smem(jacobi_oe_kernel<NV>, smem));                                               \
+    jacobi_oe_kernel<NV><<<1, threads, smem, st>>>(W, l, tol, 60, status);                                    \
     break;
     RMC_JV(1)
     RMC_JV(2)
@@ -1710,11 +1754,35 @@ static int launch_jacobi_vec(cudaStream_t st, float *W, int l, float tol, int *s
   return RMC_OK;
 }
 
+// R (FP64 row-major) -> W = R^T column-major in FP32, i.e. the same entries in the same order.
+__global__ void rows_as_cols_kernel(const double *R, int l, float *W) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < l * l; e += gridDim.x * blockDim.x) W[e] = (float)R[e];
+}
+
+// Left singular vectors of R from its right ones: R = M diag(sigma) N^T gives M = R N diag(sigma)^-1, M[:, c] =
+// R N[:, c] / sigma_c in FP64 with R upper triangular (one block per column c; the counterpart of
+// jacobi_right_kernel).
+__global__ void jacobi_left_from_right_kernel(const double *R, int l, const float *N, const float *sigma,
+                                              float *M) {
+  const int c = blockIdx.x;
+  const double inv = sigma[c] > 0.f ? 1.0 / (double)sigma[c] : 0.0;
+  for (int r = threadIdx.x; r < l; r += blockDim.x) {
+    double acc = 0.0;
+    for (int i = r; i < l; ++i) acc += R[(int64_t)r * l + i] * (double)N[(int64_t)i * l + c];
+    M[(int64_t)r * l + c] = (float)(acc * inv);
+  }
+}
+
 // Jacobi on R (FP64 row-major upper, l x l) with the group kernel: M (left singular vectors of R, row-major) and
 // sigma, descending.  fp64: rotations in FP64 (else FP32, FP64 below l = 33 as jacobi_in_fp64 says).
+// With right != nullptr and the FP32 odd-even kernel (33 <= l <= 128), the rotations run on the columns of R^T
+// (the rows of R), which for a triangular factor converge in fewer sweeps (nine against eleven on a 1/i spectrum
+// at l = 120): their normalised columns are then R's right singular vectors, written to right, and M follows as
+// R right diag(sigma)^-1; *right_done tells the caller which of the two it still has to form.
 static int launch_jacobi_grp(rmc_ctx *ctx, const double *R, int l, double *work, float *M, float *sigma,
-                             bool fp64) {
+                             bool fp64, float *right = nullptr, bool *right_done = nullptr) {
   cudaStream_t st = ctx->stream;
+  if (right_done) *right_done = false;
   if (fp64 || jacobi_in_fp64(l)) {
     const double tol = 8 * 2.220446049250313e-16 * sqrt((double)l);
     const size_t smem = sizeof(double) * (size_t)l * l;
@@ -1733,6 +1801,16 @@ static int launch_jacobi_grp(rmc_ctx *ctx, const double *R, int l, double *work,
     const float tol = 4 * 1.1920929e-7f * sqrtf((float)l);
     const size_t smem = sizeof(float) * (size_t)l * l;
     float *Wf = reinterpret_cast<float *>(work);
+    if (l <= 128 && right) {
+      rows_as_cols_kernel<<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, Wf);
+      RMC_TRY(launch_jacobi_vec(st, Wf, l, tol, ctx->d_status));
+      jacobi_left_kernel<float><<<1, 256, sizeof(double) * l, st>>>(Wf, l, right, sigma);
+      jacobi_left_from_right_kernel<<<l, 128, 0, st>>>(R, l, right, sigma, M);
+      rmc_note_launch(4);
+      RMC_LAUNCH_CHECK();
+      *right_done = true;
+      return RMC_OK;
+    }
     to_colmajor_kernel<float><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, Wf);
     if (l <= 128) {
       RMC_TRY(launch_jacobi_vec(st, Wf, l, tol, ctx->d_status));
@@ -1776,9 +1854,12 @@ int rmc_launch_svd_wide(rmc_ctx *ctx, const float *B, int64_t l_, int64_t n, int
   RMC_TRY(rmc_launch_cholqr2(ctx, Bt, n, l, l, R, rest, 2, true));           // B^T = Q2 R
   RmcProf prof(ctx, RMC_K_SMALL);
   if (jacobi_grp_fits(l, ctx->small_fp64)) {
-    RMC_TRY(launch_jacobi_grp(ctx, R, l, W, M, sigma, ctx->small_fp64));
-    jacobi_right_kernel<<<l, 128, 0, st>>>(R, l, M, sigma, Ub);                // Ub = R^T M diag(sigma)^-1
-    rmc_note_launch();
+    bool ub_done = false;
+    RMC_TRY(launch_jacobi_grp(ctx, R, l, W, M, sigma, ctx->small_fp64, Ub, &ub_done));
+    if (!ub_done) {
+      jacobi_right_kernel<<<l, 128, 0, st>>>(R, l, M, sigma, Ub);              // Ub = R^T M diag(sigma)^-1
+      rmc_note_launch();
+    }
   } else {
     rmc_note_launch(3);
     const size_t smem64 = 2 * sizeof(double) * (size_t)l * l, smem32 = 2 * sizeof(float) * (size_t)l * l;

@@ -156,7 +156,8 @@ __device__ __forceinline__ void transpose_tile_tf32(const unsigned char *src, un
 }
 
 struct GaussArgs {
-  const float *b;
+  const float *b;  // the extra column folded in by the drawing warps: b[row * ldb] (nullptr: none)
+  int64_t ldb;
   int64_t m, n, ntot, s;
   uint64_t seed;
   uint32_t instance;
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(GaussCfg<BF16>::kThreads, 1) tc_gauss_kernel(c
       if (with_b) {
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-          if (row0 + t < k_end) bv[t] = __ldg(args.b + row0 + t);
+          if (row0 + t < k_end) bv[t] = __ldg(args.b + (row0 + t) * args.ldb);
       }
       float z[4][8];
 #pragma unroll
@@ -495,14 +496,15 @@ __global__ void draw_floor_sum_kernel(const double *part, int n, double *sum) {
 }
 
 __global__ void tc_reduce_kernel(const float *__restrict__ part, int splits, int64_t s, int64_t n, int64_t ntot,
-                                 float scale, float *__restrict__ C, int64_t ldc, float *__restrict__ Cb) {
+                                 float scale, float *__restrict__ C, int64_t ldc, float *__restrict__ Cb,
+                                 int64_t ldcb) {
   const int64_t total = s * ntot;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     float acc = 0.f;
     for (int t = 0; t < splits; ++t) acc += part[t * total + e];
     const int64_t r = e / ntot, c = e - r * ntot;
     if (c < n) C[r * ldc + c] = acc * scale;
-    else Cb[r] = acc * scale;
+    else Cb[r * ldcb] = acc * scale;
   }
 }
 
@@ -597,6 +599,16 @@ int rmc_tc_gauss_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int6
   const bool bf16 = prec == RMC_BF16;
   const int kop = bf16 ? GaussCfg<true>::kKOp : GaussCfg<false>::kKOp;
   const int64_t ntot = n + (b ? 1 : 0);
+  // A matrix with one column past a multiple of 256 (an augmented [A, b] sketched as one matrix): its last column
+  // is folded in by the drawing warps like b, instead of a second column tile that would draw every normal again
+  int64_t ldb = 1, ldcb = 1;
+  if (!b && n > kN && n % kN == 1) {
+    b = A + (n - 1);
+    ldb = lda;
+    Cb = C + (n - 1);
+    ldcb = ldc;
+    --n;
+  }
   CUtensorMap map;
   RMC_TRY(make_tmap(&map, A, m, n, lda, kKStage));
   const int64_t mt = (s + kM * kMT - 1) / (kM * kMT), nt = (n + kN - 1) / kN;
@@ -606,6 +618,7 @@ int rmc_tc_gauss_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int6
   rows = (rows + kop - 1) / kop * kop;
   GaussArgs a;
   a.b = b;
+  a.ldb = ldb;
   a.m = m;
   a.n = n;
   a.ntot = ntot;
@@ -628,7 +641,7 @@ int rmc_tc_gauss_sketch(rmc_ctx *ctx, const float *A, int64_t m, int64_t n, int6
     tc_gauss_kernel<false><<<grid, GaussCfg<false>::kThreads, smem, ctx->stream>>>(map, a);
   }
   tc_reduce_kernel<<<rmc_blocks(s * ntot, 256, 8192), 256, 0, ctx->stream>>>(
-      static_cast<float *>(ws), splits, s, n, ntot, 1.0f / sqrtf((float)s), C, ldc, Cb);
+      static_cast<float *>(ws), splits, s, n, ntot, 1.0f / sqrtf((float)s), C, ldc, Cb, ldcb);
   rmc_note_launch(2);
   RMC_LAUNCH_CHECK();
   return RMC_OK;

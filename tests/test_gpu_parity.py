@@ -235,8 +235,10 @@ def test_rsvd_exact_rank(R, q):
 # TF32 keeps 10 mantissa bits: the sketch is compared at 2e-3 relative Frobenius error (the truncation of A
 # to TF32 alone shrinks entries by ~2^-11 on average), and least squares at the accuracy that implies.
 
+# n = 257 and 513: the column past the last full 256-column tile is folded in by the drawing warps
 @pytest.mark.parametrize("m,n,s,pad", [(2048, 512, 256, 0), (4097, 65, 300, 0), (70000, 20, 128, 4),
-                                       (1000, 37, 100, 3), (1, 4, 1, 0), (300000, 256, 1024, 0)])
+                                       (1000, 37, 100, 3), (1, 4, 1, 0), (300000, 256, 1024, 0),
+                                       (5000, 257, 600, 3), (3001, 513, 256, 3)])
 def test_gaussian_tf32_parity(R, m, n, s, pad):
     A = workloads.lowrank() if (m, n) == (2048, 512) else workloads.gaussian(m, n, seed=m + n)
     Ad = torch.zeros(m, n + pad, device="cuda")
@@ -274,7 +276,8 @@ def test_lsr_gaussian_tf32(R, m, n, s):
 # 2^-9 sqrt(2/3) = 1.6e-3, also for a sum of random-sign products; sketches and products are tested at 5e-3.
 
 @pytest.mark.parametrize("m,n,s,pad", [(2048, 512, 256, 0), (4097, 64, 300, 0), (70000, 20, 128, 4),
-                                       (1000, 36, 100, 4), (1, 4, 1, 0), (300000, 256, 1024, 0), (130, 260, 513, 0)])
+                                       (1000, 36, 100, 4), (1, 4, 1, 0), (300000, 256, 1024, 0), (130, 260, 513, 0),
+                                       (5000, 257, 600, 3)])
 def test_gaussian_bf16_parity(R, m, n, s, pad):
     A = workloads.lowrank() if (m, n) == (2048, 512) else workloads.gaussian(m, n, seed=m + n)
     Ad = torch.zeros(m, n + pad, device="cuda")
