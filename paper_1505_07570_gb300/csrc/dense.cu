@@ -387,99 +387,95 @@ __global__ void __launch_bounds__(512) chol32_inv_kernel(double *G, int l, float
 // pivot row: in step j every row below it is updated from row j alone,
 //   P[i][k] -= g_i P[j][k]   (k >= i),   B[i][c] -= g_i B[j][c]   (c <= j),   g_i = P[j][i] / P[j][j],  i > j,
 // with B = I at the start; finally P[j][k] = r_j U[j][k] and B[j][c] = r_j Y[j][c], r_j = sqrt(P[j][j]) and
-// Y = U^-T (forward substitution on U^T Y = I, row j of Y final in step j).  No thread writes row j in step j.
-// P is the packed upper triangle (row-major, (i, k) at i l - i(i+1)/2 + k), B the packed lower one ((i, c) at
-// i(i+1)/2 + c).  Warp w updates rows j + 1 + w + 16 r (r < 8), lanes along the row in 32-wide chunks; row j's
-// chunk is loaded once for all the warp's rows, and every load of a chunk is issued before its stores (the
-// compiler cannot see that the stores never touch row j), so a step costs a few shared-memory latencies.
+// Y = U^-T (forward substitution on U^T Y = I, row j of Y final in step j).
+// The rows live in registers: warp w owns rows i = w + 16 r (r < 8), lane q holds columns 32 c + q (c < 4) of P
+// and of B (entries outside a row's triangle are carried but never read).  In step j the owner of row j
+// publishes it to shared memory (two buffers, alternating with j), and after the step's one barrier every warp
+// reads it and updates its own rows below j in registers -- the trailing matrix never passes through shared
+// memory.  The arithmetic is the packed right-looking form's, operation for operation.
 constexpr int kCholFusedMaxL = 128;
 constexpr int kCholFusedThreads = 512;
 
 __global__ void __launch_bounds__(kCholFusedThreads) chol32_fused_kernel(double *G, int l, float *Rinv32, int *fail) {
-  extern __shared__ float cfs[];
-  const int N = l * (l + 1) / 2;
-  float *P = cfs, *B = cfs + N, *invr = cfs + 2 * N;
+  __shared__ float prow[2][kCholFusedMaxL], brow[2][kCholFusedMaxL], invr[kCholFusedMaxL];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  // the upper triangle of G, rounded to FP32 (a flat loop, so that the loads of one thread overlap)
-#pragma unroll 8
-  for (int e = t; e < l * l; e += kCholFusedThreads) {
-    const int i = e / l, k = e - i * l;
-    const double g = G[e];
-    if (k >= i) P[i * l - i * (i + 1) / 2 + k] = (float)g;
+  float P[8][4], B[8][4];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = w + 16 * r;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int k = 32 * c + lane;
+      P[r][c] = (i < l && k < l && k >= i) ? (float)G[(int64_t)i * l + k] : 0.f;
+      B[r][c] = (i < l && k == i) ? 1.f : 0.f;
+    }
   }
-  for (int e = t; e < N; e += kCholFusedThreads) B[e] = 0.f;
-  __syncthreads();
-  for (int i = t; i < l; i += kCholFusedThreads) B[i * (i + 1) / 2 + i] = 1.f;
-  __syncthreads();
   for (int j = 0; j < l; ++j) {
-    const int pj = j * l - j * (j + 1) / 2, bj = j * (j + 1) / 2;   // P[pj + k] = (j, k), B[bj + c] = (j, c)
-    const float d = P[pj + j];
+    const int buf = j & 1;
+    if (w == (j & 15)) {                       // the owner publishes row j (final since step j - 1)
+      const int rj = j >> 4;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float pv = 0.f, bv = 0.f;
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+          if (r == rj) {
+            pv = P[r][c];
+            bv = B[r][c];
+          }
+        prow[buf][32 * c + lane] = pv;
+        brow[buf][32 * c + lane] = bv;
+      }
+    }
+    __syncthreads();
+    const float d = prow[buf][j];
     if (!(d > 0.f) || !isfinite(d)) {        // uniform: every thread read the same pivot
       if (t == 0) fail[0] = 1;
       return;
     }
     const float invd = 1.f / d;
     if (t == 0) invr[j] = 1.f / sqrtf(d);
-    float pjk[4], bjc[4], g[8];
+    float pjk[4], bjc[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int k = 32 * c + lane;
-      pjk[c] = (k > j && k < l) ? P[pj + k] : 0.f;
-      bjc[c] = (k <= j) ? B[bj + k] : 0.f;
+      pjk[c] = (k > j && k < l) ? prow[buf][k] : 0.f;
+      bjc[c] = (k <= j) ? brow[buf][k] : 0.f;
     }
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      const int i = j + 1 + w + 16 * r;
-      g[r] = i < l ? P[pj + i] * invd : 0.f;
-    }
-    // upper: rows i, columns k >= i
+      const int i = w + 16 * r;
+      if (i > j && i < l) {                    // uniform across the warp
+        const float g = prow[buf][i] * invd;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int i = j + 1 + w + 16 * r;
-      if (i >= l) break;                      // uniform across the warp
-      const int pi = i * l - i * (i + 1) / 2;
-      float v[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int k = 32 * c + lane;
-        v[c] = (k >= i && k < l) ? P[pi + k] : 0.f;
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int k = 32 * c + lane;
-        if (k >= i && k < l) P[pi + k] = fmaf(-g[r], pjk[c], v[c]);
+        for (int c = 0; c < 4; ++c) {
+          const int k = 32 * c + lane;
+          if (k >= i && k < l) P[r][c] = fmaf(-g, pjk[c], P[r][c]);
+          if (k <= j) B[r][c] = fmaf(-g, bjc[c], B[r][c]);
+        }
       }
     }
-    // lower: rows i, columns c <= j
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int i = j + 1 + w + 16 * r;
-      if (i >= l) break;
-      const int bi = i * (i + 1) / 2;
-      float v[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int cc = 32 * c + lane;
-        v[c] = (cc <= j) ? B[bi + cc] : 0.f;
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int cc = 32 * c + lane;
-        if (cc <= j) B[bi + cc] = fmaf(-g[r], bjc[c], v[c]);
-      }
-    }
-    __syncthreads();
   }
+  __syncthreads();   // invr complete
   if (t == 0) fail[0] = 0;
   // R (FP64, upper, zeros below) and R^-1 = Y^T (FP32, row-major): R[i][k] = P[i][k] / r_i, R^-1[c][j] = B[j][c] / r_j
-  for (int e = t; e < l * l; e += kCholFusedThreads) {
-    const int i = e / l, k = e % l;
-    G[e] = (k >= i) ? (double)(P[i * l - i * (i + 1) / 2 + k] * invr[i]) : 0.0;
-    Rinv32[e] = (k >= i) ? B[k * (k + 1) / 2 + i] * invr[k] : 0.f;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = w + 16 * r;
+    if (i < l) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int k = 32 * c + lane;
+        if (k < l) {
+          G[(int64_t)i * l + k] = (k >= i) ? (double)(P[r][c] * invr[i]) : 0.0;
+          Rinv32[(int64_t)k * l + i] = (k <= i) ? B[r][c] * invr[i] : 0.f;
+        }
+      }
+    }
   }
 }
 
-size_t chol32_fused_smem_bytes(int l) { return sizeof(float) * ((size_t)l * (l + 1) + (size_t)l); }
+size_t chol32_fused_smem_bytes(int l) { (void)l; return 0; }
 
 // Least squares on the augmented FP64 Gram matrix G ((n+1) x (n+1), last column g = [S^T A]^T S^T b):
 // U = chol32(G11), then x0 = U^-1 U^-T g and x += U^-1 U^-T (g - G11 x) with FP64 residuals (iters times).
