@@ -442,6 +442,8 @@ __global__ void __launch_bounds__(kCholFusedThreads) chol32_fused_kernel(double 
       pjk[c] = (k > j && k < l) ? prow[buf][k] : 0.f;
       bjc[c] = (k <= j) ? brow[buf][k] : 0.f;
     }
+    // pjk is zero at k <= j and k >= l, bjc at k > j: the updates need no masks.  Where they reach entries
+    // outside row i's triangle (j < k < i of P) those entries are never read again.
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int i = w + 16 * r;
@@ -449,9 +451,8 @@ __global__ void __launch_bounds__(kCholFusedThreads) chol32_fused_kernel(double 
         const float g = prow[buf][i] * invd;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const int k = 32 * c + lane;
-          if (k >= i && k < l) P[r][c] = fmaf(-g, pjk[c], P[r][c]);
-          if (k <= j) B[r][c] = fmaf(-g, bjc[c], B[r][c]);
+          P[r][c] = fmaf(-g, pjk[c], P[r][c]);
+          B[r][c] = fmaf(-g, bjc[c], B[r][c]);
         }
       }
     }
