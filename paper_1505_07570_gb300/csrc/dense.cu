@@ -1728,7 +1728,7 @@ static bool jacobi_grp_fits(int l, bool fp64) {
 }
 
 // FP32 Jacobi of the column-major l x l W (l <= 128) with the vectorised kernel.
-static int launch_jacobi_vec(cudaStream_t st, float *W, int l, float tol, int *status) {
+static int launch_jacobi_oe(cudaStream_t st, float *W, int l, float tol, int *status) {
   const int nv = (l + 31) / 32;
   const size_t smem = sizeof(float) * 32 * nv * (size_t)((l + 1) & ~1);   // one slot per position
   // eight lanes per column pair, rounded up to whole warps (the kernel's shuffles name every lane of a warp)
@@ -1800,7 +1800,7 @@ static int launch_jacobi_grp(rmc_ctx *ctx, const double *R, int l, double *work,
     float *Wf = reinterpret_cast<float *>(work);
     if (l <= 128 && right) {
       rows_as_cols_kernel<<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, Wf);
-      RMC_TRY(launch_jacobi_vec(st, Wf, l, tol, ctx->d_status));
+      RMC_TRY(launch_jacobi_oe(st, Wf, l, tol, ctx->d_status));
       jacobi_left_kernel<float><<<1, 256, sizeof(double) * l, st>>>(Wf, l, right, sigma);
       jacobi_left_from_right_kernel<<<l, 128, 0, st>>>(R, l, right, sigma, M);
       rmc_note_launch(4);
@@ -1810,7 +1810,7 @@ static int launch_jacobi_grp(rmc_ctx *ctx, const double *R, int l, double *work,
     }
     to_colmajor_kernel<float><<<rmc_blocks(l * l, 256), 256, 0, st>>>(R, l, Wf);
     if (l <= 128) {
-      RMC_TRY(launch_jacobi_vec(st, Wf, l, tol, ctx->d_status));
+      RMC_TRY(launch_jacobi_oe(st, Wf, l, tol, ctx->d_status));
     } else {
       if (smem > 48 * 1024)
         RMC_TRY_CUDA(rmc_allow_smem(jacobi_grp_kernel<float, 8>, smem));
