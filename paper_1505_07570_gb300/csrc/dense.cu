@@ -1937,7 +1937,7 @@ constexpr int kRefineSteps = 4;
 static int atr_chunks(int64_t s) { return (int)std::min<int64_t>(64, std::max<int64_t>(1, s / 32)); }
 
 struct LsrBufs {
-  double *G, *xs, *r, *part, *gpart;
+  double *G, *xs, *r, *part, *gpart, *Gsq;
   float *Rf, *Dinv, *Ri, *M;
   int *flags;  // kLsrFlagWords words, see the refinement kernels
 };
@@ -1955,8 +1955,46 @@ static LsrBufs lsr_carve(WsCarve &w, int64_t s, int64_t n, int num_sms) {
   b.Dinv = w.take<float>((size_t)nb * kPanel * kPanel);
   b.Ri = w.take<float>((size_t)n * n);
   b.M = w.take<float>((size_t)n * n);
+  b.Gsq = n <= kCholFusedMaxL ? w.take<double>((size_t)n * n) : nullptr;
   b.gpart = reinterpret_cast<double *>(w.take<char>(gram_ws(s, l, num_sms)));
   return b;
+}
+
+__global__ void lsr_gsq_init_kernel(const double *G, int ldg, int n, double *Gsq, int *flags) {
+  if (blockIdx.x == 0 && threadIdx.x < kLsrFlagWords) flags[threadIdx.x] = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e - (int64_t)i * n);
+    Gsq[e] = G[(int64_t)i * ldg + j];
+  }
+}
+
+// FP32 Cholesky factor R of the n x n Gram matrix in b.G (leading dimension ldg) and R^-1 in b.Ri (row-major,
+// upper); b.flags are cleared first and flags[0] = 1 marks a breakdown.  n <= 128: the single-CTA fused kernel
+// on a contiguous copy (two launches); larger n: 32-column panels, trailing updates and the blocked inverse.
+static void launch_lsr_cholesky(cudaStream_t st, const LsrBufs &b, int ldg, int n) {
+  if (n <= kCholFusedMaxL) {
+    lsr_gsq_init_kernel<<<rmc_blocks((int64_t)n * n, 256, 1024), 256, 0, st>>>(b.G, ldg, n, b.Gsq, b.flags);
+    chol32_fused_kernel<<<1, kCholFusedThreads, 0, st>>>(b.Gsq, n, b.Ri, &b.flags[0]);
+    rmc_note_launch(2);
+    return;
+  }
+  lsr_rf_init_kernel<<<rmc_blocks((int64_t)n * n, 256, 1024), 256, 0, st>>>(b.G, ldg, n, b.Rf, b.flags);
+  rmc_note_launch();
+  for (int j0 = 0; j0 < n; j0 += kPanel) {
+    const int bw = std::min(kPanel, n - j0), rest = n - j0 - bw;
+    lsr_chol_panel_kernel<<<std::max(1, (rest + 255) / 256), 256, 0, st>>>(b.Rf, n, j0, b.Dinv, &b.flags[0]);
+    rmc_note_launch();
+    if (rest > 0) {
+      const int T = (rest + 63) / 64;
+      lsr_chol_update_kernel<<<T * (T + 1) / 2, 256, 0, st>>>(b.Rf, n, j0, &b.flags[0]);
+      rmc_note_launch();
+    }
+  }
+  const int nb = (n + kPanel - 1) / kPanel;
+  const size_t tri_smem = sizeof(float) * ((size_t)nb * kPanel * kPanel + kPanel * kPanel);
+  lsr_tri_inv_kernel<<<nb, 1024, tri_smem, st>>>(b.Rf, b.Dinv, n, b.Ri, &b.flags[0]);
+  rmc_note_launch();
 }
 
 size_t rmc_lsr_solve_ws(int64_t s, int64_t n, int num_sms) {
@@ -1979,27 +2017,15 @@ int rmc_launch_lsr_solve(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n_, i
   RMC_TRY(launch_gram(ctx, SA, s, l, ldsa, b.G, b.gpart, kGramF32));
   {
     RmcProf prof(ctx, RMC_K_SMALL);
-    lsr_rf_init_kernel<<<rmc_blocks((int64_t)n * n, 256, 1024), 256, 0, st>>>(b.G, l, n, b.Rf, b.flags);
-    rmc_note_launch();
-    for (int j0 = 0; j0 < n; j0 += kPanel) {
-      const int bw = std::min(kPanel, n - j0), rest = n - j0 - bw;
-      lsr_chol_panel_kernel<<<std::max(1, (rest + 255) / 256), 256, 0, st>>>(b.Rf, n, j0, b.Dinv, &b.flags[0]);
-      rmc_note_launch();
-      if (rest > 0) {
-        const int T = (rest + 63) / 64;
-        lsr_chol_update_kernel<<<T * (T + 1) / 2, 256, 0, st>>>(b.Rf, n, j0, &b.flags[0]);
-        rmc_note_launch();
-      }
-    }
-    // M = R^-1 R^-T
     const int nb = (n + kPanel - 1) / kPanel;
     const size_t tri_smem = sizeof(float) * ((size_t)nb * kPanel * kPanel + kPanel * kPanel);
     if (tri_smem > 48 * 1024)
       RMC_TRY_CUDA(rmc_allow_smem(lsr_tri_inv_kernel, tri_smem));
-    lsr_tri_inv_kernel<<<nb, 1024, tri_smem, st>>>(b.Rf, b.Dinv, n, b.Ri, &b.flags[0]);
+    launch_lsr_cholesky(st, b, l, n);
+    // M = R^-1 R^-T
     const int T64 = (n + 63) / 64;
     lsr_inv_gram_kernel<<<T64 * (T64 + 1) / 2, 256, 0, st>>>(b.Ri, n, b.M, &b.flags[0]);
-    rmc_note_launch(2);
+    rmc_note_launch();
     RMC_TRY_CUDA(cudaMemsetAsync(b.xs, 0, sizeof(double) * n, st));
     const int chunks = atr_chunks(s);
     const int64_t rows_per = (s + chunks - 1) / chunks;
@@ -2058,27 +2084,15 @@ int rmc_launch_lsr_factor(rmc_ctx *ctx, const float *SA, int64_t s, int64_t n_, 
   RMC_TRY(launch_gram(ctx, SA, s, n, ldsa, b.G, gpart, kGramF32));
   {
     RmcProf prof(ctx, RMC_K_SMALL);
-    lsr_rf_init_kernel<<<rmc_blocks((int64_t)n * n, 256, 1024), 256, 0, st>>>(b.G, n, n, b.Rf, b.flags);
-    rmc_note_launch();
-    for (int j0 = 0; j0 < n; j0 += kPanel) {
-      const int bw = std::min(kPanel, n - j0), rest = n - j0 - bw;
-      lsr_chol_panel_kernel<<<std::max(1, (rest + 255) / 256), 256, 0, st>>>(b.Rf, n, j0, b.Dinv, &b.flags[0]);
-      rmc_note_launch();
-      if (rest > 0) {
-        const int T = (rest + 63) / 64;
-        lsr_chol_update_kernel<<<T * (T + 1) / 2, 256, 0, st>>>(b.Rf, n, j0, &b.flags[0]);
-        rmc_note_launch();
-      }
-    }
     const int nb = (n + kPanel - 1) / kPanel;
     const size_t tri_smem = sizeof(float) * ((size_t)nb * kPanel * kPanel + kPanel * kPanel);
     if (tri_smem > 48 * 1024)
       RMC_TRY_CUDA(rmc_allow_smem(lsr_tri_inv_kernel, tri_smem));
-    lsr_tri_inv_kernel<<<nb, 1024, tri_smem, st>>>(b.Rf, b.Dinv, n, b.Ri, &b.flags[0]);
+    launch_lsr_cholesky(st, b, n, n);
     const int T64 = (n + 63) / 64;
     lsr_inv_gram_kernel<<<T64 * (T64 + 1) / 2, 256, 0, st>>>(b.Ri, n, M, &b.flags[0]);
     lsr_flag_out_kernel<<<1, 1, 0, st>>>(b.flags, fail);
-    rmc_note_launch(3);
+    rmc_note_launch(2);
   }
   RMC_LAUNCH_CHECK();
   return RMC_OK;
